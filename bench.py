@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""End-to-end throughput of GMM superpixel EM (Ban, Liu, Cao, arXiv 1612.08792) on one GB300.
+
+A step is Algorithm 1, steps 1-7, on one synthetic 481x321 sRGB image
+(150 Voronoi regions, noise sigma 8; K = 1000 requested -> v = 12, K = 1040),
+10 EM iterations: CIELAB conversion, initialisation, 10 x (fused E-step +
+M-step partial sums, FP64 finalize with the eigenvalue floor), label pass
+with its log-likelihood.  The step is one CUDA-graph launch of the library
+(`gmmsp_segment`).  `value` is device time with the image already in HBM
+and L2 flushed (256 MiB memset) between timed steps; `e2e` adds the pinned
+host->device copy of the image and the device->host copy of the labels.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmmsp|reference]
+
+With N > 1 (torchrun) each rank runs an independent replica on its own image
+(no collective on the data path: the images are independent problems);
+`value` is all ranks' pixels over the slowest rank's time.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s end-to-end superpixels, learned-init vs plain EM at equal log-lik"
+UNIT = "Mpixel/s"
+W, H, K_REQ, ITERS, REGIONS, SIGMA = 481, 321, 1000, 10, 150, 8.0
+FLUSH_BYTES = 256 << 20
+# Algorithmic FP32 work of the fused E + M-partial pass, per (pixel, candidate):
+#   E: d = z - mu (5), block quadratic form (9 products, 9 multiply-adds = 27 minus
+#      the shared products folded: 23), log-normaliser add (1)              -> 28
+#   log-sum-exp: max, subtract, add, normalise                              ->  4
+#   M: W += R, R d (5), S1 += R d (5), 9 second-moment multiply-adds (18)   -> 29
+# plus per pixel 1 (log-likelihood add); 1 MUFU ex2 per candidate, 2 per pixel.
+FLOPS_PER_CAND = 61
+FLOPS_PER_PIXEL = 1
+# FP32 peak derived from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def workload_config(v, nx, ny, K):
+    return {
+        "workload": f"{W}x{H} synthetic Voronoi sRGB ({REGIONS} regions, noise sigma {SIGMA:g}), "
+                    f"K={K_REQ} requested -> v={v}, K={K}; {ITERS} plain-EM iterations (Sec. III-C init)",
+        "W": W, "H": H, "K": K, "v": v, "nx": nx, "ny": ny, "iters": ITERS,
+        "precision": "FP32 E-step, FP64 sufficient statistics / floor / inversion",
+        "l2": "flushed between timed steps (256 MiB memset, outside the timed interval)",
+        "init": "plain",
+    }
+
+
+def candidate_units(Wd, Hd, v, nx, ny):
+    """sum over pixels of |K_i|: candidates along x times candidates along y."""
+    def axis(extent, n):
+        tot = 0
+        for p in range(extent):
+            c = min(p // v, n)  # cell index (remainder strip -> n)
+            tot += sum(1 for kq in (c - 1, c, c + 1) if 0 <= kq < n)
+        return tot
+    return axis(Wd, nx) * axis(Hd, ny)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(", ") for r in self.f.read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_run(seconds: float, seed: int = 0):
+    """The FP64 CPU oracle as it stands (RGB -> CIELAB -> EM -> labels), on all host
+    threads, repeated for about `seconds`.  Returns (Mpixel/s, threads, reps)."""
+    import oracle
+    from synth import voronoi_image
+    img = voronoi_image(W, H, REGIONS, SIGMA, seed)
+    threads = oracle.max_threads()
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        lab = oracle.rgb2lab(img)
+        oracle.em(lab, W, H, K=K_REQ, T=ITERS)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return W * H * reps / el / 1e6, threads, reps, el
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    from synth import voronoi_image
+    img = voronoi_image(W, H, REGIONS, SIGMA, 0)
+    g = oracle.grid(W, H, K_REQ)
+    for _ in range(args.warmup):
+        oracle.em(oracle.rgb2lab(img), W, H, K=K_REQ, T=ITERS)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.em(oracle.rgb2lab(img), W, H, K=K_REQ, T=ITERS)
+    el = time.perf_counter() - t0
+    value = W * H * args.steps / el / 1e6
+    threads = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(g.v, g.nx, g.ny, g.K),
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} steps of one {W}x{H} image, RGB->labels, FP64 C oracle "
+                                   f"(OpenMP, {threads} threads)"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gmmsp(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    from synth import voronoi_image
+
+    img_np = voronoi_image(W, H, REGIONS, SIGMA, seed=rank)
+    img_host = torch.from_numpy(img_np).pin_memory()
+    img_dev = img_host.to("cuda")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    labels = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    sp = gm.Superpixels(img_dev, K=K_REQ, stream=stream)
+    v, nx, ny, K = sp.grid.v, sp.grid.nx, sp.grid.ny, sp.grid.K
+    N = W * H
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            sp.segment(img_dev, ITERS, out=labels)
+    stream.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(i & 0xff)
+                starts[i].record(stream)
+                sp.segment(img_dev, ITERS, out=labels)
+                ends[i].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * N * args.steps / (total_ms / 1e3) / 1e6
+
+    # log-likelihood of the timed configuration (for the equal-log-lik comparison)
+    with torch.cuda.stream(stream):
+        _, ll = sp.segment(img_dev, ITERS, out=labels, want_loglik=True)
+
+    # end to end through the public API with host buffers
+    labels_host = torch.empty((H, W), dtype=torch.int32).pin_memory()
+    dev_img2 = torch.empty_like(img_dev)
+    for _ in range(3):
+        sp.segment_host(img_host, labels_host, ITERS, dev_image=dev_img2, dev_labels=labels)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sp.segment_host(img_host, labels_host, ITERS, dev_image=dev_img2, dev_labels=labels)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = world * N * args.steps / e2e_s / 1e6
+
+    # roofline of the dominant kernel (fused E + M-partial pass), events on its stream
+    em_ms = sp.profile_kernel(gm.GMMSP_KERNEL_EM_PASS, reps=50, flush=flush)
+    units = candidate_units(W, H, v, nx, ny)
+    flops = units * FLOPS_PER_CAND + N * FLOPS_PER_PIXEL
+    achieved = flops / (em_ms * 1e-3) / 1e12
+    sp.close()
+
+    launches_per_step = 2 + 2 * ITERS + 1  # rgb2lab, init, (em_pass, finalize) x T, labels
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+        "data": "synthetic", "config": dict(workload_config(v, nx, ny, K), parallelism=f"replicas x{world}"),
+        "loglik_final": float(ll[-1]), "loglik_per_pixel": float(ll[-1]) / N,
+        "roofline": {"kernel": "k_em_pass (fused E-step + M-step partials)", "bound": "alu",
+                     "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "em_pass_ms": round(em_ms, 5), "flops_per_launch": flops},
+        "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": N * 3,
+                "d2h_bytes_per_step": N * 4},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mpx, threads, reps, el = cpu_oracle_run(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": round(mpx, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{reps} runs of the {W}x{H} workload (RGB->labels, T={ITERS}) "
+                                          f"in {el:.1f} s, FP64 C oracle, OpenMP {threads} threads"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gmmsp", choices=["gmmsp", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gmmsp(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

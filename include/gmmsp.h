@@ -1,0 +1,202 @@
+/*
+ * gmmsp.h - C ABI of the GB300 (sm_103a) GMM superpixel library.
+ *
+ * The library computes the superpixels of Ban, Liu and Cao, "Superpixel
+ * Segmentation Using Gaussian Mixture Model" (arXiv 1612.08792): one Gaussian
+ * per grid seed over the 5-D pixel vector z = (x, y, L, a, b) with a block
+ * diagonal covariance (Sec. III-C, Eq. BlockSigma), fitted by EM (Sec. III-B)
+ * where each pixel only sees the Gaussians of its neighbouring seeds
+ * (Eq. Ik), with the eigenvalue floor of Eq. (mlams)/(mlamc), and a label per
+ * pixel by maximum posterior (Eq. obtLi).  Algorithm 1, steps 1-7, is split
+ * over gmmsp_init (step 1), gmmsp_em_iters (steps 2-6) and gmmsp_labels
+ * (step 7).  The connectivity post-processing (step 8) is not part of it.
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *     memory must stay valid until the work queued on the context's stream
+ *     has finished.  Pointers named *_host are ordinary host memory.
+ *   - Work is queued on the CUDA stream given to gmmsp_init and returns
+ *     without waiting, except where a call says it synchronises.
+ *   - A call returns a gmmsp_status and never aborts the process.  Invalid
+ *     arguments are reported before any work is queued.  A CUDA error, or a
+ *     non-finite input found on the device, puts the context into an error
+ *     state: that call and every later call on it return GMMSP_E_STATE or
+ *     the original code; gmmsp_last_error() describes the cause.
+ *   - Contexts are not thread-safe; use one context per host thread.
+ *   - Superpixel k sits at grid cell (k_x, k_y) = (k mod n_x, k / n_x)
+ *     (Eq. kxy).  Per-superpixel arrays are indexed by k.
+ */
+#ifndef GMMSP_H
+#define GMMSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmmsp_ctx_s *gmmsp_ctx;   /* opaque, owned by the library */
+
+typedef enum {
+    GMMSP_OK = 0,
+    GMMSP_E_INVALID = 1,   /* bad argument; nothing was queued            */
+    GMMSP_E_CUDA = 2,      /* a CUDA call failed                          */
+    GMMSP_E_NOMEM = 3,     /* device allocation failed                    */
+    GMMSP_E_NUMERIC = 4,   /* non-finite input or parameters              */
+    GMMSP_E_TIMEOUT = 5,   /* a bounded device-side wait ran out          */
+    GMMSP_E_STATE = 6      /* context is in an error state / wrong state  */
+} gmmsp_status;
+
+/* Image formats accepted by gmmsp_init / gmmsp_reinit. */
+enum {
+    GMMSP_RGB8 = 0,   /* H rows of W x (R,G,B) uint8 sRGB, row pitch in bytes   */
+    GMMSP_LAB32 = 1   /* H rows of W x (L,a,b) float32 CIELAB, row pitch in bytes */
+};
+
+/* Arithmetic of the EM loop. */
+enum {
+    GMMSP_PREC_MIXED = 0, /* FP32 E-step; FP64 sufficient statistics from the
+                             per-cell partial on, FP64 floor and inversion  */
+    GMMSP_PREC_FP32 = 1   /* everything in FP32, raw (unshifted) moments    */
+};
+
+typedef struct {
+    int spacing;        /* v_x = v_y; if > 0 it wins over K (Eq. nxyK)          */
+    int K;              /* requested superpixel count; v = floor(sqrt(WH/K))
+                           (Eq. vxy).  The effective K = n_x n_y is reported by
+                           gmmsp_get_grid.                                     */
+    float eps_s;        /* spatial eigenvalue floor, px^2 (Sec. III-C: 2)       */
+    float eps_c;        /* colour eigenvalue floor, CIELAB^2 (Sec. IV-A: 8)     */
+    float lambda_c;     /* initial colour standard deviation; Sigma_c,0 =
+                           lambda_c^2 I (Sec. III-C; Sec. IV-A uses 8)          */
+    int input_format;   /* GMMSP_RGB8 or GMMSP_LAB32                          */
+    int precision;      /* GMMSP_PREC_MIXED or GMMSP_PREC_FP32                 */
+} gmmsp_params;
+
+/* Fills p with the paper's settings: spacing 0, K 0 (the caller sets one of
+ * them), eps_s 2, eps_c 8, lambda_c 8, RGB8, mixed precision. */
+void gmmsp_default_params(gmmsp_params *p);
+
+/*
+ * Creates a context for W x H images and runs Algorithm 1, step 1 on
+ * image_dev: converts the image to CIELAB (Sec. IV) and sets theta_0
+ * (Sec. III-C: mu_k = z at the centre pixel of cell k, Sigma_s =
+ * diag(v^2, v^2), Sigma_c = lambda_c^2 I).
+ *   image_dev    device pointer to the first row (see GMMSP_RGB8/LAB32);
+ *   pitch_bytes  distance between rows in bytes, >= 3 W (RGB8) or 12 W (LAB32);
+ *   stream       cudaStream_t to queue work on (NULL = legacy default stream).
+ * Allocates the context's device buffers (O(W H) bytes for the CIELAB image,
+ * O(K) for theta and the per-cell partial sums).  Errors: GMMSP_E_INVALID
+ * when W, H < 1, when neither spacing nor K is positive, when the grid is
+ * empty (n_x or n_y = 0), when eps or lambda_c is not positive, or for an
+ * unknown format; GMMSP_E_NOMEM; GMMSP_E_CUDA.  On error *out is NULL.
+ */
+gmmsp_status gmmsp_init(gmmsp_ctx *out, const void *image_dev, int width, int height,
+                        int pitch_bytes, const gmmsp_params *p, void *stream);
+
+/* Algorithm 1, step 1 again for a new image of the same size and format,
+ * without allocating.  Clears an earlier error state. */
+gmmsp_status gmmsp_reinit(gmmsp_ctx c, const void *image_dev, int pitch_bytes);
+
+/*
+ * Runs `iters` rounds of Algorithm 1, steps 4-6 on the current theta: each
+ * round is an E-step over every pixel (Eq. Rik, each pixel over its <= 9
+ * candidate Gaussians of Eq. Ik) fused with the per-cell partial sums of the
+ * M-step, then the mean and block covariance update (Eq. UpdateMu,
+ * UpdateSigS, UpdateSigC) with the eigenvalue floor (Eq. mlams, mlamc).
+ * The first E-step of a round on theta_t also gives L(theta_t) (the
+ * log-likelihood following Eq. ftheta, natural log, with the
+ * (2 pi)^(-5/2) constant).
+ *   loglik_host  NULL, or `iters` doubles receiving L(theta_t) of each round;
+ *                when non-NULL the call synchronises the stream.
+ * iters = 0 does nothing.  Errors: GMMSP_E_INVALID (iters < 0),
+ * GMMSP_E_CUDA, GMMSP_E_STATE.
+ */
+gmmsp_status gmmsp_em_iters(gmmsp_ctx c, int iters, double *loglik_host);
+
+/*
+ * Algorithm 1, step 7 (with the E-step of step 6 on the current theta):
+ * labels_dev[y W + x] = argmax over the pixel's candidates k of the
+ * posterior (Eq. obtLi); ties go to the smaller k.
+ *   labels_dev   device int32 array of W H entries, written;
+ *   loglik_host  NULL or one double receiving L(theta) of this E-step;
+ *                when non-NULL the call synchronises the stream.
+ */
+gmmsp_status gmmsp_labels(gmmsp_ctx c, int32_t *labels_dev, double *loglik_host);
+
+/*
+ * Whole pipeline in one call, Algorithm 1 steps 1-7: gmmsp_reinit(image),
+ * gmmsp_em_iters(iters), gmmsp_labels.  The kernel sequence is captured into
+ * a CUDA graph on the first call for a given (iters, image, labels) and
+ * replayed afterwards, so repeated calls cost one graph launch.
+ *   loglik_host  NULL, or iters + 1 doubles: L(theta_0) .. L(theta_iters);
+ *                when non-NULL the call synchronises the stream.
+ */
+gmmsp_status gmmsp_segment(gmmsp_ctx c, const void *image_dev, int pitch_bytes, int iters,
+                           int32_t *labels_dev, double *loglik_host);
+
+/*
+ * Copies the context's CIELAB image (the pixel colours c_i of z_i, Sec. III-A,
+ * after the conversion of Sec. IV) to the host as W H x (L, a, b) float32
+ * (synchronises).  Errors: GMMSP_E_INVALID for NULL.
+ */
+gmmsp_status gmmsp_get_lab(gmmsp_ctx c, float *lab_host);
+
+/* Grid of Eq. (vxy)/(nxyK): spacing v, n_x, n_y, K = n_x n_y.  Any pointer may be NULL. */
+gmmsp_status gmmsp_get_grid(gmmsp_ctx c, int *v, int *nx, int *ny, int *K);
+
+/*
+ * Copies theta to the host (synchronises): mu_host K x 5 (x, y, L, a, b),
+ * cov_s_host K x 3 (xx, xy, yy), cov_c_host K x 6 (LL, La, Lb, aa, ab, bb),
+ * the floored covariances of Eq. (eigdecrs)/(eigdecrc).  Any may be NULL.
+ */
+gmmsp_status gmmsp_get_params(gmmsp_ctx c, double *mu_host, double *cov_s_host, double *cov_c_host);
+
+/*
+ * Replaces theta (same layout as gmmsp_get_params), e.g. to resume EM from a
+ * saved state or to start from another initialisation.  Covariances must be
+ * symmetric positive definite; they are used as given (no floor).  Errors:
+ * GMMSP_E_INVALID for a NULL pointer, GMMSP_E_NUMERIC for a non-finite value
+ * or a covariance that is not positive definite.  Synchronises.
+ */
+gmmsp_status gmmsp_set_params(gmmsp_ctx c, const double *mu_host, const double *cov_s_host,
+                              const double *cov_c_host);
+
+/*
+ * Counters since the last init/reinit (synchronises): dead = superpixels
+ * kept unchanged because their total posterior weight was below 1e-8;
+ * raised_s / raised_c = eigenvalues lifted to eps_s / eps_c by the floor.
+ * Any pointer may be NULL.
+ */
+gmmsp_status gmmsp_get_stats(gmmsp_ctx c, long long *dead, long long *raised_s, long long *raised_c);
+
+/*
+ * Kernel timing (no counterpart in the paper: a measurement aid).  Launches
+ * one kernel of the pipeline `reps` times on the context's stream, each
+ * launch between two CUDA events, and returns the mean launch time in
+ * milliseconds (synchronises).  Only kernels that leave theta unchanged can
+ * be repeated, so `which` is
+ *   GMMSP_KERNEL_EM_PASS  (0)  the fused E-step + M-step partial pass on
+ *                              the current theta (rewrites the partial sums);
+ *   GMMSP_KERNEL_LABELS   (1)  the label pass (writes labels_dev).
+ * If flush_dev is non-NULL, flush_bytes of it are overwritten before every
+ * launch (outside the timed interval) so each launch starts with a cold L2.
+ */
+enum { GMMSP_KERNEL_EM_PASS = 0, GMMSP_KERNEL_LABELS = 1 };
+gmmsp_status gmmsp_profile_kernel(gmmsp_ctx c, int which, int reps, int32_t *labels_dev,
+                                  void *flush_dev, unsigned long long flush_bytes, double *avg_ms);
+
+/* Text of the last error on c (never NULL; "" when there is none). */
+const char *gmmsp_last_error(gmmsp_ctx c);
+
+/* Name of a status code. */
+const char *gmmsp_status_string(gmmsp_status s);
+
+/* Frees the context and its device buffers (synchronises its stream). NULL is ignored. */
+void gmmsp_destroy(gmmsp_ctx c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMMSP_H */

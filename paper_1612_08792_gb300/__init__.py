@@ -1,0 +1,326 @@
+"""GB300-native GMM superpixels (Ban, Liu, Cao, arXiv 1612.08792).
+
+Thin Python binding over the C ABI of ``libgmmsp.so`` (``include/gmmsp.h``).
+Every function of the C ABI is exposed under the same name and only
+marshals arguments: images, labels and streams are passed as raw device
+pointers taken from torch tensors; every step of the computation runs in
+the library's CUDA kernels.  There is no CPU fallback: if the library has
+not been built, or no CUDA device is present, calls raise.
+
+Convenience layer: :class:`Superpixels` owns one context and offers
+``em_iters`` / ``labels`` / ``segment`` on torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "GMMSP_RGB8", "GMMSP_LAB32", "GMMSP_PREC_MIXED", "GMMSP_PREC_FP32", "GmmspError",
+    "gmmsp_params", "load_library", "library_path", "Superpixels",
+    "gmmsp_default_params", "gmmsp_init", "gmmsp_reinit", "gmmsp_em_iters", "gmmsp_labels",
+    "gmmsp_segment", "gmmsp_get_lab", "gmmsp_get_grid", "gmmsp_get_params", "gmmsp_set_params", "gmmsp_get_stats",
+    "gmmsp_profile_kernel", "gmmsp_last_error", "gmmsp_status_string", "gmmsp_destroy",
+]
+
+GMMSP_RGB8, GMMSP_LAB32 = 0, 1
+GMMSP_PREC_MIXED, GMMSP_PREC_FP32 = 0, 1
+STATUS = {0: "GMMSP_OK", 1: "GMMSP_E_INVALID", 2: "GMMSP_E_CUDA", 3: "GMMSP_E_NOMEM",
+          4: "GMMSP_E_NUMERIC", 5: "GMMSP_E_TIMEOUT", 6: "GMMSP_E_STATE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "_build", "libgmmsp.so")
+
+
+class GmmspError(RuntimeError):
+    def __init__(self, status: int, message: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+
+
+class gmmsp_params(ctypes.Structure):
+    """Mirror of the C struct ``gmmsp_params`` (include/gmmsp.h)."""
+    _fields_ = [("spacing", ctypes.c_int), ("K", ctypes.c_int), ("eps_s", ctypes.c_float),
+                ("eps_c", ctypes.c_float), ("lambda_c", ctypes.c_float),
+                ("input_format", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+def load_library(path: str | None = None):
+    """Loads libgmmsp.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgmmsp.so not found at {path}: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        pint = ctypes.POINTER(ctypes.c_int)
+        pll = ctypes.POINTER(ctypes.c_longlong)
+        sig = {
+            "gmmsp_default_params": (None, [ctypes.POINTER(gmmsp_params)]),
+            "gmmsp_init": (I, [PP, P, I, I, I, ctypes.POINTER(gmmsp_params), P]),
+            "gmmsp_reinit": (I, [P, P, I]),
+            "gmmsp_em_iters": (I, [P, I, P]),
+            "gmmsp_labels": (I, [P, P, P]),
+            "gmmsp_segment": (I, [P, P, I, I, P, P]),
+            "gmmsp_get_lab": (I, [P, P]),
+            "gmmsp_get_grid": (I, [P, pint, pint, pint, pint]),
+            "gmmsp_get_params": (I, [P, P, P, P]),
+            "gmmsp_set_params": (I, [P, P, P, P]),
+            "gmmsp_get_stats": (I, [P, pll, pll, pll]),
+            "gmmsp_profile_kernel": (I, [P, I, I, P, P, ctypes.c_ulonglong, ctypes.POINTER(D)]),
+            "gmmsp_last_error": (ctypes.c_char_p, [P]),
+            "gmmsp_status_string": (ctypes.c_char_p, [I]),
+            "gmmsp_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(ctx, st: int):
+    if st != 0:
+        msg = ""
+        if ctx:
+            msg = (load_library().gmmsp_last_error(ctx) or b"").decode()
+        raise GmmspError(st, msg)
+
+
+def _dptr(t) -> int:
+    """Device pointer of a CUDA torch tensor (or an int address)."""
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor (device memory)")
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ------------------------------------------------------------------ C ABI, same names
+def gmmsp_default_params() -> gmmsp_params:
+    p = gmmsp_params()
+    load_library().gmmsp_default_params(ctypes.byref(p))
+    return p
+
+
+def gmmsp_init(image, width: int, height: int, pitch_bytes: int, params: gmmsp_params, stream=None):
+    ctx = ctypes.c_void_p()
+    st = load_library().gmmsp_init(ctypes.byref(ctx), _dptr(image), int(width), int(height),
+                                   int(pitch_bytes), ctypes.byref(params), _stream_handle(stream))
+    _check(None, st)
+    return ctx
+
+
+def gmmsp_reinit(ctx, image, pitch_bytes: int) -> None:
+    _check(ctx, load_library().gmmsp_reinit(ctx, _dptr(image), int(pitch_bytes)))
+
+
+def gmmsp_em_iters(ctx, iters: int, want_loglik: bool = False):
+    ll = np.zeros(max(iters, 1), dtype=np.float64) if want_loglik else None
+    _check(ctx, load_library().gmmsp_em_iters(
+        ctx, int(iters), ll.ctypes.data_as(ctypes.c_void_p) if ll is not None else None))
+    return ll[:iters] if ll is not None else None
+
+
+def gmmsp_labels(ctx, labels, want_loglik: bool = False):
+    ll = np.zeros(1, dtype=np.float64) if want_loglik else None
+    _check(ctx, load_library().gmmsp_labels(
+        ctx, _dptr(labels), ll.ctypes.data_as(ctypes.c_void_p) if ll is not None else None))
+    return float(ll[0]) if ll is not None else None
+
+
+def gmmsp_segment(ctx, image, pitch_bytes: int, iters: int, labels, want_loglik: bool = False):
+    ll = np.zeros(iters + 1, dtype=np.float64) if want_loglik else None
+    _check(ctx, load_library().gmmsp_segment(
+        ctx, _dptr(image), int(pitch_bytes), int(iters), _dptr(labels),
+        ll.ctypes.data_as(ctypes.c_void_p) if ll is not None else None))
+    return ll
+
+
+def gmmsp_get_lab(ctx, H: int, W: int):
+    out = np.zeros((H, W, 3), dtype=np.float32)
+    _check(ctx, load_library().gmmsp_get_lab(ctx, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def gmmsp_get_grid(ctx):
+    v, nx, ny, K = (ctypes.c_int() for _ in range(4))
+    _check(ctx, load_library().gmmsp_get_grid(ctx, ctypes.byref(v), ctypes.byref(nx),
+                                              ctypes.byref(ny), ctypes.byref(K)))
+    return v.value, nx.value, ny.value, K.value
+
+
+def gmmsp_get_params(ctx):
+    K = gmmsp_get_grid(ctx)[3]
+    mu, cs, cc = np.zeros((K, 5)), np.zeros((K, 3)), np.zeros((K, 6))
+    _check(ctx, load_library().gmmsp_get_params(ctx, mu.ctypes.data_as(ctypes.c_void_p),
+                                                cs.ctypes.data_as(ctypes.c_void_p),
+                                                cc.ctypes.data_as(ctypes.c_void_p)))
+    return mu, cs, cc
+
+
+def gmmsp_set_params(ctx, mu, cs, cc) -> None:
+    K = gmmsp_get_grid(ctx)[3]
+    mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(K, 5)
+    cs = np.ascontiguousarray(cs, dtype=np.float64).reshape(K, 3)
+    cc = np.ascontiguousarray(cc, dtype=np.float64).reshape(K, 6)
+    _check(ctx, load_library().gmmsp_set_params(ctx, mu.ctypes.data_as(ctypes.c_void_p),
+                                                cs.ctypes.data_as(ctypes.c_void_p),
+                                                cc.ctypes.data_as(ctypes.c_void_p)))
+
+
+def gmmsp_get_stats(ctx):
+    d, rs, rc = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(ctx, load_library().gmmsp_get_stats(ctx, ctypes.byref(d), ctypes.byref(rs), ctypes.byref(rc)))
+    return d.value, rs.value, rc.value
+
+
+GMMSP_KERNEL_EM_PASS, GMMSP_KERNEL_LABELS = 0, 1
+
+
+def gmmsp_profile_kernel(ctx, which: int, reps: int, labels=None, flush=None) -> float:
+    ms = ctypes.c_double()
+    fptr = _dptr(flush) if flush is not None else None
+    fbytes = int(flush.numel() * flush.element_size()) if flush is not None else 0
+    _check(ctx, load_library().gmmsp_profile_kernel(
+        ctx, int(which), int(reps), _dptr(labels) if labels is not None else None, fptr, fbytes,
+        ctypes.byref(ms)))
+    return ms.value
+
+
+def gmmsp_last_error(ctx) -> str:
+    return (load_library().gmmsp_last_error(ctx) or b"").decode()
+
+
+def gmmsp_status_string(status: int) -> str:
+    return load_library().gmmsp_status_string(int(status)).decode()
+
+
+def gmmsp_destroy(ctx) -> None:
+    load_library().gmmsp_destroy(ctx)
+
+
+# ------------------------------------------------------------------ convenience
+@dataclass
+class Grid:
+    v: int
+    nx: int
+    ny: int
+    K: int
+
+
+class Superpixels:
+    """One library context over (H, W, 3) uint8 RGB or float32 CIELAB CUDA tensors."""
+
+    def __init__(self, image, K: int = 0, spacing: int = 0, eps_s: float = 2.0, eps_c: float = 8.0,
+                 lambda_c: float = 8.0, precision: int = GMMSP_PREC_MIXED, stream=None):
+        import torch
+        if image.dim() != 3 or image.shape[2] != 3:
+            raise ValueError("image must be (H, W, 3)")
+        if image.dtype == torch.uint8:
+            fmt = GMMSP_RGB8
+        elif image.dtype == torch.float32:
+            fmt = GMMSP_LAB32
+        else:
+            raise ValueError("image must be uint8 sRGB or float32 CIELAB")
+        p = gmmsp_default_params()
+        p.spacing, p.K, p.eps_s, p.eps_c, p.lambda_c = int(spacing), int(K), eps_s, eps_c, lambda_c
+        p.input_format, p.precision = fmt, int(precision)
+        self.H, self.W = int(image.shape[0]), int(image.shape[1])
+        self.format = fmt
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = gmmsp_init(image, self.W, self.H, self._pitch(image), p, self.stream)
+        self.grid = Grid(*gmmsp_get_grid(self.ctx))
+
+    @staticmethod
+    def _pitch(image) -> int:
+        if image.stride(2) != 1 or image.stride(1) != 3:
+            raise ValueError("image rows must be packed (stride (pitch, 3, 1))")
+        return int(image.stride(0) * image.element_size())
+
+    def reinit(self, image) -> None:
+        gmmsp_reinit(self.ctx, image, self._pitch(image))
+
+    def em_iters(self, iters: int, want_loglik: bool = False):
+        return gmmsp_em_iters(self.ctx, iters, want_loglik)
+
+    def labels(self, out=None, want_loglik: bool = False):
+        import torch
+        if out is None:
+            out = torch.empty((self.H, self.W), dtype=torch.int32, device="cuda")
+        ll = gmmsp_labels(self.ctx, out, want_loglik)
+        return (out, ll) if want_loglik else out
+
+    def segment(self, image, iters: int = 10, out=None, want_loglik: bool = False):
+        import torch
+        if out is None:
+            out = torch.empty((self.H, self.W), dtype=torch.int32, device="cuda")
+        ll = gmmsp_segment(self.ctx, image, self._pitch(image), iters, out, want_loglik)
+        return (out, ll) if want_loglik else out
+
+    def segment_host(self, image_host, labels_host, iters: int = 10, dev_image=None, dev_labels=None,
+                     want_loglik: bool = False):
+        """Host buffers in, host labels out: H2D copy, the graph-captured pipeline, D2H copy.
+
+        image_host / labels_host should be pinned CPU tensors; dev_image / dev_labels
+        are reusable device staging buffers (allocated on first use).
+        """
+        import torch
+        with torch.cuda.stream(self.stream):
+            if dev_image is None:
+                dev_image = torch.empty_like(image_host, device="cuda")
+            if dev_labels is None:
+                dev_labels = torch.empty((self.H, self.W), dtype=torch.int32, device="cuda")
+            dev_image.copy_(image_host, non_blocking=True)
+            ll = gmmsp_segment(self.ctx, dev_image, self._pitch(dev_image), iters, dev_labels, want_loglik)
+            labels_host.copy_(dev_labels, non_blocking=True)
+        self.stream.synchronize()
+        return ll
+
+    def profile_kernel(self, which: int, reps: int = 20, labels=None, flush=None) -> float:
+        return gmmsp_profile_kernel(self.ctx, which, reps, labels, flush)
+
+    def get_lab(self):
+        return gmmsp_get_lab(self.ctx, self.H, self.W)
+
+    def get_params(self):
+        return gmmsp_get_params(self.ctx)
+
+    def set_params(self, mu, cs, cc) -> None:
+        gmmsp_set_params(self.ctx, mu, cs, cc)
+
+    def stats(self):
+        return gmmsp_get_stats(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            gmmsp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

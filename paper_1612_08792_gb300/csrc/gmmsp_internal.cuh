@@ -1,0 +1,79 @@
+// Internal declarations shared by the translation units of libgmmsp.
+//
+// Geometry (Eq. vxy, nxyK, Ik, kxy).  The image is covered by cells of
+// v x v pixels; cell (cx, cy) spans x in [cx v, min((cx+1) v, W)).  When
+// W mod v != 0 the last cell column cx = n_x is a narrower remainder strip
+// (likewise for rows).  Every pixel of a cell has the same candidate set:
+// k_x in {cx-1, cx, cx+1} and k_y in {cy-1, cy, cy+1}, clipped to the seed
+// grid [0, n_x) x [0, n_y).  This is Eq. (Ik) evaluated per cell: pixel x
+// lies in the x-window [max(0, v(k_x-1)), min(W, v(k_x+2))) exactly when
+// |floor(x/v) - k_x| <= 1 (the min(W, .) bound only matters for k_x = n_x-1,
+// whose window then reaches W and so covers the remainder strip).
+//
+// A candidate is addressed by its slot s = (k_y - cy + 1) * 3 + (k_x - cx + 1),
+// so increasing s is increasing k.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gmmsp {
+
+constexpr int kSlots = 9;          // |K_i| <= 9
+constexpr int kStats = 15;         // W, S1[5], S2s[3], S2c[6]
+constexpr int kPartStride = kSlots * kStats + 1;  // + per-cell log-likelihood = 136
+constexpr int kGP = 16;            // floats of packed E-step parameters per superpixel
+constexpr int kTheta = 16;         // doubles of master parameters per superpixel
+
+// Statistic index inside a slot.
+enum : int { ST_W = 0, ST_S1 = 1, ST_S2S = 6, ST_S2C = 9 };
+
+// Packed FP32 E-step parameters of superpixel k (64 bytes, 16-byte aligned):
+//   [0..4]   mu (x, y, L, a, b)
+//   [5..7]   spatial quadratic form coefficients (xx, 2xy, yy) of
+//            -(1/2) log2(e) Sigma_s^{-1}
+//   [8..13]  colour coefficients (LL, aa, bb, 2La, 2Lb, 2ab) of
+//            -(1/2) log2(e) Sigma_c^{-1}
+//   [14]     log2 of the Gaussian normaliser (2 pi)^{-5/2} det(Sigma)^{-1/2}
+//   [15]     unused
+// so log2 p(z; theta_k) = gp[14] + the two quadratic forms in d = z - mu.
+//
+// Master FP64 parameters (128 bytes): [0..4] mu, [5..7] Sigma_s (xx, xy, yy),
+// [8..13] Sigma_c (LL, La, Lb, aa, ab, bb), [14..15] unused.
+
+struct Geom {
+  int W, H;      // image size
+  int v;         // spacing v_x = v_y
+  int nx, ny;    // seed grid, K = nx * ny
+  int K;
+  int ncx, ncy;  // cell grid incl. remainder strips: ceil(W / v), ceil(H / v)
+  int ncells;
+};
+
+// Device counters (unsigned long long): dead, raised_s, raised_c, nonfinite input.
+enum : int { CNT_DEAD = 0, CNT_RAISED_S = 1, CNT_RAISED_C = 2, CNT_NONFINITE = 3, CNT_N = 4 };
+
+// ---- launchers (each returns the launch's cudaError_t) ----
+cudaError_t launch_rgb2lab(const uint8_t* img, long long pitch, const Geom& g, float4* lab,
+                           unsigned long long* counters, cudaStream_t s);
+cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float4* lab,
+                         unsigned long long* counters, cudaStream_t s);
+cudaError_t launch_init_theta(const float4* lab, const Geom& g, double lambda_c, double* theta,
+                              float* gp, cudaStream_t s);
+cudaError_t launch_em_pass(const float4* lab, const Geom& g, const float* gp, void* partials,
+                           int precision, cudaStream_t s);
+cudaError_t launch_label_pass(const float4* lab, const Geom& g, const float* gp, int32_t* labels,
+                              double* cell_ll, cudaStream_t s);
+// Finalize: ws holds finalize_workspace_doubles(g) doubles, ticket one zeroed
+// unsigned that the kernel leaves at zero.  llk_out (device) receives the
+// log-likelihood of the E-step that produced the partials.
+cudaError_t launch_finalize(const Geom& g, const void* partials, double* theta, float* gp,
+                            double eps_s, double eps_c, double* llk_out, double* ws,
+                            unsigned* ticket, unsigned long long* counters, int precision,
+                            cudaStream_t s);
+cudaError_t launch_ll_reduce(const double* cell_ll, int n, double* out, double* ws, unsigned* ticket,
+                             const Geom& g, cudaStream_t s);
+size_t finalize_workspace_doubles(const Geom& g);
+cudaError_t launch_pack_theta(const Geom& g, double* theta, float* gp, int* bad, cudaStream_t s);
+
+}  // namespace gmmsp

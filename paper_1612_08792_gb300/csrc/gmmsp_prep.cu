@@ -1,0 +1,174 @@
+// Input preparation and initial parameters.
+//
+//  * k_rgb2lab: sRGB uint8 -> CIELAB float4 (L, a, b, 0) per pixel.  The
+//    paper runs in CIELAB (Sec. IV, first paragraph) without fixing the RGB
+//    space or the white; this library reads the input as sRGB with the D65
+//    white.  The RGB -> XYZ matrix is not a literal table: the host derives
+//    it from the sRGB primaries and the white point (see api), and the
+//    kernel applies the sRGB transfer curve (through a 256-entry table built
+//    per block with powf) and the CIE 1976 L*a*b* formulas.
+//  * k_lab32: repacks a caller's float32 L,a,b image into float4 and counts
+//    non-finite values.
+//  * k_init_theta: Sec. III-C initialisation: mu_k = z of the centre pixel of
+//    cell k, Sigma_s = diag(v^2, v^2), Sigma_c = lambda_c^2 I.
+//  * k_pack_theta: re-derives the packed E-step coefficients from FP64
+//    parameters supplied by the caller (resume / external initialisation).
+#include <math.h>
+
+#include "gmmsp_internal.cuh"
+#include "gmmsp_math.cuh"
+
+namespace gmmsp {
+
+struct Rgb2LabConst {
+  float m[9];         // linear sRGB -> XYZ, row major
+  float inv_white[3]; // 1 / (Xn, Yn, Zn)
+};
+
+__device__ __forceinline__ float cielab_f(float t) {
+  // CIE 1976: cube root above (6/29)^3, the linear segment below.
+  const float d3 = 216.f / 24389.f;             // (6/29)^3
+  const float slope = 841.f / 108.f;            // 1 / (3 (6/29)^2)
+  return t > d3 ? cbrtf(t) : fmaf(slope, t, 4.f / 29.f);
+}
+
+__global__ void __launch_bounds__(256) k_rgb2lab(const uint8_t* __restrict__ img, long long pitch,
+                                                 int W, int H, float4* __restrict__ lab,
+                                                 Rgb2LabConst k) {
+  __shared__ float lin[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    const float c = float(i) * (1.f / 255.f);
+    lin[i] = c <= 0.04045f ? c * (1.f / 12.92f) : powf((c + 0.055f) * (1.f / 1.055f), 2.4f);
+  }
+  __syncthreads();
+  const long long N = (long long)W * H;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int y = int(idx / W), x = int(idx - (long long)y * W);
+    const uint8_t* p = img + (long long)y * pitch + 3LL * x;
+    const float r = lin[p[0]], g = lin[p[1]], b = lin[p[2]];
+    const float* m = k.m;
+    const float X = fmaf(m[0], r, fmaf(m[1], g, m[2] * b)) * k.inv_white[0];
+    const float Y = fmaf(m[3], r, fmaf(m[4], g, m[5] * b)) * k.inv_white[1];
+    const float Z = fmaf(m[6], r, fmaf(m[7], g, m[8] * b)) * k.inv_white[2];
+    const float fx = cielab_f(X), fy = cielab_f(Y), fz = cielab_f(Z);
+    lab[idx] = make_float4(116.f * fy - 16.f, 500.f * (fx - fy), 200.f * (fy - fz), 0.f);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_lab32(const float* __restrict__ img, long long pitch, int W,
+                                               int H, float4* __restrict__ lab,
+                                               unsigned long long* __restrict__ counters) {
+  const long long N = (long long)W * H;
+  unsigned bad = 0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int y = int(idx / W), x = int(idx - (long long)y * W);
+    const float* p = reinterpret_cast<const float*>(reinterpret_cast<const char*>(img) +
+                                                    (long long)y * pitch) + 3LL * x;
+    const float L = p[0], a = p[1], b = p[2];
+    bad += !(isfinite(L) && isfinite(a) && isfinite(b));
+    lab[idx] = make_float4(L, a, b, 0.f);
+  }
+  bad = __reduce_add_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&counters[CNT_NONFINITE], (unsigned long long)bad);
+}
+
+__global__ void k_init_theta(const float4* __restrict__ lab, Geom g, double lambda_c,
+                             double* __restrict__ theta, float* __restrict__ gp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.K) return;
+  const int kx = k % g.nx, ky = k / g.nx;
+  const int x = kx * g.v + g.v / 2, y = ky * g.v + g.v / 2;
+  const float4 c = lab[(long long)y * g.W + x];
+  const double mu[5] = {double(x), double(y), double(c.x), double(c.y), double(c.z)};
+  const double vv = double(g.v) * double(g.v), ll = lambda_c * lambda_c;
+  const double cs[3] = {vv, 0.0, vv};
+  const double cc[6] = {ll, 0.0, 0.0, ll, 0.0, ll};
+  double* th = theta + (long long)k * kTheta;
+  for (int i = 0; i < 5; ++i) th[i] = mu[i];
+  for (int i = 0; i < 3; ++i) th[5 + i] = cs[i];
+  for (int i = 0; i < 6; ++i) th[8 + i] = cc[i];
+  th[14] = th[15] = 0.0;
+  pack_gp<double>(mu, cs, cc, gp + (long long)k * kGP);
+}
+
+__global__ void k_pack_theta(Geom g, const double* __restrict__ theta, float* __restrict__ gp,
+                             int* __restrict__ bad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.K) return;
+  const double* th = theta + (long long)k * kTheta;
+  bool ok = true;
+  for (int i = 0; i < 14; ++i) ok = ok && isfinite(th[i]);
+  ok = ok && pack_gp<double>(th, th + 5, th + 8, gp + (long long)k * kGP);
+  if (!ok) atomicAdd(bad, 1);
+}
+
+static int grid_for(long long n, int block) {
+  long long b = (n + block - 1) / block;
+  if (b > 152LL * 16) b = 152LL * 16;
+  return int(b < 1 ? 1 : b);
+}
+
+// Host-side construction of the sRGB -> XYZ matrix from the primaries'
+// chromaticities and the white point (standard RGB colourimetry: each
+// column is a primary's XYZ scaled so that RGB = (1, 1, 1) maps to white).
+static Rgb2LabConst make_rgb2lab_const() {
+  const double prim[3][2] = {{0.64, 0.33}, {0.30, 0.60}, {0.15, 0.06}};  // R, G, B (x, y)
+  const double white[3] = {0.95047, 1.0, 1.08883};                        // D65 XYZ, Y = 1
+  double P[3][3];
+  for (int j = 0; j < 3; ++j) {
+    const double x = prim[j][0], y = prim[j][1];
+    P[0][j] = x / y;
+    P[1][j] = 1.0;
+    P[2][j] = (1.0 - x - y) / y;
+  }
+  // Solve P s = white by Cramer's rule.
+  auto det3 = [](const double A[3][3]) {
+    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+           A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  };
+  const double D = det3(P);
+  double s[3];
+  for (int j = 0; j < 3; ++j) {
+    double Q[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) Q[r][c] = (c == j) ? white[r] : P[r][c];
+    s[j] = det3(Q) / D;
+  }
+  Rgb2LabConst k;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) k.m[3 * r + c] = float(P[r][c] * s[c]);
+  for (int r = 0; r < 3; ++r) k.inv_white[r] = float(1.0 / white[r]);
+  return k;
+}
+
+cudaError_t launch_rgb2lab(const uint8_t* img, long long pitch, const Geom& g, float4* lab,
+                           unsigned long long* counters, cudaStream_t s) {
+  (void)counters;
+  static const Rgb2LabConst k = make_rgb2lab_const();
+  const long long N = (long long)g.W * g.H;
+  k_rgb2lab<<<grid_for(N, 256), 256, 0, s>>>(img, pitch, g.W, g.H, lab, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float4* lab,
+                         unsigned long long* counters, cudaStream_t s) {
+  const long long N = (long long)g.W * g.H;
+  k_lab32<<<grid_for(N, 256), 256, 0, s>>>(img, pitch, g.W, g.H, lab, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_theta(const float4* lab, const Geom& g, double lambda_c, double* theta,
+                              float* gp, cudaStream_t s) {
+  k_init_theta<<<(g.K + 63) / 64, 64, 0, s>>>(lab, g, lambda_c, theta, gp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_theta(const Geom& g, double* theta, float* gp, int* bad, cudaStream_t s) {
+  k_pack_theta<<<(g.K + 63) / 64, 64, 0, s>>>(g, theta, gp, bad);
+  return cudaGetLastError();
+}
+
+}  // namespace gmmsp
