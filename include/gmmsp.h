@@ -174,17 +174,40 @@ gmmsp_status gmmsp_get_stats(gmmsp_ctx c, long long *dead, long long *raised_s, 
  * Kernel timing (no counterpart in the paper: a measurement aid).  Launches
  * one kernel of the pipeline `reps` times on the context's stream, each
  * launch between two CUDA events, and returns the mean launch time in
- * milliseconds (synchronises).  Only kernels that leave theta unchanged can
- * be repeated, so `which` is
+ * milliseconds (synchronises).  `which` is
  *   GMMSP_KERNEL_EM_PASS  (0)  the fused E-step + M-step partial pass on
  *                              the current theta (rewrites the partial sums);
- *   GMMSP_KERNEL_LABELS   (1)  the label pass (writes labels_dev).
+ *   GMMSP_KERNEL_LABELS   (1)  the label pass (writes labels_dev);
+ *   GMMSP_KERNEL_FINALIZE (2)  the FP64 M-step finalize on the current partial
+ *                              sums; theta is saved before the first launch
+ *                              and restored before each one (outside the
+ *                              timed interval), so the call leaves theta as
+ *                              it found it.  Allocates a K-sized scratch copy.
  * If flush_dev is non-NULL, flush_bytes of it are overwritten before every
  * launch (outside the timed interval) so each launch starts with a cold L2.
  */
-enum { GMMSP_KERNEL_EM_PASS = 0, GMMSP_KERNEL_LABELS = 1 };
+enum { GMMSP_KERNEL_EM_PASS = 0, GMMSP_KERNEL_LABELS = 1, GMMSP_KERNEL_FINALIZE = 2 };
 gmmsp_status gmmsp_profile_kernel(gmmsp_ctx c, int which, int reps, int32_t *labels_dev,
                                   void *flush_dev, unsigned long long flush_bytes, double *avg_ms);
+
+/*
+ * Launch shape of the fused E + M-partial pass (no counterpart in the paper):
+ * the number of warps that share one v x v cell, 1, 2 or 4.  More warps per
+ * cell give small images more parallelism; one warp per cell has the least
+ * reduction work for large images.  gmmsp_init picks a default from the
+ * cell count.  Changing it drops a captured gmmsp_segment graph.
+ */
+gmmsp_status gmmsp_set_launch(gmmsp_ctx c, int warps_per_cell);
+gmmsp_status gmmsp_get_launch(gmmsp_ctx c, int *warps_per_cell);
+
+/*
+ * Autotuner: times the E + M-partial pass on the current theta for each
+ * launch shape (1, 2, 4 warps per cell; `reps` timed launches each after
+ * one warm-up), keeps the fastest and returns it in *best (may be NULL);
+ * times_ms (NULL or 3 doubles) receives the mean time of each shape.
+ * Synchronises.
+ */
+gmmsp_status gmmsp_autotune(gmmsp_ctx c, int reps, int *best, double *times_ms);
 
 /* Text of the last error on c (never NULL; "" when there is none). */
 const char *gmmsp_last_error(gmmsp_ctx c);

@@ -24,7 +24,8 @@ __all__ = [
     "gmmsp_params", "load_library", "library_path", "Superpixels",
     "gmmsp_default_params", "gmmsp_init", "gmmsp_reinit", "gmmsp_em_iters", "gmmsp_labels",
     "gmmsp_segment", "gmmsp_get_lab", "gmmsp_get_grid", "gmmsp_get_params", "gmmsp_set_params", "gmmsp_get_stats",
-    "gmmsp_profile_kernel", "gmmsp_last_error", "gmmsp_status_string", "gmmsp_destroy",
+    "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_set_launch", "gmmsp_get_launch",
+    "gmmsp_autotune", "gmmsp_last_error", "gmmsp_status_string", "gmmsp_destroy",
 ]
 
 GMMSP_RGB8, GMMSP_LAB32 = 0, 1
@@ -82,6 +83,9 @@ def load_library(path: str | None = None):
             "gmmsp_set_params": (I, [P, P, P, P]),
             "gmmsp_get_stats": (I, [P, pll, pll, pll]),
             "gmmsp_profile_kernel": (I, [P, I, I, P, P, ctypes.c_ulonglong, ctypes.POINTER(D)]),
+            "gmmsp_set_launch": (I, [P, I]),
+            "gmmsp_get_launch": (I, [P, pint]),
+            "gmmsp_autotune": (I, [P, I, pint, P]),
             "gmmsp_last_error": (ctypes.c_char_p, [P]),
             "gmmsp_status_string": (ctypes.c_char_p, [I]),
             "gmmsp_destroy": (None, [P]),
@@ -197,7 +201,25 @@ def gmmsp_get_stats(ctx):
     return d.value, rs.value, rc.value
 
 
-GMMSP_KERNEL_EM_PASS, GMMSP_KERNEL_LABELS = 0, 1
+GMMSP_KERNEL_EM_PASS, GMMSP_KERNEL_LABELS, GMMSP_KERNEL_FINALIZE = 0, 1, 2
+
+
+def gmmsp_set_launch(ctx, warps_per_cell: int) -> None:
+    _check(ctx, load_library().gmmsp_set_launch(ctx, int(warps_per_cell)))
+
+
+def gmmsp_get_launch(ctx) -> int:
+    w = ctypes.c_int()
+    _check(ctx, load_library().gmmsp_get_launch(ctx, ctypes.byref(w)))
+    return w.value
+
+
+def gmmsp_autotune(ctx, reps: int = 5):
+    best = ctypes.c_int()
+    times = np.zeros(3)
+    _check(ctx, load_library().gmmsp_autotune(ctx, int(reps), ctypes.byref(best),
+                                              times.ctypes.data_as(ctypes.c_void_p)))
+    return best.value, dict(zip((1, 2, 4), times.tolist()))
 
 
 def gmmsp_profile_kernel(ctx, which: int, reps: int, labels=None, flush=None) -> float:
@@ -208,6 +230,27 @@ def gmmsp_profile_kernel(ctx, which: int, reps: int, labels=None, flush=None) ->
         ctx, int(which), int(reps), _dptr(labels) if labels is not None else None, fptr, fbytes,
         ctypes.byref(ms)))
     return ms.value
+
+
+class gmmsp_peaks(ctypes.Structure):
+    """Mirror of ``gmmsp_peaks`` (include/gmmsp_probe.h)."""
+    _fields_ = [("sm_count", ctypes.c_int), ("clock_mhz", ctypes.c_int),
+                ("fp32_fma_tflops", ctypes.c_double), ("fp64_fma_tflops", ctypes.c_double),
+                ("fp64_fma_tflops_lane1", ctypes.c_double), ("mufu_ex2_tops", ctypes.c_double),
+                ("fp32_fma_latency_clk", ctypes.c_double), ("fp64_fma_latency_clk", ctypes.c_double)]
+
+
+def gmmsp_probe_peaks() -> dict:
+    lib = load_library()
+    f = lib.gmmsp_probe_peaks
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.POINTER(gmmsp_peaks), ctypes.c_char_p, ctypes.c_int]
+    out = gmmsp_peaks()
+    err = ctypes.create_string_buffer(256)
+    st = f(ctypes.byref(out), err, 256)
+    if st != 0:
+        raise GmmspError(2, err.value.decode())
+    return {name: getattr(out, name) for name, _ in gmmsp_peaks._fields_}
 
 
 def gmmsp_last_error(ctx) -> str:
@@ -298,6 +341,15 @@ class Superpixels:
             labels_host.copy_(dev_labels, non_blocking=True)
         self.stream.synchronize()
         return ll
+
+    def set_launch(self, warps_per_cell: int) -> None:
+        gmmsp_set_launch(self.ctx, warps_per_cell)
+
+    def get_launch(self) -> int:
+        return gmmsp_get_launch(self.ctx)
+
+    def autotune(self, reps: int = 5):
+        return gmmsp_autotune(self.ctx, reps)
 
     def profile_kernel(self, which: int, reps: int = 20, labels=None, flush=None) -> float:
         return gmmsp_profile_kernel(self.ctx, which, reps, labels, flush)

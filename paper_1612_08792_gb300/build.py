@@ -37,7 +37,8 @@ def _sources():
 def _fingerprint() -> str:
     h = hashlib.sha256()
     files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
-        os.path.join(ROOT, "include", "gmmsp.h"), os.path.abspath(__file__)]
+        os.path.join(ROOT, "include", "gmmsp.h"), os.path.join(ROOT, "include", "gmmsp_probe.h"),
+        os.path.abspath(__file__)]
     for f in files:
         h.update(f.encode())
         with open(f, "rb") as fh:

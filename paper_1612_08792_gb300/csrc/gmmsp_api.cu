@@ -55,6 +55,7 @@ struct gmmsp_ctx_s {
   unsigned* ticket = nullptr;
   unsigned long long* counters = nullptr;
   int* bad = nullptr;
+  int wpc = 1;                    // warps per cell of the E+M pass (launch shape)
   gmmsp_status state = GMMSP_OK;  // sticky error
   std::string err;
   Graph graph;
@@ -113,6 +114,15 @@ bool make_geom(int W, int H, int K_req, int spacing, Geom* g) {
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Launch shape of the E+M pass before any autotuning: enough warps to give
+// every SM about 16 of them (152 SMs on GB300), at most 4 warps per cell.
+int default_wpc(const Geom& g) {
+  const long long target = 152LL * 16;
+  if ((long long)g.ncells >= target) return 1;
+  if ((long long)g.ncells * 2 >= target) return 2;
+  return 4;
+}
+
 bool inject_alloc_failure() {
   const char* s = getenv("GMMSP_FAIL_ALLOC");
   return s && s[0] == '1';
@@ -145,7 +155,8 @@ gmmsp_status enqueue_prepare(gmmsp_ctx c, const void* image, int pitch) {
 // Enqueues `iters` EM rounds; llk[t0 + t] receives L(theta_t).
 gmmsp_status enqueue_em(gmmsp_ctx c, int iters, int t0) {
   for (int t = 0; t < iters; ++t) {
-    GM_CHECK(c, gmmsp::launch_em_pass(c->lab, c->g, c->gp, c->partials, c->p.precision, c->stream));
+    GM_CHECK(c, gmmsp::launch_em_pass(c->lab, c->g, c->gp, c->partials, c->p.precision, c->wpc,
+                                      c->stream));
     double* llk_out = c->llk + ((t0 + t) % kLlkCap);
     GM_CHECK(c, gmmsp::launch_finalize(c->g, c->partials, c->theta, c->gp, c->p.eps_s, c->p.eps_c,
                                        llk_out, c->ws, c->ticket, c->counters, c->p.precision,
@@ -232,6 +243,7 @@ gmmsp_status gmmsp_init(gmmsp_ctx* out, const void* image_dev, int width, int he
   c->p = *p;
   c->stream = static_cast<cudaStream_t>(stream);
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return GMMSP_E_CUDA; }
+  c->wpc = default_wpc(g);
 
   const size_t N = size_t(width) * height;
   size_t off = 0;
@@ -458,20 +470,44 @@ gmmsp_status gmmsp_profile_kernel(gmmsp_ctx c, int which, int reps, int32_t* lab
                                   void* flush_dev, unsigned long long flush_bytes, double* avg_ms) {
   gmmsp_status st = check_ready(c);
   if (st != GMMSP_OK) return st;
-  if (reps < 1 || !avg_ms || (which != GMMSP_KERNEL_EM_PASS && which != GMMSP_KERNEL_LABELS) ||
+  if (reps < 1 || !avg_ms ||
+      (which != GMMSP_KERNEL_EM_PASS && which != GMMSP_KERNEL_LABELS && which != GMMSP_KERNEL_FINALIZE) ||
       (which == GMMSP_KERNEL_LABELS && !labels_dev))
     return fail(c, GMMSP_E_INVALID, "bad profile arguments");
+  const size_t th_bytes = size_t(c->g.K) * gmmsp::kTheta * sizeof(double);
+  const size_t gp_bytes = size_t(c->g.K) * gmmsp::kGP * sizeof(float);
+  void* save = nullptr;
+  if (which == GMMSP_KERNEL_FINALIZE) {
+    // The finalize rewrites theta from the partial sums; keep a copy of theta
+    // and the packed coefficients and put them back before every launch.
+    GM_CHECK(c, cudaMalloc(&save, th_bytes + gp_bytes));
+    GM_CHECK(c, cudaMemcpyAsync(save, c->theta, th_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    GM_CHECK(c, cudaMemcpyAsync(static_cast<char*>(save) + th_bytes, c->gp, gp_bytes,
+                                cudaMemcpyDeviceToDevice, c->stream));
+  }
   std::vector<cudaEvent_t> ev(2 * size_t(reps), nullptr);
-  for (auto& e : ev) GM_CHECK(c, cudaEventCreate(&e));
   gmmsp_status out = GMMSP_OK;
+  for (auto& e : ev)
+    if (out == GMMSP_OK && cudaEventCreate(&e) != cudaSuccess) out = fail(c, GMMSP_E_CUDA, "cudaEventCreate");
   for (int r = 0; r < reps && out == GMMSP_OK; ++r) {
     cudaError_t e = cudaSuccess;
-    if (flush_dev && flush_bytes) e = cudaMemsetAsync(flush_dev, r & 0xff, flush_bytes, c->stream);
+    if (save) {
+      e = cudaMemcpyAsync(c->theta, save, th_bytes, cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->gp, static_cast<char*>(save) + th_bytes, gp_bytes, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    }
+    if (e == cudaSuccess && flush_dev && flush_bytes) e = cudaMemsetAsync(flush_dev, r & 0xff, flush_bytes, c->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r], c->stream);
-    if (e == cudaSuccess)
-      e = (which == GMMSP_KERNEL_EM_PASS)
-              ? gmmsp::launch_em_pass(c->lab, c->g, c->gp, c->partials, c->p.precision, c->stream)
-              : gmmsp::launch_label_pass(c->lab, c->g, c->gp, labels_dev, c->cell_ll, c->stream);
+    if (e == cudaSuccess) {
+      if (which == GMMSP_KERNEL_EM_PASS)
+        e = gmmsp::launch_em_pass(c->lab, c->g, c->gp, c->partials, c->p.precision, c->wpc, c->stream);
+      else if (which == GMMSP_KERNEL_LABELS)
+        e = gmmsp::launch_label_pass(c->lab, c->g, c->gp, labels_dev, c->cell_ll, c->stream);
+      else
+        e = gmmsp::launch_finalize(c->g, c->partials, c->theta, c->gp, c->p.eps_s, c->p.eps_c, c->llk,
+                                   c->ws, c->ticket, c->counters, c->p.precision, c->stream);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r + 1], c->stream);
     if (e != cudaSuccess) out = cuda_fail(c, e, "profile launch");
   }
@@ -486,9 +522,50 @@ gmmsp_status gmmsp_profile_kernel(gmmsp_ctx c, int which, int reps, int32_t* lab
     if (e != cudaSuccess) out = cuda_fail(c, e, "profile timing");
     else *avg_ms = sum / reps;
   }
+  if (save) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(save);
+  }
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
   return out;
+}
+
+gmmsp_status gmmsp_set_launch(gmmsp_ctx c, int warps_per_cell) {
+  if (!c) return GMMSP_E_INVALID;
+  if (warps_per_cell != 1 && warps_per_cell != 2 && warps_per_cell != 4)
+    return fail(c, GMMSP_E_INVALID, "warps_per_cell must be 1, 2 or 4");
+  if (warps_per_cell != c->wpc) free_graph(c);
+  c->wpc = warps_per_cell;
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_get_launch(gmmsp_ctx c, int* warps_per_cell) {
+  if (!c || !warps_per_cell) return GMMSP_E_INVALID;
+  *warps_per_cell = c->wpc;
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_autotune(gmmsp_ctx c, int reps, int* best, double* times_ms) {
+  gmmsp_status st = check_ready(c);
+  if (st != GMMSP_OK) return st;
+  if (reps < 1) return fail(c, GMMSP_E_INVALID, "reps < 1");
+  const int cand[3] = {1, 2, 4};
+  const int keep = c->wpc;
+  double best_ms = 1e30;
+  int best_w = keep;
+  for (int i = 0; i < 3; ++i) {
+    c->wpc = cand[i];
+    double ms = 0.0;
+    st = gmmsp_profile_kernel(c, GMMSP_KERNEL_EM_PASS, reps + 1, nullptr, nullptr, 0, &ms);
+    if (st != GMMSP_OK) { c->wpc = keep; return st; }
+    if (times_ms) times_ms[i] = ms;
+    if (ms < best_ms) { best_ms = ms; best_w = cand[i]; }
+  }
+  c->wpc = keep;
+  st = gmmsp_set_launch(c, best_w);
+  if (best) *best = best_w;
+  return st;
 }
 
 void gmmsp_destroy(gmmsp_ctx c) {

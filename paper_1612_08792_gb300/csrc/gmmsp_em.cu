@@ -33,8 +33,6 @@ namespace gmmsp {
 
 constexpr int kEmWarps = 4;          // cells per 128-thread block
 constexpr int kRedRows = 68;         // rows of the reduction buffer (2 halves of 136)
-constexpr int kRedLd = 33;           // padded row length (conflict-free transposes)
-constexpr int kEmSmemPerWarp = kSlots * 4 * 16 + kRedRows * kRedLd * 4;
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -95,6 +93,7 @@ __device__ __forceinline__ void stage_params(const Geom& g, const Cell& c, const
 
 // log2 p(z; theta_k) for one candidate: the log normaliser plus the two
 // quadratic forms, with -1/2 log2(e) Sigma^{-1} folded into the coefficients.
+// fx, fy are the pixel's coordinates relative to the candidate's cell origin.
 __device__ __forceinline__ float log2_density(const float4* P, float fx, float fy, float4 z) {
   const float4 p0 = P[0], p1 = P[1], p2 = P[2], p3 = P[3];
   const float dx = fx - p0.x, dy = fy - p0.y;
@@ -108,17 +107,20 @@ __device__ __forceinline__ float log2_density(const float4* P, float fx, float f
   return q;
 }
 
-// One pixel of the fused E + M-partial pass.
+// One pixel of the fused E + M-partial pass.  fxs[j] / fys[j] are the
+// pixel's coordinates relative to the origin of the candidate cells of
+// column / row j (exact small integers), see rel_coords().
 template <bool FULL, bool SHIFT>
-__device__ __forceinline__ void em_pixel(const float4* sp, unsigned mask, float fx, float fy,
-                                         float4 z, float (&acc)[kSlots * kStats], float& ll) {
+__device__ __forceinline__ void em_pixel(const float4* sp, unsigned mask, const float (&fxs)[3],
+                                         const float (&fys)[3], float4 z,
+                                         float (&acc)[kSlots * kStats], float& ll) {
   float e[kSlots];
   float m = -INFINITY;
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     e[s] = 0.f;
     if (FULL || ((mask >> s) & 1u)) {
-      e[s] = log2_density(sp + 4 * s, fx, fy, z);
+      e[s] = log2_density(sp + 4 * s, fxs[s % 3], fys[s / 3], z);
       m = fmaxf(m, e[s]);
     }
   }
@@ -136,7 +138,7 @@ __device__ __forceinline__ void em_pixel(const float4* sp, unsigned mask, float 
   for (int s = 0; s < kSlots; ++s) {
     if (FULL || ((mask >> s) & 1u)) {
       const float r = e[s] * inv;
-      float dx = fx, dy = fy, dL = z.x, da = z.y, db = z.z;
+      float dx = fxs[s % 3], dy = fys[s / 3], dL = z.x, da = z.y, db = z.z;
       if (SHIFT) {
         const float4 p0 = sp[4 * s], p1 = sp[4 * s + 1];
         dx -= p0.x; dy -= p0.y; dL -= p0.z; da -= p0.w; db -= p1.x;
@@ -158,67 +160,121 @@ __device__ __forceinline__ void em_pixel(const float4* sp, unsigned mask, float 
   }
 }
 
-template <bool FULL, bool SHIFT>
+// Coordinates of pixel (rx, ry) of a cell relative to the cell origins of
+// the candidate columns/rows cx-1, cx, cx+1: rx + v, rx, rx - v.
+__device__ __forceinline__ void rel_coords(int rx, int ry, int v, float (&fxs)[3], float (&fys)[3]) {
+  fxs[0] = float(rx + v); fxs[1] = float(rx); fxs[2] = float(rx - v);
+  fys[0] = float(ry + v); fys[1] = float(ry); fys[2] = float(ry - v);
+}
+
+template <bool FULL, bool SHIFT, int LANES>
 __device__ __forceinline__ void em_cell_pixels(const float4* __restrict__ lab, const Geom& g,
-                                               const Cell& c, const float4* sp, int lane,
+                                               const Cell& c, const float4* sp, int t,
                                                float (&acc)[kSlots * kStats], float& ll) {
   const int npx = c.cw * c.ch;
   const float inv_cw = 1.f / float(c.cw);
-  for (int p = lane; p < npx; p += 32) {
-    // row = floor(p / cw): exact, since (p + 1/2) / cw is at least 1/(2 cw) away from an integer
-    const int ry = __float2int_rz((float(p) + 0.5f) * inv_cw);
-    const int rx = p - ry * c.cw;
-    const int x = c.x0 + rx, y = c.y0 + ry;
-    const float4 z = __ldg(lab + (long long)y * g.W + x);
-    em_pixel<FULL, SHIFT>(sp, c.mask, float(x), float(y), z, acc, ll);
+  // Pixel p of the cell: row floor(p / cw) (exact: (p + 1/2) / cw is at least
+  // 1/(2 cw) away from an integer), column p - row * cw.  The next pixel's
+  // colour is loaded before the current one is processed.
+  auto locate = [&](int p, int& rx, int& ry) {
+    ry = __float2int_rz((float(p) + 0.5f) * inv_cw);
+    rx = p - ry * c.cw;
+  };
+  int p = t, rx = 0, ry = 0;
+  float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (p < npx) {
+    locate(p, rx, ry);
+    z = __ldg(lab + (long long)(c.y0 + ry) * g.W + (c.x0 + rx));
+  }
+  while (p < npx) {
+    const int pn = p + LANES;
+    int rxn = 0, ryn = 0;
+    float4 zn = z;
+    if (pn < npx) {
+      locate(pn, rxn, ryn);
+      zn = __ldg(lab + (long long)(c.y0 + ryn) * g.W + (c.x0 + rxn));
+    }
+    float fxs[3], fys[3];
+    rel_coords(rx, ry, g.v, fxs, fys);
+    em_pixel<FULL, SHIFT>(sp, c.mask, fxs, fys, z, acc, ll);
+    p = pn; rx = rxn; ry = ryn; z = zn;
   }
 }
 
 // Fused E-step + M-step partial sums.  PT = double (mixed precision, shifted
-// moments) or float (all-FP32 variant, raw moments).
-template <typename PT, bool SHIFT>
+// moments) or float (all-FP32 variant, raw moments).  WPC warps share one
+// cell (more parallelism for small images); a 128-thread block holds
+// 4 / WPC cells.  The WPC x 32 per-thread accumulator sets of a cell are
+// summed through shared memory: every thread writes its column of a
+// 68-row tile (two tiles for the 136 sums), then each thread adds up whole rows.
+template <typename PT, bool SHIFT, int WPC>
 __global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(const float4* __restrict__ lab, Geom g,
                                                            const float* __restrict__ gp,
                                                            PT* __restrict__ partials) {
+  constexpr int kLanes = 32 * WPC;             // threads per cell
+  constexpr int kCellsPerBlock = kEmWarps / WPC;
+  constexpr int kLd = kLanes + 1;              // padded row: conflict-free transposes
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* base = smem_raw + warp * kEmSmemPerWarp;
-  float4* sp = reinterpret_cast<float4*>(base);
-  float* red = reinterpret_cast<float*>(base + kSlots * 4 * 16);
-  const int cell = blockIdx.x * kEmWarps + warp;
-  if (cell >= g.ncells) return;  // whole warp; no block-wide barrier follows
-  const Cell c = make_cell(g, cell);
-  stage_params(g, c, gp, sp, lane);
+  const int slot = warp / WPC;                 // cell slot within the block
+  const int t = (warp % WPC) * 32 + lane;      // thread index within the cell
+  float4* sp = reinterpret_cast<float4*>(smem_raw) + slot * (kSlots * 4);
+  float* red = reinterpret_cast<float*>(smem_raw + kCellsPerBlock * kSlots * 4 * 16) +
+               slot * (kRedRows * kLd);
+  const int cell = blockIdx.x * kCellsPerBlock + slot;
+  const bool active = cell < g.ncells;         // inactive threads still reach every barrier
+  Cell c = {};
+  if (active) {
+    c = make_cell(g, cell);
+    for (int i = t; i < kSlots * 4; i += kLanes) {
+      const int s = i >> 2, q = i & 3;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if ((c.mask >> s) & 1u) {
+        const int k = (c.cy - 1 + s / 3) * g.nx + (c.cx - 1 + s % 3);
+        v = __ldg(reinterpret_cast<const float4*>(gp) + k * 4 + q);
+      }
+      sp[i] = v;
+    }
+  }
+  if (WPC == 1) __syncwarp(); else __syncthreads();
 
   float acc[kSlots * kStats];
 #pragma unroll
   for (int j = 0; j < kSlots * kStats; ++j) acc[j] = 0.f;
   float ll = 0.f;
-  if (c.mask == 0x1ffu)
-    em_cell_pixels<true, SHIFT>(lab, g, c, sp, lane, acc, ll);
-  else
-    em_cell_pixels<false, SHIFT>(lab, g, c, sp, lane, acc, ll);
+  if (active) {
+    if (c.mask == 0x1ffu)
+      em_cell_pixels<true, SHIFT, kLanes>(lab, g, c, sp, t, acc, ll);
+    else
+      em_cell_pixels<false, SHIFT, kLanes>(lab, g, c, sp, t, acc, ll);
+  }
 
-  // Cross-lane sums: lane l writes column l of a rows x 32 tile, then each
-  // lane adds up whole rows.  Row 135 carries the log-likelihood (log2 units).
+  // Row 135 carries the log-likelihood (log2 units until written).
   PT* out = partials + (long long)cell * kPartStride;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
 #pragma unroll
     for (int j = 0; j < kRedRows; ++j) {
       const int row = h * kRedRows + j;
-      red[j * kRedLd + lane] = (row < kSlots * kStats) ? acc[row] : ll;
+      red[j * kLd + t] = (row < kSlots * kStats) ? acc[row] : ll;
     }
-    __syncwarp();
-    for (int j = lane; j < kRedRows; j += 32) {
-      float s = 0.f;
+    if (WPC == 1) __syncwarp(); else __syncthreads();
+    if (active) {
+      for (int j = t; j < kRedRows; j += kLanes) {
+        float s = 0.f;
 #pragma unroll 8
-      for (int q = 0; q < 32; ++q) s += red[j * kRedLd + q];
-      const int row = h * kRedRows + j;
-      out[row] = (row < kSlots * kStats) ? PT(s) : PT(s) * PT(0.69314718055994530942);
+        for (int q = 0; q < kLanes; ++q) s += red[j * kLd + q];
+        const int row = h * kRedRows + j;
+        out[row] = (row < kSlots * kStats) ? PT(s) : PT(s) * PT(0.69314718055994530942);
+      }
     }
-    __syncwarp();
+    if (WPC == 1) __syncwarp(); else __syncthreads();
   }
+}
+
+template <int WPC>
+constexpr int em_smem_bytes() {
+  return (kEmWarps / WPC) * (kSlots * 4 * 16 + kRedRows * (32 * WPC + 1) * 4);
 }
 
 // Label pass: argmax posterior per pixel (ties to the smaller k, i.e. the
@@ -234,7 +290,8 @@ __device__ __forceinline__ void label_cell_pixels(const float4* __restrict__ lab
     const int rx = p - ry * c.cw;
     const int x = c.x0 + rx, y = c.y0 + ry;
     const float4 z = __ldg(lab + (long long)y * g.W + x);
-    const float fx = float(x), fy = float(y);
+    float fxs[3], fys[3];
+    rel_coords(rx, ry, g.v, fxs, fys);
     float e[kSlots];
     float m = -INFINITY;
     int best = 0;
@@ -242,7 +299,7 @@ __device__ __forceinline__ void label_cell_pixels(const float4* __restrict__ lab
     for (int s = 0; s < kSlots; ++s) {
       e[s] = 0.f;
       if (FULL || ((c.mask >> s) & 1u)) {
-        e[s] = log2_density(sp + 4 * s, fx, fy, z);
+        e[s] = log2_density(sp + 4 * s, fxs[s % 3], fys[s / 3], z);
         if (e[s] > m) { m = e[s]; best = s; }
       }
     }
@@ -277,7 +334,7 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass(const float4* __re
 }
 
 // ---------------------------------------------------------------- finalize
-constexpr int kFinThreads = 64;
+constexpr int kFinThreads = 32;  // one warp per block: spreads small K over more SMs
 
 // Deterministic sum of the per-cell log-likelihoods: each block adds a fixed
 // strided subset and a tree, the last block to finish adds the block sums in
@@ -348,35 +405,34 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Geom g, const PT* __re
       dead = 1;  // reading: a superpixel with no weight keeps theta_k
     } else {
       float* G = gp + (long long)k * kGP;
-      const T iw = T(1) / Wk;
+      const T iw = Num<T>::rcp(Wk);
       T mu[5], cs[3], cc[6];
+      const T ox = T(kx * g.v), oy = T(ky * g.v);  // origin of k's cell
+      // Moments about r: Sigma = S2 / W - d d^T with d = S1 / W.  The shifted
+      // path has r = mu_ref, the FP32 mean the E-step subtracted (spatial part
+      // relative to the cell origin); the raw path has r = 0.
+      T dl[5];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) dl[j] = S[ST_S1 + j] * iw;
+      cs[0] = fma(-dl[0], dl[0], S[ST_S2S + 0] * iw);
+      cs[1] = fma(-dl[0], dl[1], S[ST_S2S + 1] * iw);
+      cs[2] = fma(-dl[1], dl[1], S[ST_S2S + 2] * iw);
+      cc[0] = fma(-dl[2], dl[2], S[ST_S2C + 0] * iw);
+      cc[1] = fma(-dl[2], dl[3], S[ST_S2C + 1] * iw);
+      cc[2] = fma(-dl[2], dl[4], S[ST_S2C + 2] * iw);
+      cc[3] = fma(-dl[3], dl[3], S[ST_S2C + 3] * iw);
+      cc[4] = fma(-dl[3], dl[4], S[ST_S2C + 4] * iw);
+      cc[5] = fma(-dl[4], dl[4], S[ST_S2C + 5] * iw);
       if (kShifted) {
-        // d = z - mu_ref with mu_ref the FP32 mean the E-step used.
-        T dl[5];
+        mu[0] = ox + (T(G[0]) + dl[0]);
+        mu[1] = oy + (T(G[1]) + dl[1]);
 #pragma unroll
-        for (int j = 0; j < 5; ++j) { dl[j] = S[ST_S1 + j] * iw; mu[j] = T(G[j]) + dl[j]; }
-        cs[0] = S[ST_S2S + 0] * iw - dl[0] * dl[0];
-        cs[1] = S[ST_S2S + 1] * iw - dl[0] * dl[1];
-        cs[2] = S[ST_S2S + 2] * iw - dl[1] * dl[1];
-        cc[0] = S[ST_S2C + 0] * iw - dl[2] * dl[2];
-        cc[1] = S[ST_S2C + 1] * iw - dl[2] * dl[3];
-        cc[2] = S[ST_S2C + 2] * iw - dl[2] * dl[4];
-        cc[3] = S[ST_S2C + 3] * iw - dl[3] * dl[3];
-        cc[4] = S[ST_S2C + 4] * iw - dl[3] * dl[4];
-        cc[5] = S[ST_S2C + 5] * iw - dl[4] * dl[4];
+        for (int j = 2; j < 5; ++j) mu[j] = T(G[j]) + dl[j];
       } else {
-        // raw moments: mu = S1 / W, Sigma = S2 / W - mu mu^T
+        mu[0] = ox + dl[0];
+        mu[1] = oy + dl[1];
 #pragma unroll
-        for (int j = 0; j < 5; ++j) mu[j] = S[ST_S1 + j] * iw;
-        cs[0] = S[ST_S2S + 0] * iw - mu[0] * mu[0];
-        cs[1] = S[ST_S2S + 1] * iw - mu[0] * mu[1];
-        cs[2] = S[ST_S2S + 2] * iw - mu[1] * mu[1];
-        cc[0] = S[ST_S2C + 0] * iw - mu[2] * mu[2];
-        cc[1] = S[ST_S2C + 1] * iw - mu[2] * mu[3];
-        cc[2] = S[ST_S2C + 2] * iw - mu[2] * mu[4];
-        cc[3] = S[ST_S2C + 3] * iw - mu[3] * mu[3];
-        cc[4] = S[ST_S2C + 4] * iw - mu[3] * mu[4];
-        cc[5] = S[ST_S2C + 5] * iw - mu[4] * mu[4];
+        for (int j = 2; j < 5; ++j) mu[j] = dl[j];
       }
       rs = clamp_sym2<T>(cs, T(eps_s));
       rc = clamp_sym3<T>(cc, T(eps_c));
@@ -387,7 +443,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Geom g, const PT* __re
       for (int j = 0; j < 3; ++j) th[5 + j] = double(cs[j]);
 #pragma unroll
       for (int j = 0; j < 6; ++j) th[8 + j] = double(cc[j]);
-      pack_gp<T>(mu, cs, cc, G);
+      pack_gp<T>(mu, cs, cc, ox, oy, G);
     }
   }
   dead = __reduce_add_sync(0xffffffffu, dead);
@@ -410,19 +466,38 @@ static int ll_blocks(const Geom& g) { return (g.K + kFinThreads - 1) / kFinThrea
 
 size_t finalize_workspace_doubles(const Geom& g) { return size_t(ll_blocks(g)) + 1; }
 
-template <typename PT, bool SHIFT>
+template <typename PT, bool SHIFT, int WPC>
 static cudaError_t em_pass_impl(const float4* lab, const Geom& g, const float* gp, PT* partials,
                                 cudaStream_t s) {
-  const int smem = kEmWarps * kEmSmemPerWarp;
-  const int blocks = (g.ncells + kEmWarps - 1) / kEmWarps;
-  k_em_pass<PT, SHIFT><<<blocks, kEmWarps * 32, smem, s>>>(lab, g, gp, partials);
+  constexpr int smem = em_smem_bytes<WPC>();
+  static_assert(smem <= 227 * 1024, "shared memory");
+  static bool attr_set = false;  // per process; the attribute is per function
+  if (!attr_set && smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_em_pass<PT, SHIFT, WPC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  constexpr int cpb = kEmWarps / WPC;
+  const int blocks = (g.ncells + cpb - 1) / cpb;
+  k_em_pass<PT, SHIFT, WPC><<<blocks, kEmWarps * 32, smem, s>>>(lab, g, gp, partials);
   return cudaGetLastError();
 }
 
+template <typename PT, bool SHIFT>
+static cudaError_t em_pass_wpc(const float4* lab, const Geom& g, const float* gp, PT* partials,
+                               int wpc, cudaStream_t s) {
+  switch (wpc) {
+    case 2: return em_pass_impl<PT, SHIFT, 2>(lab, g, gp, partials, s);
+    case 4: return em_pass_impl<PT, SHIFT, 4>(lab, g, gp, partials, s);
+    default: return em_pass_impl<PT, SHIFT, 1>(lab, g, gp, partials, s);
+  }
+}
+
 cudaError_t launch_em_pass(const float4* lab, const Geom& g, const float* gp, void* partials,
-                           int precision, cudaStream_t s) {
-  if (precision == 1) return em_pass_impl<float, false>(lab, g, gp, static_cast<float*>(partials), s);
-  return em_pass_impl<double, true>(lab, g, gp, static_cast<double*>(partials), s);
+                           int precision, int wpc, cudaStream_t s) {
+  if (precision == 1) return em_pass_wpc<float, false>(lab, g, gp, static_cast<float*>(partials), wpc, s);
+  return em_pass_wpc<double, true>(lab, g, gp, static_cast<double*>(partials), wpc, s);
 }
 
 cudaError_t launch_label_pass(const float4* lab, const Geom& g, const float* gp, int32_t* labels,

@@ -29,7 +29,8 @@ constexpr int kTheta = 16;         // doubles of master parameters per superpixe
 enum : int { ST_W = 0, ST_S1 = 1, ST_S2S = 6, ST_S2C = 9 };
 
 // Packed FP32 E-step parameters of superpixel k (64 bytes, 16-byte aligned):
-//   [0..4]   mu (x, y, L, a, b)
+//   [0..4]   mu (x - k_x v, y - k_y v, L, a, b): the spatial mean relative
+//            to the first pixel of the superpixel's own cell
 //   [5..7]   spatial quadratic form coefficients (xx, 2xy, yy) of
 //            -(1/2) log2(e) Sigma_s^{-1}
 //   [8..13]  colour coefficients (LL, aa, bb, 2La, 2Lb, 2ab) of
@@ -60,8 +61,9 @@ cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float
                          unsigned long long* counters, cudaStream_t s);
 cudaError_t launch_init_theta(const float4* lab, const Geom& g, double lambda_c, double* theta,
                               float* gp, cudaStream_t s);
+// wpc: warps per cell (1, 2 or 4).
 cudaError_t launch_em_pass(const float4* lab, const Geom& g, const float* gp, void* partials,
-                           int precision, cudaStream_t s);
+                           int precision, int wpc, cudaStream_t s);
 cudaError_t launch_label_pass(const float4* lab, const Geom& g, const float* gp, int32_t* labels,
                               double* cell_ll, cudaStream_t s);
 // Finalize: ws holds finalize_workspace_doubles(g) doubles, ticket one zeroed

@@ -2,6 +2,12 @@
 // scalar type: double for the mixed-precision path, float for the all-FP32
 // variant.
 //
+// GB300 runs FP64 at about 1/64 of the FP32 rate and a dependent FP64
+// multiply-add takes about 64 clocks, so the FP64 code below avoids FP64
+// division, square root and transcendental functions: reciprocals and
+// eigenvalues start from an FP32 estimate and are refined by FP64 Newton
+// steps, which gives FP64-accurate results with short dependency chains.
+//
 //  * clamp_sym2 / clamp_sym3: the eigenvalue floor of Eq. (mlams)/(mlamc)
 //    followed by the reconstruction of Eq. (eigdecrs)/(eigdecrc).  Writing the
 //    covariance as sum_j lambda_j P_j with P_j its spectral projectors, the
@@ -9,11 +15,13 @@
 //    most one projector is needed: with one raised eigenvalue it is P_1, with
 //    two it is I - P_3 (the floored matrix is then eps I + (lambda_3 - eps) P_3),
 //    and each projector is a polynomial in Sigma (Lagrange form over the
-//    eigenvalues), so no eigenvectors are formed.  The 2x2 eigenvalues are in
-//    closed form; the 3x3 ones use the trigonometric solution of the
-//    characteristic cubic (O. K. Smith, "Eigenvalues of a symmetric 3x3
-//    matrix", Comm. ACM 4(4), 1961).  A pivot test of Sigma - eps I (its
-//    LDL^T inertia) skips the eigenvalues when none is below the floor.
+//    eigenvalues), so no eigenvectors are formed.  Whether any eigenvalue is
+//    below the floor is decided first from the leading principal minors of
+//    Sigma - eps I (Sylvester's criterion), which needs no eigenvalues.  The
+//    2x2 eigenvalues are in closed form; the 3x3 ones start from the
+//    trigonometric solution of the characteristic cubic (O. K. Smith,
+//    "Eigenvalues of a symmetric 3x3 matrix", Comm. ACM 4(4), 1961) and are
+//    polished by Newton steps on the cubic.
 //  * pack_gp: inverse and log-determinant of the floored blocks (adjugate
 //    formula) folded into the packed FP32 E-step coefficients.
 #pragma once
@@ -24,35 +32,55 @@
 
 namespace gmmsp {
 
-template <typename T> struct MathConst;
-template <> struct MathConst<double> {
+template <typename T> struct Num;
+
+template <> struct Num<double> {
   static constexpr double kLog2e = 1.4426950408889634074;
-  static constexpr double kHalfD_Ln2Pi = 4.5946926660233541;  // (5/2) ln(2 pi)
-  static constexpr double kTwoPiOver3 = 2.0943951023931954923;
-  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-  static __device__ __forceinline__ double acos_(double x) { return acos(x); }
-  static __device__ __forceinline__ double cos_(double x) { return cos(x); }
-  static __device__ __forceinline__ double log_(double x) { return log(x); }
+  static constexpr double kHalfD_Log2_2Pi = 6.6287403236807968;  // (5/2) log2(2 pi)
+  // 1/x: FP32 estimate, two Newton steps (relative error ~2^-46 -> ~2^-92).
+  static __device__ __forceinline__ double rcp(double x) {
+    double r = double(__frcp_rn(float(x)));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+  }
+  // sqrt(x), x > 0: FP32 estimate of 1/sqrt, two Newton steps, then x * rsqrt.
+  static __device__ __forceinline__ double sqrt_(double x) {
+    double y = double(rsqrtf(float(x)));
+    const double hx = 0.5 * x;
+    y = y * fma(-hx * y, y, 1.5);
+    y = y * fma(-hx * y, y, 1.5);
+    return x * y;
+  }
+  // log2(x), x > 0, to FP32 accuracy (the result is stored as FP32).
+  static __device__ __forceinline__ float log2_(double x) {
+    int e;
+    const double m = frexp(x, &e);  // x = m 2^e, m in [0.5, 1)
+    return float(e) + __log2f(float(m));
+  }
 };
-template <> struct MathConst<float> {
+
+template <> struct Num<float> {
   static constexpr float kLog2e = 1.44269504f;
-  static constexpr float kHalfD_Ln2Pi = 4.59469267f;
-  static constexpr float kTwoPiOver3 = 2.09439510f;
+  static constexpr float kHalfD_Log2_2Pi = 6.62874032f;
+  static __device__ __forceinline__ float rcp(float x) { return 1.0f / x; }
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-  static __device__ __forceinline__ float acos_(float x) { return acosf(x); }
-  static __device__ __forceinline__ float cos_(float x) { return cosf(x); }
-  static __device__ __forceinline__ float log_(float x) { return logf(x); }
+  static __device__ __forceinline__ float log2_(float x) { return log2f(x); }
 };
 
 // Floor the eigenvalues of the symmetric 2x2 A = {xx, xy, yy} at eps.
 // Returns the number of raised eigenvalues.
 template <typename T>
 __device__ int clamp_sym2(T* A, T eps) {
-  using M = MathConst<T>;
+  using M = Num<T>;
   const T a = A[0], b = A[1], c = A[2];
+  // Sylvester on A - eps I: both eigenvalues >= eps when both minors are > 0.
+  if (a - eps > T(0) && fma(a - eps, c - eps, -b * b) > T(0)) return 0;
   const T m = T(0.5) * (a + c), h = T(0.5) * (a - c);
-  const T r = M::sqrt_(h * h + b * b);
-  const T l1 = m - r, l2 = m + r;           // l1 <= l2
+  const T r2 = fma(h, h, b * b);
+  const T r = r2 > T(0) ? M::sqrt_(r2) : T(0);
+  const T l1 = m - r, l2 = m + r;  // l1 <= l2
   const int n = (l1 < eps) + (l2 < eps);
   if (n == 0) return 0;
   if (n == 2 || r <= T(1e-12) * (fabs(m) + eps)) {
@@ -61,111 +89,133 @@ __device__ int clamp_sym2(T* A, T eps) {
     return n;
   }
   // One raised: A + (eps - l1) P_1 with P_1 = (l2 I - A) / (l2 - l1).
-  const T g = (eps - l1) / (T(2) * r);
-  A[0] = a + g * (l2 - a);
-  A[1] = b - g * b;
-  A[2] = c + g * (l2 - c);
+  const T g = (eps - l1) * M::rcp(T(2) * r);
+  A[0] = fma(g, l2 - a, a);
+  A[1] = fma(-g, b, b);
+  A[2] = fma(g, l2 - c, c);
   return 1;
+}
+
+// Eigenvalues of a symmetric 3x3 in FP32 (Smith 1961), ascending.
+__device__ __forceinline__ void eig3_seed(float a00, float a01, float a02, float a11, float a12,
+                                          float a22, float& l1, float& l2, float& l3) {
+  const float q = (a00 + a11 + a22) * (1.f / 3.f);
+  const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+  const float p2 = (b00 * b00 + b11 * b11 + b22 * b22 +
+                    2.f * (a01 * a01 + a02 * a02 + a12 * a12)) * (1.f / 6.f);
+  if (!(p2 > 0.f)) { l1 = l2 = l3 = q; return; }
+  const float p = sqrtf(p2);
+  const float detB = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) +
+                     a02 * (a01 * a12 - b11 * a02);
+  float hr = detB / (2.f * p2 * p);
+  hr = fminf(1.f, fmaxf(-1.f, hr));
+  const float phi = acosf(hr) * (1.f / 3.f);
+  l3 = q + 2.f * p * cosf(phi);
+  l1 = q + 2.f * p * cosf(phi + 2.09439510f);
+  l2 = 3.f * q - l1 - l3;
 }
 
 // Floor the eigenvalues of the symmetric 3x3 A = {LL, La, Lb, aa, ab, bb}.
 template <typename T>
 __device__ int clamp_sym3(T* A, T eps) {
-  using M = MathConst<T>;
+  using M = Num<T>;
   const T a00 = A[0], a01 = A[1], a02 = A[2], a11 = A[3], a12 = A[4], a22 = A[5];
-  // Inertia of A - eps I from the pivots of its LDL^T factorisation: all
-  // positive means every eigenvalue is above the floor.
+  // Sylvester's criterion on A - eps I: all leading minors > 0 <=> every
+  // eigenvalue of A is above the floor.
   {
-    const T d1 = a00 - eps;
-    if (d1 > T(0)) {
-      const T l10 = a01 / d1, l20 = a02 / d1;
-      const T d2 = (a11 - eps) - l10 * a01;
-      if (d2 > T(0)) {
-        const T e21 = a12 - l20 * a01;
-        const T d3 = (a22 - eps) - l20 * a02 - e21 * e21 / d2;
-        if (d3 > T(0)) return 0;
-      }
-    }
+    const T e00 = a00 - eps, e11 = a11 - eps, e22 = a22 - eps;
+    const T m2 = fma(e00, e11, -a01 * a01);
+    const T c00 = fma(e11, e22, -a12 * a12);
+    const T c01 = fma(a02, a12, -a01 * e22);
+    const T c02 = fma(a01, a12, -a02 * e11);
+    const T m3 = fma(e00, c00, fma(a01, c01, a02 * c02));
+    if (e00 > T(0) && m2 > T(0) && m3 > T(0)) return 0;
   }
-  // Eigenvalues (Smith 1961): B = (A - q I) / p, lambda = q + 2 p cos(phi + 2 pi j / 3).
-  const T q = (a00 + a11 + a22) / T(3);
-  const T b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
-  const T off = a01 * a01 + a02 * a02 + a12 * a12;
-  const T p2 = (b00 * b00 + b11 * b11 + b22 * b22 + T(2) * off) / T(6);
-  T l1, l2, l3;  // ascending
-  if (p2 <= T(0)) {
-    l1 = l2 = l3 = q;
-  } else {
-    const T p = M::sqrt_(p2);
-    const T detB = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) +
-                   a02 * (a01 * a12 - b11 * a02);
-    T hr = detB / (T(2) * p2 * p);
-    hr = hr < T(-1) ? T(-1) : (hr > T(1) ? T(1) : hr);
-    const T phi = M::acos_(hr) / T(3);
-    l3 = q + T(2) * p * M::cos_(phi);
-    l1 = q + T(2) * p * M::cos_(phi + M::kTwoPiOver3);
-    l2 = T(3) * q - l1 - l3;
-  }
-  const int n = (l1 < eps) + (l2 < eps) + (l3 < eps);
+  // Characteristic cubic lambda^3 - c2 lambda^2 + c1 lambda - c0.
+  const T c2 = a00 + a11 + a22;
+  const T c1 = fma(a00, a11, -a01 * a01) + fma(a00, a22, -a02 * a02) + fma(a11, a22, -a12 * a12);
+  const T c0 = a00 * fma(a11, a22, -a12 * a12) - a01 * fma(a01, a22, -a12 * a02) +
+               a02 * fma(a01, a12, -a11 * a02);
+  float f1, f2, f3;
+  eig3_seed(float(a00), float(a01), float(a02), float(a11), float(a12), float(a22), f1, f2, f3);
+  const int n = (T(f1) < eps) + (T(f2) < eps) + (T(f3) < eps);
   if (n == 0) return 0;
-  const T spread = l3 - l1;
-  if (n == 3 || spread <= T(1e-9) * (fabs(l3) + eps)) {
-    const T f = (n == 3) ? eps : (q > eps ? q : eps);
+  const T spread = T(f3) - T(f1);
+  const T scale = fabs(T(f3)) + eps;
+  if (n == 3 || spread <= T(1e-6) * scale) {
+    const T f = (n == 3) ? eps : (c2 / T(3) > eps ? c2 / T(3) : eps);
     A[0] = f; A[1] = T(0); A[2] = T(0); A[3] = f; A[4] = T(0); A[5] = f;
     return n;
   }
+  // The raised eigenvalue (n = 1) or the one kept (n = 2), polished by two
+  // Newton steps on the cubic; the other two enter only through their sum and
+  // product, which follow from the cubic's coefficients.
+  T lj = (n == 1) ? T(f1) : T(f3);
+  T dp = T(0);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const T pv = fma(fma(lj - c2, lj, c1), lj, -c0);   // p(lj)
+    dp = fma(fma(T(3), lj, -T(2) * c2), lj, c1);        // p'(lj)
+    if (fabs(dp) > T(1e-12) * scale * scale) lj -= pv * T(__frcp_rn(float(dp)));
+  }
+  dp = fma(fma(T(3), lj, -T(2) * c2), lj, c1);  // (lj - la)(lj - lb)
+  if (!(fabs(dp) > T(1e-12) * scale * scale)) {
+    const T f = c2 / T(3) > eps ? c2 / T(3) : eps;
+    A[0] = f; A[1] = T(0); A[2] = T(0); A[3] = f; A[4] = T(0); A[5] = f;
+    return n;
+  }
+  const T sum = c2 - lj;                   // la + lb
+  const T prod = fma(-lj, sum, c1);        // la lb
   // S2 = A * A (symmetric, six entries).
-  const T s00 = a00 * a00 + a01 * a01 + a02 * a02;
-  const T s01 = a00 * a01 + a01 * a11 + a02 * a12;
-  const T s02 = a00 * a02 + a01 * a12 + a02 * a22;
-  const T s11 = a01 * a01 + a11 * a11 + a12 * a12;
-  const T s12 = a01 * a02 + a11 * a12 + a12 * a22;
-  const T s22 = a02 * a02 + a12 * a12 + a22 * a22;
-  // Projector onto eigenvalue lj: (A - la I)(A - lb I) / ((lj - la)(lj - lb))
-  //   = (A^2 - (la + lb) A + la lb I) / den.
-  T lj, la, lb;
-  if (n == 1) { lj = l1; la = l2; lb = l3; } else { lj = l3; la = l1; lb = l2; }
-  const T sum = la + lb, prod = la * lb;
-  const T den = (lj - la) * (lj - lb);
-  T P00 = (s00 - sum * a00 + prod) / den, P01 = (s01 - sum * a01) / den;
-  T P02 = (s02 - sum * a02) / den, P11 = (s11 - sum * a11 + prod) / den;
-  T P12 = (s12 - sum * a12) / den, P22 = (s22 - sum * a22 + prod) / den;
+  const T s00 = fma(a00, a00, fma(a01, a01, a02 * a02));
+  const T s01 = fma(a00, a01, fma(a01, a11, a02 * a12));
+  const T s02 = fma(a00, a02, fma(a01, a12, a02 * a22));
+  const T s11 = fma(a01, a01, fma(a11, a11, a12 * a12));
+  const T s12 = fma(a01, a02, fma(a11, a12, a12 * a22));
+  const T s22 = fma(a02, a02, fma(a12, a12, a22 * a22));
+  // Projector onto lj: (A^2 - (la + lb) A + la lb I) / ((lj - la)(lj - lb)).
+  const T g = ((n == 1) ? (eps - lj) : (lj - eps)) * M::rcp(dp);
+  const T P00 = fma(-sum, a00, s00) + prod, P01 = fma(-sum, a01, s01), P02 = fma(-sum, a02, s02);
+  const T P11 = fma(-sum, a11, s11) + prod, P12 = fma(-sum, a12, s12), P22 = fma(-sum, a22, s22) + prod;
   if (n == 1) {
-    const T g = eps - l1;  // A + (eps - l1) P_1
-    A[0] = a00 + g * P00; A[1] = a01 + g * P01; A[2] = a02 + g * P02;
-    A[3] = a11 + g * P11; A[4] = a12 + g * P12; A[5] = a22 + g * P22;
+    // A + (eps - l1) P_1
+    A[0] = fma(g, P00, a00); A[1] = fma(g, P01, a01); A[2] = fma(g, P02, a02);
+    A[3] = fma(g, P11, a11); A[4] = fma(g, P12, a12); A[5] = fma(g, P22, a22);
   } else {
-    const T g = l3 - eps;  // eps I + (l3 - eps) P_3
-    A[0] = eps + g * P00; A[1] = g * P01; A[2] = g * P02;
-    A[3] = eps + g * P11; A[4] = g * P12; A[5] = eps + g * P22;
+    // eps I + (l3 - eps) P_3
+    A[0] = fma(g, P00, eps); A[1] = g * P01; A[2] = g * P02;
+    A[3] = fma(g, P11, eps); A[4] = g * P12; A[5] = fma(g, P22, eps);
   }
   return n;
 }
 
-// Packs mu and the (floored) blocks into the FP32 E-step coefficients.
+// Packs mu and the (floored) blocks into the FP32 E-step coefficients.  The
+// spatial mean is stored relative to (ox, oy), the first pixel of the
+// superpixel's own grid cell (k_x v, k_y v), so that it keeps FP32 precision
+// on large images (absolute coordinates near 4000 would round to 2.4e-4 px).
 // Returns false when a block is not positive definite (leading minors).
 template <typename T>
-__device__ bool pack_gp(const T* mu, const T* cs, const T* cc, float* gp) {
-  using M = MathConst<T>;
+__device__ bool pack_gp(const T* mu, const T* cs, const T* cc, T ox, T oy, float* gp) {
+  using M = Num<T>;
   // spatial 2x2
-  const T ds = cs[0] * cs[2] - cs[1] * cs[1];
+  const T ds = fma(cs[0], cs[2], -cs[1] * cs[1]);
   // colour 3x3 cofactors
-  const T c00 = cc[3] * cc[5] - cc[4] * cc[4];
-  const T c01 = cc[2] * cc[4] - cc[1] * cc[5];
-  const T c02 = cc[1] * cc[4] - cc[2] * cc[3];
-  const T c11 = cc[0] * cc[5] - cc[2] * cc[2];
-  const T c12 = cc[1] * cc[2] - cc[0] * cc[4];
-  const T c22 = cc[0] * cc[3] - cc[1] * cc[1];
-  const T dc = cc[0] * c00 + cc[1] * c01 + cc[2] * c02;
+  const T c00 = fma(cc[3], cc[5], -cc[4] * cc[4]);
+  const T c01 = fma(cc[2], cc[4], -cc[1] * cc[5]);
+  const T c02 = fma(cc[1], cc[4], -cc[2] * cc[3]);
+  const T c11 = fma(cc[0], cc[5], -cc[2] * cc[2]);
+  const T c12 = fma(cc[1], cc[2], -cc[0] * cc[4]);
+  const T c22 = fma(cc[0], cc[3], -cc[1] * cc[1]);
+  const T dc = fma(cc[0], c00, fma(cc[1], c01, cc[2] * c02));
   if (!(cs[0] > T(0) && ds > T(0) && cc[0] > T(0) && c22 > T(0) && dc > T(0))) return false;
-  const T hs = T(-0.5) * M::kLog2e / ds;   // -(1/2) log2(e) / det
-  const T hc = T(-0.5) * M::kLog2e / dc;
+  const T hs = T(-0.5) * M::kLog2e * M::rcp(ds);   // -(1/2) log2(e) / det
+  const T hc = T(-0.5) * M::kLog2e * M::rcp(dc);
   float4* o = reinterpret_cast<float4*>(gp);
-  o[0] = make_float4(float(mu[0]), float(mu[1]), float(mu[2]), float(mu[3]));
+  o[0] = make_float4(float(mu[0] - ox), float(mu[1] - oy), float(mu[2]), float(mu[3]));
   o[1] = make_float4(float(mu[4]), float(hs * cs[2]), float(T(-2) * hs * cs[1]), float(hs * cs[0]));
   o[2] = make_float4(float(hc * c00), float(hc * c11), float(hc * c22), float(T(2) * hc * c01));
-  const T lnorm = (T(-0.5) * M::log_(ds * dc) - M::kHalfD_Ln2Pi) * M::kLog2e;
-  o[3] = make_float4(float(T(2) * hc * c02), float(T(2) * hc * c12), float(lnorm), 0.f);
+  const float lnorm = -0.5f * (M::log2_(ds) + M::log2_(dc)) - float(M::kHalfD_Log2_2Pi);
+  o[3] = make_float4(float(T(2) * hc * c02), float(T(2) * hc * c12), lnorm, 0.f);
   return true;
 }
 

@@ -90,7 +90,7 @@ __global__ void k_init_theta(const float4* __restrict__ lab, Geom g, double lamb
   for (int i = 0; i < 3; ++i) th[5 + i] = cs[i];
   for (int i = 0; i < 6; ++i) th[8 + i] = cc[i];
   th[14] = th[15] = 0.0;
-  pack_gp<double>(mu, cs, cc, gp + (long long)k * kGP);
+  pack_gp<double>(mu, cs, cc, double(kx * g.v), double(ky * g.v), gp + (long long)k * kGP);
 }
 
 __global__ void k_pack_theta(Geom g, const double* __restrict__ theta, float* __restrict__ gp,
@@ -100,7 +100,9 @@ __global__ void k_pack_theta(Geom g, const double* __restrict__ theta, float* __
   const double* th = theta + (long long)k * kTheta;
   bool ok = true;
   for (int i = 0; i < 14; ++i) ok = ok && isfinite(th[i]);
-  ok = ok && pack_gp<double>(th, th + 5, th + 8, gp + (long long)k * kGP);
+  const int kx = k % g.nx, ky = k / g.nx;
+  ok = ok && pack_gp<double>(th, th + 5, th + 8, double(kx * g.v), double(ky * g.v),
+                             gp + (long long)k * kGP);
   if (!ok) atomicAdd(bad, 1);
 }
 

@@ -1,0 +1,148 @@
+// Arithmetic-rate probes (declared in include/gmmsp_probe.h).  Each kernel
+// runs a fixed number of independent dependency chains per thread so that
+// the pipe, not latency, limits it; a single-thread kernel measures the
+// latency of a dependent chain with clock64().
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/gmmsp_probe.h"
+
+namespace {
+
+constexpr int kChains = 8;
+
+__global__ void k_ffma(float* out, int iters) {
+  float a[kChains];
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) a[j] = threadIdx.x * 1e-3f + j;
+  const float b = 0.9999f, c = 1e-4f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < kChains; ++j) a[j] = fmaf(a[j], b, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) s += a[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void k_dfma(double* out, int iters, int active_lanes) {
+  if ((threadIdx.x & 31) >= active_lanes) return;
+  double a[kChains];
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) a[j] = threadIdx.x * 1e-3 + j;
+  const double b = 0.9999, c = 1e-4;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = fma(a[j], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) s += a[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void k_ex2(float* out, int iters) {
+  float a[kChains];
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) a[j] = -0.001f * (threadIdx.x & 63) - 0.1f * j;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) {
+      float y;
+      asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a[j]));
+      a[j] = -y;  // stays in (-1, 0)
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) s += a[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void k_latency(double* out, long long* clk, int iters) {
+  float f = out[0] > 1e300 ? 2.f : 1.0001f;
+  double d = out[1] > 1e300 ? 2.0 : 1.0000001;
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i) f = fmaf(f, 0.99999f, 1e-6f);
+  const long long t1 = clock64();
+  for (int i = 0; i < iters; ++i) d = fma(d, 0.9999999, 1e-9);
+  const long long t2 = clock64();
+  out[2] = f;
+  out[3] = d;
+  clk[0] = t1 - t0;
+  clk[1] = t2 - t1;
+}
+
+template <typename F>
+float time_ms(F launch) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  launch();  // warm-up
+  cudaEventRecord(a);
+  launch();
+  cudaEventRecord(b);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+
+}  // namespace
+
+extern "C" int gmmsp_probe_peaks(gmmsp_peaks* out, char* err, int err_len) {
+  if (!out) return 1;
+  memset(out, 0, sizeof(*out));
+  int dev = 0;
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, dev);
+  int clk_khz = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+  if (e != cudaSuccess) {
+    if (err && err_len > 0) snprintf(err, err_len, "%s", cudaGetErrorString(e));
+    return 2;
+  }
+  out->sm_count = prop.multiProcessorCount;
+  out->clock_mhz = clk_khz / 1000;
+  const int blocks = prop.multiProcessorCount * 8, threads = 256;
+  void* buf = nullptr;
+  e = cudaMalloc(&buf, size_t(blocks) * threads * sizeof(double) + 64);
+  if (e != cudaSuccess) {
+    if (err && err_len > 0) snprintf(err, err_len, "%s", cudaGetErrorString(e));
+    return 2;
+  }
+  const int it32 = 256, it64 = 1024, itx = 4096;
+  float ms = time_ms([&] { k_ffma<<<blocks, threads>>>((float*)buf, it32); });
+  out->fp32_fma_tflops = double(blocks) * threads * it32 * 4 * kChains * 2 / (ms * 1e-3) / 1e12;
+  ms = time_ms([&] { k_dfma<<<blocks, threads>>>((double*)buf, it64, 32); });
+  out->fp64_fma_tflops = double(blocks) * threads * it64 * kChains * 2 / (ms * 1e-3) / 1e12;
+  ms = time_ms([&] { k_dfma<<<blocks, threads>>>((double*)buf, it64, 1); });
+  out->fp64_fma_tflops_lane1 = double(blocks) * (threads / 32) * it64 * kChains * 2 / (ms * 1e-3) / 1e12;
+  ms = time_ms([&] { k_ex2<<<blocks, threads>>>((float*)buf, itx); });
+  out->mufu_ex2_tops = double(blocks) * threads * itx * kChains / (ms * 1e-3) / 1e12;
+  e = cudaMemset(buf, 0, 64);
+  long long* clk = reinterpret_cast<long long*>(static_cast<char*>(buf) + 32);
+  const int itl = 1 << 16;
+  if (e == cudaSuccess) {
+    k_latency<<<1, 1>>>((double*)buf, clk, itl);
+    e = cudaDeviceSynchronize();
+  }
+  long long h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, clk, sizeof(h), cudaMemcpyDeviceToHost);
+  out->fp32_fma_latency_clk = double(h[0]) / itl;
+  out->fp64_fma_latency_clk = double(h[1]) / itl;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    if (err && err_len > 0) snprintf(err, err_len, "%s", cudaGetErrorString(e));
+    return 2;
+  }
+  return 0;
+}

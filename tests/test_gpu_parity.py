@@ -29,10 +29,12 @@ def lab_input(W, H, regions, sigma, seed):
     return img, oracle.rgb2lab(img).astype(np.float32)
 
 
-def run_gpu(gm, lab32, K=0, spacing=0, T=10, precision=0):
+def run_gpu(gm, lab32, K=0, spacing=0, T=10, precision=0, wpc=None):
     import torch
     dev = torch.from_numpy(lab32).cuda()
     sp = gm.Superpixels(dev, K=K, spacing=spacing, precision=precision)
+    if wpc is not None:
+        sp.set_launch(wpc)
     ll = list(sp.em_iters(T, want_loglik=True)) if T > 0 else []
     labels, ll_last = sp.labels(want_loglik=True)
     mu, cs, cc = sp.get_params()
@@ -55,11 +57,12 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("wpc", [1, 2, 4])
 @pytest.mark.parametrize("W,H,R,sigma,seed,K,sp,T", CASES)
-def test_em_matches_oracle(gm, W, H, R, sigma, seed, K, sp, T):
+def test_em_matches_oracle(gm, W, H, R, sigma, seed, K, sp, T, wpc):
     _, lab32 = lab_input(W, H, R, sigma, seed)
     ref = oracle.em(lab32.astype(np.float64), W, H, K=K, spacing=sp, T=T)
-    got = run_gpu(gm, lab32, K=K, spacing=sp, T=T)
+    got = run_gpu(gm, lab32, K=K, spacing=sp, T=T, wpc=wpc)
     assert (got["grid"].v, got["grid"].nx, got["grid"].ny, got["grid"].K) == \
         (ref.grid.v, ref.grid.nx, ref.grid.ny, ref.grid.K)
     np.testing.assert_allclose(got["ll"], ref.loglik, rtol=parity.LL_RTOL)
@@ -195,6 +198,25 @@ def test_fp32_variant_error_is_reported(gm):
     assert e_mixed <= parity.COV_TOL
     assert e_fp32 < 0.5
     assert (fp32["labels"] == ref.labels).mean() > 0.95
+
+
+def test_autotune_and_kernel_timing(gm):
+    import torch
+    W, H = 481, 321
+    img = torch.from_numpy(voronoi_image(W, H, 150, 8.0, seed=4)).cuda()
+    sp = gm.Superpixels(img, K=1000)
+    sp.em_iters(2)
+    before = sp.get_params()
+    best, times = sp.autotune(reps=3)
+    assert best in (1, 2, 4) and sp.get_launch() == best
+    assert all(t > 0 for t in times.values())
+    labels = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    for which in (gm.GMMSP_KERNEL_EM_PASS, gm.GMMSP_KERNEL_FINALIZE, gm.GMMSP_KERNEL_LABELS):
+        assert sp.profile_kernel(which, reps=3, labels=labels) > 0
+    after = sp.get_params()  # timing leaves theta as it was
+    for a, b in zip(before, after):
+        np.testing.assert_array_equal(a, b)
+    sp.close()
 
 
 def test_nonfinite_input_is_reported(gm):
