@@ -523,6 +523,9 @@ gmmsp_status gmmsp_profile_kernel(gmmsp_ctx c, int which, int reps, int32_t* lab
     else *avg_ms = sum / reps;
   }
   if (save) {
+    cudaMemcpyAsync(c->theta, save, th_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->gp, static_cast<char*>(save) + th_bytes, gp_bytes, cudaMemcpyDeviceToDevice,
+                    c->stream);
     cudaStreamSynchronize(c->stream);
     cudaFree(save);
   }
