@@ -148,14 +148,14 @@ gmmsp_status enqueue_prepare(gmmsp_ctx c, const void* image, int pitch) {
   else
     GM_CHECK(c, gmmsp::launch_lab32(static_cast<const float*>(image), pitch, g, c->lab, c->counters,
                                     c->stream));
-  GM_CHECK(c, gmmsp::launch_init_theta(c->lab, g, c->p.lambda_c, c->theta, c->gp, c->stream));
+  GM_CHECK(c, gmmsp::launch_init_theta(gmmsp::LabPacked{c->lab, g.W}, g, c->p.lambda_c, c->theta, c->gp, c->stream));
   return GMMSP_OK;
 }
 
 // Enqueues `iters` EM rounds; llk[t0 + t] receives L(theta_t).
 gmmsp_status enqueue_em(gmmsp_ctx c, int iters, int t0) {
   for (int t = 0; t < iters; ++t) {
-    GM_CHECK(c, gmmsp::launch_em_pass(c->lab, c->g, c->gp, c->partials, c->p.precision, c->wpc,
+    GM_CHECK(c, gmmsp::launch_em_pass(gmmsp::LabPacked{c->lab, c->g.W}, c->g, c->gp, c->partials, c->p.precision, c->wpc,
                                       c->stream));
     double* llk_out = c->llk + ((t0 + t) % kLlkCap);
     GM_CHECK(c, gmmsp::launch_finalize(c->g, c->partials, c->theta, c->gp, c->p.eps_s, c->p.eps_c,
@@ -166,7 +166,7 @@ gmmsp_status enqueue_em(gmmsp_ctx c, int iters, int t0) {
 }
 
 gmmsp_status enqueue_labels(gmmsp_ctx c, int32_t* labels, double* llk_out) {
-  GM_CHECK(c, gmmsp::launch_label_pass(c->lab, c->g, c->gp, labels, c->cell_ll, c->stream));
+  GM_CHECK(c, gmmsp::launch_label_pass(gmmsp::LabPacked{c->lab, c->g.W}, c->g, c->gp, labels, c->cell_ll, c->stream));
   if (llk_out)
     GM_CHECK(c, gmmsp::launch_ll_reduce(c->cell_ll, c->g.ncells, llk_out, c->ws, c->ticket, c->g,
                                         c->stream));
@@ -501,9 +501,9 @@ gmmsp_status gmmsp_profile_kernel(gmmsp_ctx c, int which, int reps, int32_t* lab
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r], c->stream);
     if (e == cudaSuccess) {
       if (which == GMMSP_KERNEL_EM_PASS)
-        e = gmmsp::launch_em_pass(c->lab, c->g, c->gp, c->partials, c->p.precision, c->wpc, c->stream);
+        e = gmmsp::launch_em_pass(gmmsp::LabPacked{c->lab, c->g.W}, c->g, c->gp, c->partials, c->p.precision, c->wpc, c->stream);
       else if (which == GMMSP_KERNEL_LABELS)
-        e = gmmsp::launch_label_pass(c->lab, c->g, c->gp, labels_dev, c->cell_ll, c->stream);
+        e = gmmsp::launch_label_pass(gmmsp::LabPacked{c->lab, c->g.W}, c->g, c->gp, labels_dev, c->cell_ll, c->stream);
       else
         e = gmmsp::launch_finalize(c->g, c->partials, c->theta, c->gp, c->p.eps_s, c->p.eps_c, c->llk,
                                    c->ws, c->ticket, c->counters, c->p.precision, c->stream);

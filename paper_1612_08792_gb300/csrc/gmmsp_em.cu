@@ -167,8 +167,8 @@ __device__ __forceinline__ void rel_coords(int rx, int ry, int v, float (&fxs)[3
   fys[0] = float(ry + v); fys[1] = float(ry); fys[2] = float(ry - v);
 }
 
-template <bool FULL, bool SHIFT, int LANES>
-__device__ __forceinline__ void em_cell_pixels(const float4* __restrict__ lab, const Geom& g,
+template <bool FULL, bool SHIFT, int LANES, class Src>
+__device__ __forceinline__ void em_cell_pixels(const Src& lab, const Geom& g,
                                                const Cell& c, const float4* sp, int t,
                                                float (&acc)[kSlots * kStats], float& ll) {
   const int npx = c.cw * c.ch;
@@ -184,7 +184,7 @@ __device__ __forceinline__ void em_cell_pixels(const float4* __restrict__ lab, c
   float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   if (p < npx) {
     locate(p, rx, ry);
-    z = __ldg(lab + (long long)(c.y0 + ry) * g.W + (c.x0 + rx));
+    z = lab.load(c.x0 + rx, c.y0 + ry);
   }
   while (p < npx) {
     const int pn = p + LANES;
@@ -192,7 +192,7 @@ __device__ __forceinline__ void em_cell_pixels(const float4* __restrict__ lab, c
     float4 zn = z;
     if (pn < npx) {
       locate(pn, rxn, ryn);
-      zn = __ldg(lab + (long long)(c.y0 + ryn) * g.W + (c.x0 + rxn));
+      zn = lab.load(c.x0 + rxn, c.y0 + ryn);
     }
     float fxs[3], fys[3];
     rel_coords(rx, ry, g.v, fxs, fys);
@@ -207,8 +207,8 @@ __device__ __forceinline__ void em_cell_pixels(const float4* __restrict__ lab, c
 // 4 / WPC cells.  The WPC x 32 per-thread accumulator sets of a cell are
 // summed through shared memory: every thread writes its column of a
 // 68-row tile (two tiles for the 136 sums), then each thread adds up whole rows.
-template <typename PT, bool SHIFT, int WPC>
-__global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(const float4* __restrict__ lab, Geom g,
+template <typename PT, bool SHIFT, int WPC, class Src>
+__global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(Src lab, Geom g,
                                                            const float* __restrict__ gp,
                                                            PT* __restrict__ partials) {
   constexpr int kLanes = 32 * WPC;             // threads per cell
@@ -244,9 +244,9 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(const float4* __restr
   float ll = 0.f;
   if (active) {
     if (c.mask == 0x1ffu)
-      em_cell_pixels<true, SHIFT, kLanes>(lab, g, c, sp, t, acc, ll);
+      em_cell_pixels<true, SHIFT, kLanes, Src>(lab, g, c, sp, t, acc, ll);
     else
-      em_cell_pixels<false, SHIFT, kLanes>(lab, g, c, sp, t, acc, ll);
+      em_cell_pixels<false, SHIFT, kLanes, Src>(lab, g, c, sp, t, acc, ll);
   }
 
   // Row 135 carries the log-likelihood (log2 units until written).
@@ -279,8 +279,8 @@ constexpr int em_smem_bytes() {
 
 // Label pass: argmax posterior per pixel (ties to the smaller k, i.e. the
 // smaller slot) and the per-cell log-likelihood.
-template <bool FULL>
-__device__ __forceinline__ void label_cell_pixels(const float4* __restrict__ lab, const Geom& g,
+template <bool FULL, class Src>
+__device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
                                                   const Cell& c, const float4* sp, int lane,
                                                   int32_t* __restrict__ labels, float& ll) {
   const int npx = c.cw * c.ch;
@@ -289,7 +289,7 @@ __device__ __forceinline__ void label_cell_pixels(const float4* __restrict__ lab
     const int ry = __float2int_rz((float(p) + 0.5f) * inv_cw);
     const int rx = p - ry * c.cw;
     const int x = c.x0 + rx, y = c.y0 + ry;
-    const float4 z = __ldg(lab + (long long)y * g.W + x);
+    const float4 z = lab.load(x, y);
     float fxs[3], fys[3];
     rel_coords(rx, ry, g.v, fxs, fys);
     float e[kSlots];
@@ -312,8 +312,8 @@ __device__ __forceinline__ void label_cell_pixels(const float4* __restrict__ lab
   }
 }
 
-__global__ void __launch_bounds__(kEmWarps * 32) k_label_pass(const float4* __restrict__ lab,
-                                                              Geom g, const float* __restrict__ gp,
+template <class Src>
+__global__ void __launch_bounds__(kEmWarps * 32) k_label_pass(Src lab, Geom g, const float* __restrict__ gp,
                                                               int32_t* __restrict__ labels,
                                                               double* __restrict__ cell_ll) {
   __shared__ float4 sp_all[kEmWarps][kSlots * 4];
@@ -325,9 +325,9 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass(const float4* __re
   stage_params(g, c, gp, sp, lane);
   float ll = 0.f;
   if (c.mask == 0x1ffu)
-    label_cell_pixels<true>(lab, g, c, sp, lane, labels, ll);
+    label_cell_pixels<true, Src>(lab, g, c, sp, lane, labels, ll);
   else
-    label_cell_pixels<false>(lab, g, c, sp, lane, labels, ll);
+    label_cell_pixels<false, Src>(lab, g, c, sp, lane, labels, ll);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
   if (lane == 0) cell_ll[cell] = double(ll) * 0.69314718055994530942;
@@ -466,46 +466,58 @@ static int ll_blocks(const Geom& g) { return (g.K + kFinThreads - 1) / kFinThrea
 
 size_t finalize_workspace_doubles(const Geom& g) { return size_t(ll_blocks(g)) + 1; }
 
-template <typename PT, bool SHIFT, int WPC>
-static cudaError_t em_pass_impl(const float4* lab, const Geom& g, const float* gp, PT* partials,
+template <typename PT, bool SHIFT, int WPC, class Src>
+static cudaError_t em_pass_impl(Src lab, const Geom& g, const float* gp, PT* partials,
                                 cudaStream_t s) {
   constexpr int smem = em_smem_bytes<WPC>();
   static_assert(smem <= 227 * 1024, "shared memory");
   static bool attr_set = false;  // per process; the attribute is per function
   if (!attr_set && smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_em_pass<PT, SHIFT, WPC>,
+    cudaError_t e = cudaFuncSetAttribute(k_em_pass<PT, SHIFT, WPC, Src>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   constexpr int cpb = kEmWarps / WPC;
   const int blocks = (g.ncells + cpb - 1) / cpb;
-  k_em_pass<PT, SHIFT, WPC><<<blocks, kEmWarps * 32, smem, s>>>(lab, g, gp, partials);
+  k_em_pass<PT, SHIFT, WPC, Src><<<blocks, kEmWarps * 32, smem, s>>>(lab, g, gp, partials);
   return cudaGetLastError();
 }
 
-template <typename PT, bool SHIFT>
-static cudaError_t em_pass_wpc(const float4* lab, const Geom& g, const float* gp, PT* partials,
-                               int wpc, cudaStream_t s) {
+template <typename PT, bool SHIFT, class Src>
+static cudaError_t em_pass_wpc(Src lab, const Geom& g, const float* gp, PT* partials, int wpc,
+                               cudaStream_t s) {
   switch (wpc) {
-    case 2: return em_pass_impl<PT, SHIFT, 2>(lab, g, gp, partials, s);
-    case 4: return em_pass_impl<PT, SHIFT, 4>(lab, g, gp, partials, s);
-    default: return em_pass_impl<PT, SHIFT, 1>(lab, g, gp, partials, s);
+    case 2: return em_pass_impl<PT, SHIFT, 2, Src>(lab, g, gp, partials, s);
+    case 4: return em_pass_impl<PT, SHIFT, 4, Src>(lab, g, gp, partials, s);
+    default: return em_pass_impl<PT, SHIFT, 1, Src>(lab, g, gp, partials, s);
   }
 }
 
-cudaError_t launch_em_pass(const float4* lab, const Geom& g, const float* gp, void* partials,
-                           int precision, int wpc, cudaStream_t s) {
-  if (precision == 1) return em_pass_wpc<float, false>(lab, g, gp, static_cast<float*>(partials), wpc, s);
-  return em_pass_wpc<double, true>(lab, g, gp, static_cast<double*>(partials), wpc, s);
+template <class Src>
+cudaError_t launch_em_pass(Src lab, const Geom& g, const float* gp, void* partials, int precision,
+                           int wpc, cudaStream_t s) {
+  if (precision == 1)
+    return em_pass_wpc<float, false, Src>(lab, g, gp, static_cast<float*>(partials), wpc, s);
+  return em_pass_wpc<double, true, Src>(lab, g, gp, static_cast<double*>(partials), wpc, s);
 }
 
-cudaError_t launch_label_pass(const float4* lab, const Geom& g, const float* gp, int32_t* labels,
+template <class Src>
+cudaError_t launch_label_pass(Src lab, const Geom& g, const float* gp, int32_t* labels,
                               double* cell_ll, cudaStream_t s) {
   const int blocks = (g.ncells + kEmWarps - 1) / kEmWarps;
-  k_label_pass<<<blocks, kEmWarps * 32, 0, s>>>(lab, g, gp, labels, cell_ll);
+  k_label_pass<Src><<<blocks, kEmWarps * 32, 0, s>>>(lab, g, gp, labels, cell_ll);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_em_pass<LabPacked>(LabPacked, const Geom&, const float*, void*, int, int,
+                                               cudaStream_t);
+template cudaError_t launch_em_pass<LabPitched>(LabPitched, const Geom&, const float*, void*, int, int,
+                                                cudaStream_t);
+template cudaError_t launch_label_pass<LabPacked>(LabPacked, const Geom&, const float*, int32_t*, double*,
+                                                  cudaStream_t);
+template cudaError_t launch_label_pass<LabPitched>(LabPitched, const Geom&, const float*, int32_t*,
+                                                   double*, cudaStream_t);
 
 cudaError_t launch_finalize(const Geom& g, const void* partials, double* theta, float* gp,
                             double eps_s, double eps_c, double* llk_out, double* ws,

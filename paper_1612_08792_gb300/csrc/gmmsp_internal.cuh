@@ -51,6 +51,21 @@ struct Geom {
   int ncells;
 };
 
+// Where the kernels read the CIELAB colour of pixel (x, y) from.
+struct LabPacked {  // the context's image: one float4 (L, a, b, 0) per pixel
+  const float4* p;
+  int W;
+  __device__ __forceinline__ float4 load(int x, int y) const { return __ldg(p + (long long)y * W + x); }
+};
+struct LabPitched {  // a caller's image: rows of (L, a, b) float32, row pitch in bytes
+  const char* p;
+  long long pitch;
+  __device__ __forceinline__ float4 load(int x, int y) const {
+    const float* q = reinterpret_cast<const float*>(p + (long long)y * pitch) + 3LL * x;
+    return make_float4(__ldg(q), __ldg(q + 1), __ldg(q + 2), 0.f);
+  }
+};
+
 // Device counters (unsigned long long): dead, raised_s, raised_c, nonfinite input.
 enum : int { CNT_DEAD = 0, CNT_RAISED_S = 1, CNT_RAISED_C = 2, CNT_NONFINITE = 3, CNT_N = 4 };
 
@@ -59,12 +74,15 @@ cudaError_t launch_rgb2lab(const uint8_t* img, long long pitch, const Geom& g, f
                            unsigned long long* counters, cudaStream_t s);
 cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float4* lab,
                          unsigned long long* counters, cudaStream_t s);
-cudaError_t launch_init_theta(const float4* lab, const Geom& g, double lambda_c, double* theta,
-                              float* gp, cudaStream_t s);
+template <class Src>
+cudaError_t launch_init_theta(Src lab, const Geom& g, double lambda_c, double* theta, float* gp,
+                              cudaStream_t s);
 // wpc: warps per cell (1, 2 or 4).
-cudaError_t launch_em_pass(const float4* lab, const Geom& g, const float* gp, void* partials,
-                           int precision, int wpc, cudaStream_t s);
-cudaError_t launch_label_pass(const float4* lab, const Geom& g, const float* gp, int32_t* labels,
+template <class Src>
+cudaError_t launch_em_pass(Src lab, const Geom& g, const float* gp, void* partials, int precision,
+                           int wpc, cudaStream_t s);
+template <class Src>
+cudaError_t launch_label_pass(Src lab, const Geom& g, const float* gp, int32_t* labels,
                               double* cell_ll, cudaStream_t s);
 // Finalize: ws holds finalize_workspace_doubles(g) doubles, ticket one zeroed
 // unsigned that the kernel leaves at zero.  llk_out (device) receives the

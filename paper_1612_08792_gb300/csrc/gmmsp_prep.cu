@@ -74,13 +74,14 @@ __global__ void __launch_bounds__(256) k_lab32(const float* __restrict__ img, lo
   if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&counters[CNT_NONFINITE], (unsigned long long)bad);
 }
 
-__global__ void k_init_theta(const float4* __restrict__ lab, Geom g, double lambda_c,
-                             double* __restrict__ theta, float* __restrict__ gp) {
+template <class Src>
+__global__ void k_init_theta(Src lab, Geom g, double lambda_c, double* __restrict__ theta,
+                             float* __restrict__ gp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= g.K) return;
   const int kx = k % g.nx, ky = k / g.nx;
   const int x = kx * g.v + g.v / 2, y = ky * g.v + g.v / 2;
-  const float4 c = lab[(long long)y * g.W + x];
+  const float4 c = lab.load(x, y);
   const double mu[5] = {double(x), double(y), double(c.x), double(c.y), double(c.z)};
   const double vv = double(g.v) * double(g.v), ll = lambda_c * lambda_c;
   const double cs[3] = {vv, 0.0, vv};
@@ -162,11 +163,17 @@ cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_theta(const float4* lab, const Geom& g, double lambda_c, double* theta,
-                              float* gp, cudaStream_t s) {
-  k_init_theta<<<(g.K + 63) / 64, 64, 0, s>>>(lab, g, lambda_c, theta, gp);
+template <class Src>
+cudaError_t launch_init_theta(Src lab, const Geom& g, double lambda_c, double* theta, float* gp,
+                              cudaStream_t s) {
+  k_init_theta<Src><<<(g.K + 63) / 64, 64, 0, s>>>(lab, g, lambda_c, theta, gp);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_init_theta<LabPacked>(LabPacked, const Geom&, double, double*, float*,
+                                                  cudaStream_t);
+template cudaError_t launch_init_theta<LabPitched>(LabPitched, const Geom&, double, double*, float*,
+                                                   cudaStream_t);
 
 cudaError_t launch_pack_theta(const Geom& g, double* theta, float* gp, int* bad, cudaStream_t s) {
   k_pack_theta<<<(g.K + 63) / 64, 64, 0, s>>>(g, theta, gp, bad);
