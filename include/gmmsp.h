@@ -209,6 +209,42 @@ gmmsp_status gmmsp_get_launch(gmmsp_ctx c, int *warps_per_cell);
  */
 gmmsp_status gmmsp_autotune(gmmsp_ctx c, int reps, int *best, double *times_ms);
 
+/*
+ * Allocation-free segmentation (the paper has no counterpart; this serves
+ * callers that cannot allocate device memory where they run: code inside a
+ * memory pool or a caching allocator that owns all device memory, code that
+ * must not trigger the device synchronisation that cudaMalloc/cudaFree can
+ * cause, and plug-ins that are only handed their input and output buffers).
+ *
+ * Runs the same steps as gmmsp_init (GMMSP_LAB32) + gmmsp_em_iters(iters) +
+ * gmmsp_labels on a CIELAB image, with the same kernels, and allocates
+ * nothing: its working memory (theta, the packed E-step coefficients, the
+ * per-cell partial sums, counters) is one fixed __device__ array of
+ * GMMSP_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *   lab_dev      device rows of W x (L, a, b) float32, 4-byte aligned;
+ *   pitch_bytes  row pitch, >= 12 W, a multiple of 4;
+ *   p            spacing or K, eps_s, eps_c, lambda_c as for gmmsp_init
+ *                (input_format is ignored; precision must be MIXED);
+ *   labels_dev   device int32[W H], written (argmax posterior, Eq. obtLi);
+ *   stream       cudaStream_t to queue on; the call does not synchronise;
+ *   err          NULL, or err_len bytes receiving a message on failure.
+ * Limits: the cell grid ceil(W/v) x ceil(H/v) may hold at most
+ * GMMSP_NOALLOC_MAX_CELLS cells (e.g. 481x321 at v >= 8, 1920x1080 at
+ * v >= 30); larger grids return GMMSP_E_INVALID with the sizes in err.
+ * Every call shares the one array, which keeps the previous call's
+ * contents (the call clears what must start at zero): calls that overlap on
+ * the GPU (different streams, devices' work still in flight on another
+ * stream) race and must be serialised by the caller.  On each device the
+ * first call looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.
+ */
+#define GMMSP_NOALLOC_MAX_CELLS 4096
+#define GMMSP_NOALLOC_SCRATCH_BYTES ((5u << 20) + (64u << 10))
+gmmsp_status gmmsp_segment_lab_noalloc(const float *lab_dev, int width, int height, int pitch_bytes,
+                                       const gmmsp_params *p, int iters, int32_t *labels_dev,
+                                       void *stream, char *err, int err_len);
+
 /* Text of the last error on c (never NULL; "" when there is none). */
 const char *gmmsp_last_error(gmmsp_ctx c);
 

@@ -25,7 +25,7 @@ __all__ = [
     "gmmsp_default_params", "gmmsp_init", "gmmsp_reinit", "gmmsp_em_iters", "gmmsp_labels",
     "gmmsp_segment", "gmmsp_get_lab", "gmmsp_get_grid", "gmmsp_get_params", "gmmsp_set_params", "gmmsp_get_stats",
     "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_set_launch", "gmmsp_get_launch",
-    "gmmsp_autotune", "gmmsp_last_error", "gmmsp_status_string", "gmmsp_destroy",
+    "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "gmmsp_status_string", "gmmsp_destroy",
 ]
 
 GMMSP_RGB8, GMMSP_LAB32 = 0, 1
@@ -251,6 +251,21 @@ def gmmsp_probe_peaks() -> dict:
     if st != 0:
         raise GmmspError(2, err.value.decode())
     return {name: getattr(out, name) for name, _ in gmmsp_peaks._fields_}
+
+
+def gmmsp_segment_lab_noalloc(lab, width: int, height: int, pitch_bytes: int, params: gmmsp_params,
+                              iters: int, labels, stream=None) -> None:
+    """Allocation-free pipeline on a CIELAB float32 image (see include/gmmsp.h)."""
+    lib = load_library()
+    f = lib.gmmsp_segment_lab_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(gmmsp_params),
+                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
+    err = ctypes.create_string_buffer(256)
+    st = f(_dptr(lab), int(width), int(height), int(pitch_bytes), ctypes.byref(params), int(iters),
+           _dptr(labels), _stream_handle(stream), err, 256)
+    if st != 0:
+        raise GmmspError(st, err.value.decode())
 
 
 def gmmsp_last_error(ctx) -> str:
