@@ -245,6 +245,20 @@ gmmsp_status gmmsp_segment_lab_noalloc(const float *lab_dev, int width, int heig
                                        const gmmsp_params *p, int iters, int32_t *labels_dev,
                                        void *stream, char *err, int err_len);
 
+/*
+ * In-pipeline kernel timing (no counterpart in the paper: a measurement aid).
+ * gmmsp_set_timing(c, 1) makes every later call record a CUDA event between
+ * its steps (inside a gmmsp_segment graph they become event nodes; changing
+ * the setting drops a captured graph).  gmmsp_get_timing synchronises and
+ * returns, for the last call that queued work, the milliseconds between
+ * consecutive events: for gmmsp_segment with T iterations the 2T + 2 values
+ * are [conversion + theta_0, E+M pass 0, finalize 0, ..., E+M pass T-1,
+ * finalize T-1, label pass]; gmmsp_em_iters gives the 2T pass/finalize
+ * values; gmmsp_labels one.  *n receives the count, at most cap are written.
+ */
+gmmsp_status gmmsp_set_timing(gmmsp_ctx c, int enable);
+gmmsp_status gmmsp_get_timing(gmmsp_ctx c, double *ms, int cap, int *n);
+
 /* Text of the last error on c (never NULL; "" when there is none). */
 const char *gmmsp_last_error(gmmsp_ctx c);
 

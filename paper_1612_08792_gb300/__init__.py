@@ -24,7 +24,7 @@ __all__ = [
     "gmmsp_params", "load_library", "library_path", "Superpixels",
     "gmmsp_default_params", "gmmsp_init", "gmmsp_reinit", "gmmsp_em_iters", "gmmsp_labels",
     "gmmsp_segment", "gmmsp_get_lab", "gmmsp_get_grid", "gmmsp_get_params", "gmmsp_set_params", "gmmsp_get_stats",
-    "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_set_launch", "gmmsp_get_launch",
+    "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_set_timing", "gmmsp_get_timing", "gmmsp_set_launch", "gmmsp_get_launch",
     "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "gmmsp_status_string", "gmmsp_destroy",
 ]
 
@@ -83,6 +83,8 @@ def load_library(path: str | None = None):
             "gmmsp_set_params": (I, [P, P, P, P]),
             "gmmsp_get_stats": (I, [P, pll, pll, pll]),
             "gmmsp_profile_kernel": (I, [P, I, I, P, P, ctypes.c_ulonglong, ctypes.POINTER(D)]),
+            "gmmsp_set_timing": (I, [P, I]),
+            "gmmsp_get_timing": (I, [P, P, I, pint]),
             "gmmsp_set_launch": (I, [P, I]),
             "gmmsp_get_launch": (I, [P, pint]),
             "gmmsp_autotune": (I, [P, I, pint, P]),
@@ -202,6 +204,18 @@ def gmmsp_get_stats(ctx):
 
 
 GMMSP_KERNEL_EM_PASS, GMMSP_KERNEL_LABELS, GMMSP_KERNEL_FINALIZE = 0, 1, 2
+
+
+def gmmsp_set_timing(ctx, enable: bool) -> None:
+    _check(ctx, load_library().gmmsp_set_timing(ctx, int(bool(enable))))
+
+
+def gmmsp_get_timing(ctx):
+    buf = np.zeros(4096)
+    n = ctypes.c_int()
+    _check(ctx, load_library().gmmsp_get_timing(ctx, buf.ctypes.data_as(ctypes.c_void_p), 4096,
+                                                ctypes.byref(n)))
+    return buf[:min(n.value, 4096)].copy()
 
 
 def gmmsp_set_launch(ctx, warps_per_cell: int) -> None:
@@ -356,6 +370,12 @@ class Superpixels:
             labels_host.copy_(dev_labels, non_blocking=True)
         self.stream.synchronize()
         return ll
+
+    def set_timing(self, enable: bool) -> None:
+        gmmsp_set_timing(self.ctx, enable)
+
+    def get_timing(self):
+        return gmmsp_get_timing(self.ctx)
 
     def set_launch(self, warps_per_cell: int) -> None:
         gmmsp_set_launch(self.ctx, warps_per_cell)

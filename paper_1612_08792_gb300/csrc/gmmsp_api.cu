@@ -2,7 +2,7 @@
 // argument checks, device buffers and the launch sequence of Algorithm 1.
 //
 // Device memory of a context is one allocation carved into:
-//   lab       W H float4          CIELAB image, (L, a, b, 0) per pixel
+//   lab       3 W H float         CIELAB image as planes L, a, b
 //   theta     K x 16 double       master parameters (mu, Sigma_s, Sigma_c)
 //   gp        K x 16 float        packed E-step coefficients
 //   partials  ncells x 136        per-cell FP64 (FP32 variant: float) partial sums
@@ -25,6 +25,19 @@
 
 using gmmsp::Geom;
 
+namespace gmmsp {
+// Programmatic dependent launch measured slower than plain stream order for
+// this pipeline on GB300 (about 2x per EM iteration on 481x321), so it is off
+// unless GMMSP_PDL=1 is set.
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("GMMSP_PDL");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+}  // namespace gmmsp
+
 namespace {
 
 constexpr int kLlkCap = 1024;
@@ -35,6 +48,7 @@ struct Graph {
   const void* image = nullptr;
   int pitch = 0;
   int32_t* labels = nullptr;
+  bool want_ll = false;
 };
 
 }  // namespace
@@ -45,7 +59,7 @@ struct gmmsp_ctx_s {
   cudaStream_t stream = nullptr;
   int device = 0;
   void* slab = nullptr;
-  float4* lab = nullptr;
+  float* lab = nullptr;           // CIELAB planes L, a, b (W H floats each)
   double* theta = nullptr;
   float* gp = nullptr;
   void* partials = nullptr;
@@ -56,6 +70,9 @@ struct gmmsp_ctx_s {
   unsigned long long* counters = nullptr;
   int* bad = nullptr;
   int wpc = 1;                    // warps per cell of the E+M pass (launch shape)
+  bool timing = false;            // record events between the kernels (gmmsp_set_timing)
+  std::vector<cudaEvent_t> tev;   // timing events, created on demand
+  int tev_used = 0;               // events recorded by the last enqueued sequence
   gmmsp_status state = GMMSP_OK;  // sticky error
   std::string err;
   Graph graph;
@@ -138,9 +155,30 @@ gmmsp_status check_ready(gmmsp_ctx c) {
   return GMMSP_OK;
 }
 
+// With timing on, records an event on the context's stream (as an event
+// node when the stream is being captured into a graph).
+gmmsp_status mark(gmmsp_ctx c) {
+  if (!c->timing) return GMMSP_OK;
+  if (c->tev_used == int(c->tev.size())) {
+    cudaEvent_t e = nullptr;
+    GM_CHECK(c, cudaEventCreate(&e));
+    c->tev.push_back(e);
+  }
+  GM_CHECK(c, cudaEventRecordWithFlags(c->tev[c->tev_used], c->stream, cudaEventRecordExternal));
+  ++c->tev_used;
+  return GMMSP_OK;
+}
+
+#define GM_MARK(c)                          \
+  do {                                      \
+    gmmsp_status s_ = mark(c);              \
+    if (s_ != GMMSP_OK) return s_;          \
+  } while (0)
+
 // Enqueues step 1 of Algorithm 1: image -> CIELAB, theta_0; clears counters.
 gmmsp_status enqueue_prepare(gmmsp_ctx c, const void* image, int pitch) {
   const Geom& g = c->g;
+  GM_MARK(c);
   GM_CHECK(c, cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * gmmsp::CNT_N, c->stream));
   if (c->p.input_format == GMMSP_RGB8)
     GM_CHECK(c, gmmsp::launch_rgb2lab(static_cast<const uint8_t*>(image), pitch, g, c->lab, c->counters,
@@ -148,28 +186,32 @@ gmmsp_status enqueue_prepare(gmmsp_ctx c, const void* image, int pitch) {
   else
     GM_CHECK(c, gmmsp::launch_lab32(static_cast<const float*>(image), pitch, g, c->lab, c->counters,
                                     c->stream));
-  GM_CHECK(c, gmmsp::launch_init_theta(gmmsp::LabPacked{c->lab, g.W}, g, c->p.lambda_c, c->theta, c->gp, c->stream));
+  GM_CHECK(c, gmmsp::launch_init_theta(gmmsp::LabPlanar{c->lab, (long long)g.W * g.H, g.W}, g, c->p.lambda_c, c->theta, c->gp, c->stream));
+  GM_MARK(c);
   return GMMSP_OK;
 }
 
-// Enqueues `iters` EM rounds; llk[t0 + t] receives L(theta_t).
-gmmsp_status enqueue_em(gmmsp_ctx c, int iters, int t0) {
+// Enqueues `iters` EM rounds; with want_ll, llk[t0 + t] receives L(theta_t).
+gmmsp_status enqueue_em(gmmsp_ctx c, int iters, int t0, bool want_ll) {
   for (int t = 0; t < iters; ++t) {
-    GM_CHECK(c, gmmsp::launch_em_pass(gmmsp::LabPacked{c->lab, c->g.W}, c->g, c->gp, c->partials, c->p.precision, c->wpc,
+    GM_CHECK(c, gmmsp::launch_em_pass(gmmsp::LabPlanar{c->lab, (long long)c->g.W * c->g.H, c->g.W}, c->g, c->gp, c->partials, c->p.precision, c->wpc,
                                       c->stream));
-    double* llk_out = c->llk + ((t0 + t) % kLlkCap);
+    double* llk_out = want_ll ? c->llk + ((t0 + t) % kLlkCap) : nullptr;
+    GM_MARK(c);
     GM_CHECK(c, gmmsp::launch_finalize(c->g, c->partials, c->theta, c->gp, c->p.eps_s, c->p.eps_c,
                                        llk_out, c->ws, c->ticket, c->counters, c->p.precision,
                                        c->stream));
+    GM_MARK(c);
   }
   return GMMSP_OK;
 }
 
 gmmsp_status enqueue_labels(gmmsp_ctx c, int32_t* labels, double* llk_out) {
-  GM_CHECK(c, gmmsp::launch_label_pass(gmmsp::LabPacked{c->lab, c->g.W}, c->g, c->gp, labels, c->cell_ll, c->stream));
+  GM_CHECK(c, gmmsp::launch_label_pass(gmmsp::LabPlanar{c->lab, (long long)c->g.W * c->g.H, c->g.W}, c->g, c->gp, labels, c->cell_ll, c->stream));
   if (llk_out)
     GM_CHECK(c, gmmsp::launch_ll_reduce(c->cell_ll, c->g.ncells, llk_out, c->ws, c->ticket, c->g,
                                         c->stream));
+  GM_MARK(c);
   return GMMSP_OK;
 }
 
@@ -187,6 +229,12 @@ gmmsp_status sync_and_check(gmmsp_ctx c) {
 void free_graph(gmmsp_ctx c) {
   if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
   c->graph = Graph();
+}
+
+void free_timing(gmmsp_ctx c) {
+  for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+  c->tev.clear();
+  c->tev_used = 0;
 }
 
 }  // namespace
@@ -247,7 +295,7 @@ gmmsp_status gmmsp_init(gmmsp_ctx* out, const void* image_dev, int width, int he
 
   const size_t N = size_t(width) * height;
   size_t off = 0;
-  const size_t o_lab = off;      off += align_up(N * sizeof(float4));
+  const size_t o_lab = off;      off += align_up(3 * N * sizeof(float));
   const size_t o_theta = off;    off += align_up(size_t(g.K) * gmmsp::kTheta * sizeof(double));
   const size_t o_gp = off;       off += align_up(size_t(g.K) * gmmsp::kGP * sizeof(float));
   const size_t o_part = off;     off += align_up(partial_bytes(g, p->precision));
@@ -264,7 +312,7 @@ gmmsp_status gmmsp_init(gmmsp_ctx* out, const void* image_dev, int width, int he
     return e == cudaErrorMemoryAllocation ? GMMSP_E_NOMEM : GMMSP_E_CUDA;
   }
   char* b = static_cast<char*>(c->slab);
-  c->lab = reinterpret_cast<float4*>(b + o_lab);
+  c->lab = reinterpret_cast<float*>(b + o_lab);
   c->theta = reinterpret_cast<double*>(b + o_theta);
   c->gp = reinterpret_cast<float*>(b + o_gp);
   c->partials = b + o_part;
@@ -305,9 +353,11 @@ gmmsp_status gmmsp_em_iters(gmmsp_ctx c, int iters, double* loglik_host) {
   gmmsp_status st = check_ready(c);
   if (st != GMMSP_OK) return st;
   if (iters < 0) return fail(c, GMMSP_E_INVALID, "iters < 0");
+  c->tev_used = 0;
+  GM_MARK(c);
   for (int done = 0; done < iters; done += kLlkCap) {
     const int n = iters - done < kLlkCap ? iters - done : kLlkCap;
-    st = enqueue_em(c, n, 0);
+    st = enqueue_em(c, n, 0, loglik_host != nullptr);
     if (st != GMMSP_OK) return st;
     if (loglik_host) {
       GM_CHECK(c, cudaMemcpyAsync(loglik_host + done, c->llk, sizeof(double) * n, cudaMemcpyDeviceToHost,
@@ -323,6 +373,8 @@ gmmsp_status gmmsp_labels(gmmsp_ctx c, int32_t* labels_dev, double* loglik_host)
   gmmsp_status st = check_ready(c);
   if (st != GMMSP_OK) return st;
   if (!labels_dev) return fail(c, GMMSP_E_INVALID, "null labels");
+  c->tev_used = 0;
+  GM_MARK(c);
   st = enqueue_labels(c, labels_dev, loglik_host ? c->llk : nullptr);
   if (st != GMMSP_OK) return st;
   if (loglik_host) {
@@ -343,21 +395,24 @@ gmmsp_status gmmsp_segment(gmmsp_ctx c, const void* image_dev, int pitch_bytes, 
   c->state = GMMSP_OK;
   c->err.clear();
   gmmsp_status st;
+  const bool want_ll = loglik_host != nullptr;
   if (c->stream == nullptr) {
     // The legacy default stream cannot be captured: plain launches.
+    c->tev_used = 0;
     st = enqueue_prepare(c, image_dev, pitch_bytes);
-    if (st == GMMSP_OK) st = enqueue_em(c, iters, 0);
-    if (st == GMMSP_OK) st = enqueue_labels(c, labels_dev, c->llk + iters);
+    if (st == GMMSP_OK) st = enqueue_em(c, iters, 0, want_ll);
+    if (st == GMMSP_OK) st = enqueue_labels(c, labels_dev, want_ll ? c->llk + iters : nullptr);
     if (st != GMMSP_OK) return st;
   } else {
     Graph& gr = c->graph;
     if (!(gr.exec && gr.iters == iters && gr.image == image_dev && gr.pitch == pitch_bytes &&
-          gr.labels == labels_dev)) {
+          gr.labels == labels_dev && gr.want_ll == want_ll)) {
       free_graph(c);
+      c->tev_used = 0;
       GM_CHECK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
       st = enqueue_prepare(c, image_dev, pitch_bytes);
-      if (st == GMMSP_OK) st = enqueue_em(c, iters, 0);
-      if (st == GMMSP_OK) st = enqueue_labels(c, labels_dev, c->llk + iters);
+      if (st == GMMSP_OK) st = enqueue_em(c, iters, 0, want_ll);
+      if (st == GMMSP_OK) st = enqueue_labels(c, labels_dev, want_ll ? c->llk + iters : nullptr);
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
       if (st != GMMSP_OK) {
@@ -375,6 +430,7 @@ gmmsp_status gmmsp_segment(gmmsp_ctx c, const void* image_dev, int pitch_bytes, 
       gr.image = image_dev;
       gr.pitch = pitch_bytes;
       gr.labels = labels_dev;
+      gr.want_ll = want_ll;
     }
     GM_CHECK(c, cudaGraphLaunch(gr.exec, c->stream));
   }
@@ -391,13 +447,13 @@ gmmsp_status gmmsp_get_lab(gmmsp_ctx c, float* lab_host) {
   if (st != GMMSP_OK) return st;
   if (!lab_host) return fail(c, GMMSP_E_INVALID, "null output");
   const size_t N = size_t(c->g.W) * c->g.H;
-  std::vector<float4> tmp(N);
-  GM_CHECK(c, cudaMemcpyAsync(tmp.data(), c->lab, N * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<float> tmp(3 * N);
+  GM_CHECK(c, cudaMemcpyAsync(tmp.data(), c->lab, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   GM_CHECK(c, cudaStreamSynchronize(c->stream));
   for (size_t i = 0; i < N; ++i) {
-    lab_host[3 * i + 0] = tmp[i].x;
-    lab_host[3 * i + 1] = tmp[i].y;
-    lab_host[3 * i + 2] = tmp[i].z;
+    lab_host[3 * i + 0] = tmp[i];
+    lab_host[3 * i + 1] = tmp[N + i];
+    lab_host[3 * i + 2] = tmp[2 * N + i];
   }
   return GMMSP_OK;
 }
@@ -501,11 +557,11 @@ gmmsp_status gmmsp_profile_kernel(gmmsp_ctx c, int which, int reps, int32_t* lab
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r], c->stream);
     if (e == cudaSuccess) {
       if (which == GMMSP_KERNEL_EM_PASS)
-        e = gmmsp::launch_em_pass(gmmsp::LabPacked{c->lab, c->g.W}, c->g, c->gp, c->partials, c->p.precision, c->wpc, c->stream);
+        e = gmmsp::launch_em_pass(gmmsp::LabPlanar{c->lab, (long long)c->g.W * c->g.H, c->g.W}, c->g, c->gp, c->partials, c->p.precision, c->wpc, c->stream);
       else if (which == GMMSP_KERNEL_LABELS)
-        e = gmmsp::launch_label_pass(gmmsp::LabPacked{c->lab, c->g.W}, c->g, c->gp, labels_dev, c->cell_ll, c->stream);
+        e = gmmsp::launch_label_pass(gmmsp::LabPlanar{c->lab, (long long)c->g.W * c->g.H, c->g.W}, c->g, c->gp, labels_dev, c->cell_ll, c->stream);
       else
-        e = gmmsp::launch_finalize(c->g, c->partials, c->theta, c->gp, c->p.eps_s, c->p.eps_c, c->llk,
+        e = gmmsp::launch_finalize(c->g, c->partials, c->theta, c->gp, c->p.eps_s, c->p.eps_c, nullptr,
                                    c->ws, c->ticket, c->counters, c->p.precision, c->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r + 1], c->stream);
@@ -571,10 +627,32 @@ gmmsp_status gmmsp_autotune(gmmsp_ctx c, int reps, int* best, double* times_ms) 
   return st;
 }
 
+gmmsp_status gmmsp_set_timing(gmmsp_ctx c, int enable) {
+  if (!c) return GMMSP_E_INVALID;
+  if (bool(enable) != c->timing) free_graph(c);
+  c->timing = enable != 0;
+  c->tev_used = 0;
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_get_timing(gmmsp_ctx c, double* ms, int cap, int* n) {
+  if (!c || !n || (cap > 0 && !ms)) return GMMSP_E_INVALID;
+  GM_CHECK(c, cudaStreamSynchronize(c->stream));
+  const int m = c->tev_used > 0 ? c->tev_used - 1 : 0;
+  *n = m;
+  for (int i = 0; i < m && i < cap; ++i) {
+    float t = 0.f;
+    GM_CHECK(c, cudaEventElapsedTime(&t, c->tev[i], c->tev[i + 1]));
+    ms[i] = t;
+  }
+  return GMMSP_OK;
+}
+
 void gmmsp_destroy(gmmsp_ctx c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   free_graph(c);
+  free_timing(c);
   if (c->slab) cudaFree(c->slab);
   delete c;
 }

@@ -2,28 +2,30 @@
 // finalize with the eigenvalue floor, and the label pass.
 //
 // Work decomposition.  The pixels of one v x v cell share one candidate set
-// (see gmmsp_internal.cuh), so one warp takes one cell: it stages the <= 9
-// candidates' packed parameters in shared memory (read back as warp-wide
-// broadcasts), walks the cell's pixels 32 at a time with one 16-byte load per
-// pixel, and per pixel
-//   E:  evaluates log2 p(z; theta_k) for its candidates (Eq. gaussian with the
-//       block covariance), forms the posteriors R_ik (Eq. Rik) with the
-//       log-sum-exp held in registers, and accumulates ln sum_k p (the
-//       log-likelihood L following Eq. ftheta);
-//   M:  adds R_ik and R_ik d, R_ik d d^T (block-diagonal entries only) into
-//       per-lane FP32 accumulators, d = z - mu_k(old) (the data shifted by
-//       the previous mean so the second moments do not cancel).
-// The 32 lanes' 9 x 15 accumulators are then summed through shared memory
-// (a transpose, so every lane adds up whole rows) and written once per cell
-// as FP64: a block-level partial, with no global atomics.
+// (see gmmsp_internal.cuh), so one warp (or 2 or 4, the autotuned launch
+// shape) takes one cell: it stages the <= 9 candidates' packed parameters in
+// shared memory (read back as warp-wide broadcasts) and walks the cell's
+// pixels 32 at a time:
+//   E:  each lane evaluates log2 p(z; theta_k) of its pixel for the
+//       candidates (Eq. gaussian with the block covariance), forms the
+//       posteriors R_ik (Eq. Rik) with the log-sum-exp held in registers, and
+//       accumulates ln sum_k p (the log-likelihood L following Eq. ftheta);
+//   M:  through shared memory, lane l < 27 adds R_ik, R_ik d and the block
+//       entries of R_ik d d^T of slot l mod 9 over a third of the 32 pixels,
+//       d = z - mu_k(old) (the data shifted by the previous mean so that the
+//       FP32 second moments do not cancel).
+// The per-lane sums are added per slot and per cell in shared memory and
+// written once per cell as FP64: a block-level partial, with no global
+// atomics (k_em_pass).
 //
-// The finalize (one thread per superpixel k, FP64) adds the <= 9 partials of
-// the cells whose candidate set holds k in a fixed order, giving the sums
-// over the pixel set I_k of Eq. (Ik), and turns them into Eq. (UpdateMu),
-// (UpdateSigS) and (UpdateSigC):
+// The finalize adds the <= 9 partials of the cells whose candidate set holds
+// k in a fixed order, giving the sums over the pixel set I_k of Eq. (Ik), and
+// turns them into Eq. (UpdateMu), (UpdateSigS) and (UpdateSigC) in FP64:
 //   mu = mu_old + S1 / W,   Sigma = S2 / W - (S1 / W)(S1 / W)^T,
 // then applies the floor of Eq. (mlams)/(mlamc) and re-packs the E-step
-// coefficients.  A superpixel with W < 1e-8 keeps its parameters.
+// coefficients (k_finalize_l16: 16 lanes per superpixel for small K;
+// k_finalize: one thread per superpixel for large K and the FP32 variant).
+// A superpixel with W < 1e-8 keeps its parameters.
 #include <math.h>
 
 #include "gmmsp_internal.cuh"
@@ -32,7 +34,6 @@
 namespace gmmsp {
 
 constexpr int kEmWarps = 4;          // cells per 128-thread block
-constexpr int kRedRows = 68;         // rows of the reduction buffer (2 halves of 136)
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -107,59 +108,6 @@ __device__ __forceinline__ float log2_density(const float4* P, float fx, float f
   return q;
 }
 
-// One pixel of the fused E + M-partial pass.  fxs[j] / fys[j] are the
-// pixel's coordinates relative to the origin of the candidate cells of
-// column / row j (exact small integers), see rel_coords().
-template <bool FULL, bool SHIFT>
-__device__ __forceinline__ void em_pixel(const float4* sp, unsigned mask, const float (&fxs)[3],
-                                         const float (&fys)[3], float4 z,
-                                         float (&acc)[kSlots * kStats], float& ll) {
-  float e[kSlots];
-  float m = -INFINITY;
-#pragma unroll
-  for (int s = 0; s < kSlots; ++s) {
-    e[s] = 0.f;
-    if (FULL || ((mask >> s) & 1u)) {
-      e[s] = log2_density(sp + 4 * s, fxs[s % 3], fys[s / 3], z);
-      m = fmaxf(m, e[s]);
-    }
-  }
-  float sum = 0.f;
-#pragma unroll
-  for (int s = 0; s < kSlots; ++s) {
-    if (FULL || ((mask >> s) & 1u)) {
-      e[s] = ex2_approx(e[s] - m);
-      sum += e[s];
-    }
-  }
-  const float inv = rcp_approx(sum);
-  ll += m + lg2_approx(sum);
-#pragma unroll
-  for (int s = 0; s < kSlots; ++s) {
-    if (FULL || ((mask >> s) & 1u)) {
-      const float r = e[s] * inv;
-      float dx = fxs[s % 3], dy = fys[s / 3], dL = z.x, da = z.y, db = z.z;
-      if (SHIFT) {
-        const float4 p0 = sp[4 * s], p1 = sp[4 * s + 1];
-        dx -= p0.x; dy -= p0.y; dL -= p0.z; da -= p0.w; db -= p1.x;
-      }
-      float* A = acc + s * kStats;
-      const float rx = r * dx, ry = r * dy, rL = r * dL, ra = r * da, rb = r * db;
-      A[0] += r;
-      A[1] += rx; A[2] += ry; A[3] += rL; A[4] += ra; A[5] += rb;
-      A[6] = fmaf(rx, dx, A[6]);
-      A[7] = fmaf(rx, dy, A[7]);
-      A[8] = fmaf(ry, dy, A[8]);
-      A[9] = fmaf(rL, dL, A[9]);
-      A[10] = fmaf(rL, da, A[10]);
-      A[11] = fmaf(rL, db, A[11]);
-      A[12] = fmaf(ra, da, A[12]);
-      A[13] = fmaf(ra, db, A[13]);
-      A[14] = fmaf(rb, db, A[14]);
-    }
-  }
-}
-
 // Coordinates of pixel (rx, ry) of a cell relative to the cell origins of
 // the candidate columns/rows cx-1, cx, cx+1: rx + v, rx, rx - v.
 __device__ __forceinline__ void rel_coords(int rx, int ry, int v, float (&fxs)[3], float (&fys)[3]) {
@@ -167,114 +115,213 @@ __device__ __forceinline__ void rel_coords(int rx, int ry, int v, float (&fxs)[3
   fys[0] = float(ry + v); fys[1] = float(ry); fys[2] = float(ry - v);
 }
 
-template <bool FULL, bool SHIFT, int LANES, class Src>
-__device__ __forceinline__ void em_cell_pixels(const Src& lab, const Geom& g,
-                                               const Cell& c, const float4* sp, int t,
-                                               float (&acc)[kSlots * kStats], float& ll) {
-  const int npx = c.cw * c.ch;
-  const float inv_cw = 1.f / float(c.cw);
-  // Pixel p of the cell: row floor(p / cw) (exact: (p + 1/2) / cw is at least
-  // 1/(2 cw) away from an integer), column p - row * cw.  The next pixel's
-  // colour is loaded before the current one is processed.
-  auto locate = [&](int p, int& rx, int& ry) {
-    ry = __float2int_rz((float(p) + 0.5f) * inv_cw);
-    rx = p - ry * c.cw;
-  };
-  int p = t, rx = 0, ry = 0;
-  float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (p < npx) {
-    locate(p, rx, ry);
-    z = lab.load(c.x0 + rx, c.y0 + ry);
-  }
-  while (p < npx) {
-    const int pn = p + LANES;
-    int rxn = 0, ryn = 0;
-    float4 zn = z;
-    if (pn < npx) {
-      locate(pn, rxn, ryn);
-      zn = lab.load(c.x0 + rxn, c.y0 + ryn);
+// E part for one pixel: the posteriors of its candidates (Eq. Rik) into
+// R[0..8] (zero for slots off the grid) and ln-sum-exp in log2 units into ll.
+template <bool FULL>
+__device__ __forceinline__ void e_pixel(const float4* sp, unsigned mask, const float (&fxs)[3],
+                                        const float (&fys)[3], float4 z, float (&R)[kSlots],
+                                        float& ll) {
+  float m = -INFINITY;
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    R[s] = 0.f;
+    if (FULL || ((mask >> s) & 1u)) {
+      R[s] = log2_density(sp + 4 * s, fxs[s % 3], fys[s / 3], z);
+      m = fmaxf(m, R[s]);
     }
-    float fxs[3], fys[3];
-    rel_coords(rx, ry, g.v, fxs, fys);
-    em_pixel<FULL, SHIFT>(sp, c.mask, fxs, fys, z, acc, ll);
-    p = pn; rx = rxn; ry = ryn; z = zn;
   }
+  float sum = 0.f;
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    if (FULL || ((mask >> s) & 1u)) {
+      R[s] = ex2_approx(R[s] - m);
+      sum += R[s];
+    }
+  }
+  const float inv = rcp_approx(sum);
+  ll += m + lg2_approx(sum);
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) R[s] *= inv;
 }
 
 // Fused E-step + M-step partial sums.  PT = double (mixed precision, shifted
 // moments) or float (all-FP32 variant, raw moments).  WPC warps share one
-// cell (more parallelism for small images); a 128-thread block holds
-// 4 / WPC cells.  The WPC x 32 per-thread accumulator sets of a cell are
-// summed through shared memory: every thread writes its column of a
-// 68-row tile (two tiles for the 136 sums), then each thread adds up whole rows.
+// cell; a 128-thread block holds 4 / WPC cells.
+//
+// Each warp walks its share of the cell 32 pixels at a time.  Every lane
+// takes one pixel through the E part (its <= 9 posteriors and its
+// log-likelihood) and leaves the posteriors and the pixel's colour and
+// position in shared memory.  Then lane l < 27 accumulates the 15 statistics
+// of slot s = l mod 9 over every third pixel of the 32 (pixels l / 9,
+// l / 9 + 3, ...), with d = z - mu_s(old): each lane holds 15 accumulators
+// instead of 9 x 15, which keeps the register count (and so the occupancy)
+// of the kernel independent of the candidate count.  At the end the three
+// lanes of each slot, then the WPC warps, are added through shared memory and
+// written once per cell as FP64 (no global atomics).
+constexpr int kRStride = 12;  // floats per pixel row of posteriors
+
+template <int WPC>
+struct EmSmem {
+  float4 sp[kEmWarps / WPC][kSlots * 4];            // candidate parameters per cell
+  float R[kEmWarps][32 * kRStride];                 // posteriors of the 32 pixels in flight
+  float4 Z[kEmWarps][32];                           // (L, a, b, -) of those pixels
+  float2 XY[kEmWarps][32];                          // their position in the cell
+  float part[kEmWarps][kSlots * kStats + 1 + 3];    // per-warp sums (row 135: log-likelihood)
+  float red[kEmWarps][27][kStats + 1];              // per-lane sums before the 3-lane add
+};
+
+template <int WPC>
+constexpr int em_smem_bytes() { return int(sizeof(EmSmem<WPC>)); }
+
+template <bool FULL, bool SHIFT, int WPC, class Src>
+__device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, const Cell& c,
+                                             EmSmem<WPC>& sm, int slot, int warp, int lane, int wic,
+                                             float (&acc)[kStats], float& ll) {
+  const int npx = c.cw * c.ch;
+  const float inv_cw = 1.f / float(c.cw);
+  const float4* sp = sm.sp[slot];
+  float* Rw = sm.R[warp];
+  float4* Zw = sm.Z[warp];
+  float2* XYw = sm.XY[warp];
+  // M-part role of this lane: slot ms, pixel phase ph (lanes 27-31 idle there)
+  const int ms = lane % 9, ph = lane / 9;
+  const bool m_on = lane < 27 && (FULL || ((c.mask >> ms) & 1u));
+  float cx = 0.f, cy = 0.f, mL = 0.f, ma = 0.f, mb = 0.f;
+  {
+    const float4 p0 = sp[4 * ms], p1 = sp[4 * ms + 1];
+    // d_x = rx + (1 - ms % 3) v - mu_x (mu_x relative to the candidate's cell origin)
+    cx = float((1 - ms % 3) * g.v) - (SHIFT ? p0.x : 0.f);
+    cy = float((1 - ms / 3) * g.v) - (SHIFT ? p0.y : 0.f);
+    if (SHIFT) { mL = p0.z; ma = p0.w; mb = p1.x; }
+  }
+  // The colour of this lane's next pixel is loaded one batch ahead.
+  auto locate = [&](int p, int& rx, int& ry) {
+    ry = __float2int_rz((float(p) + 0.5f) * inv_cw);  // exact floor(p / cw)
+    rx = p - ry * c.cw;
+  };
+  float4 zn = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (wic * 32 + lane < npx) {
+    int rx0, ry0;
+    locate(wic * 32 + lane, rx0, ry0);
+    zn = lab.load(c.x0 + rx0, c.y0 + ry0);
+  }
+  for (int base = wic * 32; base < npx; base += 32 * WPC) {
+    const int p = base + lane;
+    float R[kSlots];
+    const float4 z = zn;
+    if (p + 32 * WPC < npx) {
+      int rx1, ry1;
+      locate(p + 32 * WPC, rx1, ry1);
+      zn = lab.load(c.x0 + rx1, c.y0 + ry1);
+    }
+    int rx = 0, ry = 0;
+    if (p < npx) {
+      locate(p, rx, ry);
+      float fxs[3], fys[3];
+      rel_coords(rx, ry, g.v, fxs, fys);
+      e_pixel<FULL>(sp, c.mask, fxs, fys, z, R, ll);
+    } else {
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) R[s] = 0.f;
+    }
+    float4* rrow = reinterpret_cast<float4*>(Rw + lane * kRStride);
+    rrow[0] = make_float4(R[0], R[1], R[2], R[3]);
+    rrow[1] = make_float4(R[4], R[5], R[6], R[7]);
+    Rw[lane * kRStride + 8] = R[8];
+    Zw[lane] = z;
+    XYw[lane] = make_float2(float(rx), float(ry));
+    __syncwarp();
+    if (m_on) {
+      const int np = min(32, npx - base);
+#pragma unroll 4
+      for (int q = ph; q < np; q += 3) {
+        const float r = Rw[q * kRStride + ms];
+        const float2 xy = XYw[q];
+        const float4 zz = Zw[q];
+        const float dx = xy.x + cx, dy = xy.y + cy;
+        const float dL = zz.x - mL, da = zz.y - ma, db = zz.z - mb;
+        const float rxd = r * dx, ryd = r * dy, rL = r * dL, ra = r * da, rb = r * db;
+        acc[0] += r;
+        acc[1] += rxd; acc[2] += ryd; acc[3] += rL; acc[4] += ra; acc[5] += rb;
+        acc[6] = fmaf(rxd, dx, acc[6]);
+        acc[7] = fmaf(rxd, dy, acc[7]);
+        acc[8] = fmaf(ryd, dy, acc[8]);
+        acc[9] = fmaf(rL, dL, acc[9]);
+        acc[10] = fmaf(rL, da, acc[10]);
+        acc[11] = fmaf(rL, db, acc[11]);
+        acc[12] = fmaf(ra, da, acc[12]);
+        acc[13] = fmaf(ra, db, acc[13]);
+        acc[14] = fmaf(rb, db, acc[14]);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <typename PT, bool SHIFT, int WPC, class Src>
-__global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(Src lab, Geom g,
-                                                           const float* __restrict__ gp,
+__global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(Src lab, Geom g, const float* __restrict__ gp,
                                                            PT* __restrict__ partials) {
-  constexpr int kLanes = 32 * WPC;             // threads per cell
   constexpr int kCellsPerBlock = kEmWarps / WPC;
-  constexpr int kLd = kLanes + 1;              // padded row: conflict-free transposes
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  EmSmem<WPC>& sm = *reinterpret_cast<EmSmem<WPC>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int slot = warp / WPC;                 // cell slot within the block
-  const int t = (warp % WPC) * 32 + lane;      // thread index within the cell
-  float4* sp = reinterpret_cast<float4*>(smem_raw) + slot * (kSlots * 4);
-  float* red = reinterpret_cast<float*>(smem_raw + kCellsPerBlock * kSlots * 4 * 16) +
-               slot * (kRedRows * kLd);
+  const int slot = warp / WPC;       // cell slot within the block
+  const int wic = warp % WPC;        // warp index within the cell
+  const int t = wic * 32 + lane;     // thread index within the cell
   const int cell = blockIdx.x * kCellsPerBlock + slot;
-  const bool active = cell < g.ncells;         // inactive threads still reach every barrier
+  const bool active = cell < g.ncells;  // inactive threads still reach every barrier
   Cell c = {};
+  if (active) c = make_cell(g, cell);
+  pdl_wait();  // gp and the image are written by the preceding kernels
+  pdl_trigger();
   if (active) {
-    c = make_cell(g, cell);
-    for (int i = t; i < kSlots * 4; i += kLanes) {
+    for (int i = t; i < kSlots * 4; i += 32 * WPC) {
       const int s = i >> 2, q = i & 3;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if ((c.mask >> s) & 1u) {
         const int k = (c.cy - 1 + s / 3) * g.nx + (c.cx - 1 + s % 3);
         v = __ldg(reinterpret_cast<const float4*>(gp) + k * 4 + q);
       }
-      sp[i] = v;
+      sm.sp[slot][i] = v;
     }
   }
   if (WPC == 1) __syncwarp(); else __syncthreads();
 
-  float acc[kSlots * kStats];
+  float acc[kStats];
 #pragma unroll
-  for (int j = 0; j < kSlots * kStats; ++j) acc[j] = 0.f;
+  for (int j = 0; j < kStats; ++j) acc[j] = 0.f;
   float ll = 0.f;
   if (active) {
     if (c.mask == 0x1ffu)
-      em_cell_pixels<true, SHIFT, kLanes, Src>(lab, g, c, sp, t, acc, ll);
+      em_cell_warp<true, SHIFT, WPC, Src>(lab, g, c, sm, slot, warp, lane, wic, acc, ll);
     else
-      em_cell_pixels<false, SHIFT, kLanes, Src>(lab, g, c, sp, t, acc, ll);
+      em_cell_warp<false, SHIFT, WPC, Src>(lab, g, c, sm, slot, warp, lane, wic, acc, ll);
   }
-
-  // Row 135 carries the log-likelihood (log2 units until written).
-  PT* out = partials + (long long)cell * kPartStride;
+  // Per-warp totals: add the three lanes of each slot, and the lanes' log-likelihoods.
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+  if (lane < 27) {
 #pragma unroll
-    for (int j = 0; j < kRedRows; ++j) {
-      const int row = h * kRedRows + j;
-      red[j * kLd + t] = (row < kSlots * kStats) ? acc[row] : ll;
-    }
-    if (WPC == 1) __syncwarp(); else __syncthreads();
-    if (active) {
-      for (int j = t; j < kRedRows; j += kLanes) {
-        float s = 0.f;
-#pragma unroll 8
-        for (int q = 0; q < kLanes; ++q) s += red[j * kLd + q];
-        const int row = h * kRedRows + j;
-        out[row] = (row < kSlots * kStats) ? PT(s) : PT(s) * PT(0.69314718055994530942);
-      }
-    }
-    if (WPC == 1) __syncwarp(); else __syncthreads();
+    for (int j = 0; j < kStats; ++j) sm.red[warp][lane][j] = acc[j];
   }
-}
-
-template <int WPC>
-constexpr int em_smem_bytes() {
-  return (kEmWarps / WPC) * (kSlots * 4 * 16 + kRedRows * (32 * WPC + 1) * 4);
+  __syncwarp();
+  for (int o = lane; o < kSlots * kStats; o += 32) {
+    const int s = o / kStats, j = o - s * kStats;
+    sm.part[warp][o] = sm.red[warp][s][j] + sm.red[warp][s + 9][j] + sm.red[warp][s + 18][j];
+  }
+  if (lane == 0) sm.part[warp][kSlots * kStats] = ll;
+  if (WPC == 1) __syncwarp(); else __syncthreads();
+  // Cell totals (sum over the WPC warps of the cell), written as PT.
+  if (active) {
+    PT* out = partials + (long long)cell * kPartStride;
+    const int w0 = slot * WPC;
+    for (int o = t; o < kPartStride; o += 32 * WPC) {
+      float v = sm.part[w0][o];
+#pragma unroll
+      for (int w = 1; w < WPC; ++w) v += sm.part[w0 + w][o];
+      out[o] = (o < kSlots * kStats) ? PT(v) : PT(v) * PT(0.69314718055994530942);
+    }
+  }
 }
 
 // Label pass: argmax posterior per pixel (ties to the smaller k, i.e. the
@@ -319,6 +366,8 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass(Src lab, Geom g, c
   __shared__ float4 sp_all[kEmWarps][kSlots * 4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cell = blockIdx.x * kEmWarps + warp;
+  pdl_wait();
+  pdl_trigger();
   if (cell >= g.ncells) return;
   const Cell c = make_cell(g, cell);
   float4* sp = sp_all[warp];
@@ -339,17 +388,17 @@ constexpr int kFinThreads = 32;  // one warp per block: spreads small K over mor
 // Deterministic sum of the per-cell log-likelihoods: each block adds a fixed
 // strided subset and a tree, the last block to finish adds the block sums in
 // block order (one atomic ticket; no thread waits on another).
-template <typename PT>
+template <typename PT, int NT>
 __device__ void block_ll_sum(const PT* vals, long long stride, int n, double* blk, unsigned* ticket,
                              double* out) {
-  __shared__ double red[kFinThreads];
+  __shared__ double red[NT];
   __shared__ bool last;
   double s = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT)
     s += double(vals[(long long)i * stride]);
   red[threadIdx.x] = s;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+  for (int w = NT / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
@@ -359,12 +408,22 @@ __device__ void block_ll_sum(const PT* vals, long long stride, int n, double* bl
     last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  // The last block adds the block sums: thread t takes blocks t, t + NT, ...,
+  // then a tree (FP64 adds are slow on this part: keep the chain short).
+  if (last) {
     __threadfence();
     double t = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) t += *((volatile double*)&blk[b]);
-    *out = t;
-    *ticket = 0u;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) t += *((volatile double*)&blk[b]);
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = NT / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      *out = red[0];
+      *ticket = 0u;
+    }
   }
 }
 
@@ -377,7 +436,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Geom g, const PT* __re
                                                           unsigned long long* counters) {
   using T = PT;  // arithmetic type of the update: double, or float for the FP32 variant
   constexpr bool kShifted = sizeof(PT) == 8;
-  if (llk_out) block_ll_sum<PT>(partials + kSlots * kStats, kPartStride, g.ncells, blk, ticket, llk_out);
+  pdl_wait();
+  pdl_trigger();
+  if (llk_out)
+    block_ll_sum<PT, kFinThreads>(partials + kSlots * kStats, kPartStride, g.ncells, blk, ticket, llk_out);
 
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned dead = 0, rs = 0, rc = 0;
@@ -456,15 +518,251 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Geom g, const PT* __re
   }
 }
 
+// Finalize for small K (mixed precision): 16 lanes per superpixel.  On
+// GB300 an FP64 warp instruction occupies its SM sub-partition for ~64
+// clocks whatever the number of active lanes, so the latency of a small
+// finalize is the count of FP64 instructions on one warp's path.  Here the
+// lanes of a half-warp share one superpixel and evaluate the independent
+// pieces side by side with one instruction, reading their operands through a
+// per-superpixel shared-memory array and small index tables:
+//   lane j < 15 adds statistic j over the <= 9 cells holding k;
+//   lanes 0-8 form the moment entries M (Sigma_s: xx xy yy, Sigma_c: LL La Lb
+//   aa ab bb); lanes 0-6 form the 2x2 products-minus-products that the floor
+//   test, the characteristic cubic, the projector and the adjugate need;
+//   lanes 5-13 scale the packed coefficients.
+// The floor itself (Eq. mlams/mlamc) is decided by Sylvester's criterion on
+// Sigma - eps I; a raised colour eigenvalue starts from the FP32 Smith
+// solution and takes one FP64 Newton step on the cubic, and the floored block
+// is Sigma + (eps - l1) P1 or eps I + (l3 - eps) P3 with the projector a
+// polynomial in Sigma (see gmmsp_math.cuh).
+constexpr int kFin16Threads = 64;  // 4 superpixels per block
+
+__device__ __forceinline__ int nib(unsigned long long table, int i) {
+  return int((table >> (4 * i)) & 0xFull);
+}
+
+// FP64 1/x from the MUFU FP32 estimate (relative error < 2^-22) and one
+// FP64 Newton step (relative error < 2^-44).
+__device__ __forceinline__ double rcp64(double x) {
+  float r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(float(x)));
+  const double r = double(r0);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
+// x > 0 for a finite double, tested on its bits (integer pipe, not FP64).
+__device__ __forceinline__ bool dpos(double x) { return __double_as_longlong(x) > 0; }
+
+__global__ void __launch_bounds__(kFin16Threads) k_finalize_l16(Geom g, const double* __restrict__ partials,
+                                                              double* __restrict__ theta,
+                                                              float* __restrict__ gp, double eps_s,
+                                                              double eps_c, double* llk_out, double* blk,
+                                                              unsigned* ticket,
+                                                              unsigned long long* counters) {
+  __shared__ double sh[kFin16Threads / 16][48];
+  __shared__ float shf[kFin16Threads / 16][8];
+  pdl_wait();
+  pdl_trigger();
+  if (llk_out)
+    block_ll_sum<double, kFin16Threads>(partials + kSlots * kStats, kPartStride, g.ncells, blk, ticket,
+                                        llk_out);
+  constexpr unsigned kFull = 0xffffffffu;
+  const int l = threadIdx.x & 15, q = threadIdx.x >> 4;
+  double* X = sh[q];   // [0..14] sums, [16..20] d, [21..29] M, [30..36] products, [37..45] scratch
+  float* F = shf[q];
+  const int k = blockIdx.x * (kFin16Threads / 16) + q;
+  const bool valid = k < g.K;
+  const int kk = valid ? k : 0;
+  const int kx = kk % g.nx, ky = kk / g.nx;
+
+  // 1. Sums over the pixel set I_k: lane l < 15 adds statistic l of the <= 9
+  //    cells holding k (cell (kx+dx, ky+dy) holds k in slot (1-dy)*3+(1-dx)).
+  {
+    double v[9];
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int cy = ky + dy, cx = kx + dx;
+        const bool in = valid && l < kStats && cy >= 0 && cy < g.ncy && cx >= 0 && cx < g.ncx;
+        v[(dy + 1) * 3 + (dx + 1)] =
+            in ? __ldg(partials + (long long)(cy * g.ncx + cx) * kPartStride +
+                       ((1 - dy) * 3 + (1 - dx)) * kStats + l)
+               : 0.0;
+      }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) s += v[j];
+    if (l < kStats) X[l] = s;
+  }
+  __syncwarp();
+  const double Wk = X[ST_W];
+  // reading: no weight -> theta_k kept (positive doubles order like their bits)
+  const bool live = valid && __double_as_longlong(Wk) >= __double_as_longlong(1e-8);
+  const double iw = rcp64(live ? Wk : 1.0);
+  if (l < 5) X[16 + l] = X[ST_S1 + l] * iw;  // d = S1 / W
+  __syncwarp();
+  // 2. Moments about the new mean: M_e = S2_e / W - d_a d_b.
+  if (l < 9)
+    X[21 + l] = fma(-X[16 + nib(0x433222100ull, l)], X[16 + nib(0x443432110ull, l)], X[ST_S2S + l] * iw);
+  // new mean (lanes 0-4): mu_ref + d, mu_ref being the FP32 mean the E-step used
+  float* G = gp + (long long)kk * kGP;
+  const double org = (l == 0) ? double(kx * g.v) : (l == 1 ? double(ky * g.v) : 0.0);
+  const double mu_l = org + (double(G[l < 5 ? l : 0]) + X[16 + (l < 5 ? l : 0)]);
+  __syncwarp();
+
+  // 3. Floor test (Sylvester on M - eps I).  E = M with shifted diagonals in
+  //    X[37..45]; products (lane j): 0 c00' 1 unused 2 m2 3 c01' 4 c02' 5 det2 spatial.
+  if (l < 9) {
+    const double sft = (l == 0 || l == 2) ? eps_s : ((l == 3 || l == 6 || l == 8) ? eps_c : 0.0);
+    X[37 + l] = X[21 + l] - sft;
+  }
+  __syncwarp();
+  //            lane:  6 5 4 3 2 1 0
+  // p (E index)        . 0 4 5 3 3 6      q: . 2 7 7 6 8 8
+  // r                  . 1 5 4 4 5 7      t: . 1 6 8 4 5 7
+  if (l < 6) {
+    const double* E = X + 37;
+    X[30 + l] = fma(E[nib(0x045336ull, l)], E[nib(0x277688ull, l)],
+                    -E[nib(0x154457ull, l)] * E[nib(0x168457ull, l)]);
+  }
+  __syncwarp();
+  bool need_s, need_c;
+  {
+    const double* E = X + 37;
+    const double m3 = fma(E[3], X[30], fma(E[4], X[33], E[5] * X[34]));
+    need_c = live && !(dpos(E[3]) && dpos(X[32]) && dpos(m3));
+    need_s = live && !(dpos(E[0]) && dpos(X[35]));
+  }
+  int rc = 0, rs = 0;
+  __syncwarp();
+  if (__any_sync(kFull, need_c)) {
+    // Characteristic cubic lambda^3 - c2 lambda^2 + c1 lambda - c0 of the colour
+    // block: products (lane j < 5) M00 M11 M22 c01 c02 of M.
+    if (l < 5) {
+      const double* A = X + 21;
+      X[30 + l] = fma(A[nib(0x45336ull, l)], A[nib(0x77688ull, l)], -A[nib(0x54457ull, l)] * A[nib(0x68457ull, l)]);
+    }
+    if (l < 6) F[l] = float(X[24 + l]);
+    __syncwarp();
+    const double a00 = X[24], a01 = X[25], a02 = X[26], a11 = X[27], a22 = X[29];
+    const double c2 = a00 + a11 + a22;
+    const double c1 = X[30] + X[31] + X[32];
+    const double c0 = fma(a00, X[30], fma(a01, X[33], a02 * X[34]));
+    float f1, f2, f3;
+    eig3_seed(F[0], F[1], F[2], F[3], F[4], F[5], f1, f2, f3);
+    const float fe = float(eps_c);
+    const int n = (f1 < fe) + (f2 < fe) + (f3 < fe);
+    const double scale = fabs(double(f3)) + eps_c;
+    const bool degenerate = n == 3 || double(f3) - double(f1) <= 1e-6 * scale;
+    double lj = double(n == 1 ? f1 : f3);
+    {
+      const double pv = fma(fma(lj - c2, lj, c1), lj, -c0);
+      const double dp0 = fma(fma(3.0, lj, -2.0 * c2), lj, c1);
+      float r;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(float(dp0)));
+      if (fabs(dp0) > 1e-12 * scale * scale) lj = fma(-pv, double(r), lj);
+    }
+    const double dp = fma(fma(3.0, lj, -2.0 * c2), lj, c1);  // (lj - la)(lj - lb)
+    const double sum = c2 - lj, prod = fma(-lj, sum, c1);
+    const bool flat = degenerate || !(fabs(dp) > 1e-12 * scale * scale);
+    const double gnum = (n == 1) ? eps_c - lj : lj - eps_c;
+    const double gk = gnum * rcp64(flat ? 1.0 : dp);
+    // Projector entry j (lanes 0-5, order LL La Lb aa ab bb):
+    //   (A^2)_j - sum A_j + prod [j diagonal]; A^2_j = row_r . col_c (3 terms).
+    double newA = 0.0;
+    if (l < 6) {
+      const double* A = X + 24;
+      // (A^2)_j = sum_m A[r][m] A[m][c] with (r, c) of entry j
+      const int rr = nib(0x211000ull, l), cc_ = nib(0x221210ull, l);
+      auto idx = [](int a, int b) {  // packed index of A[a][b]
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+      };
+      double a2 = 0.0;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) a2 = fma(A[idx(rr, m)], A[idx(m, cc_)], a2);
+      const bool diag = (l == 0 || l == 3 || l == 5);
+      const double P = fma(-sum, A[l], a2) + (diag ? prod : 0.0);
+      const double base = (n == 1) ? A[l] : (diag ? eps_c : 0.0);
+      newA = flat ? (diag ? (n == 3 ? eps_c : fmax(c2 / 3.0, eps_c)) : 0.0) : fma(gk, P, base);
+    }
+    __syncwarp();
+    if (need_c && l < 6) X[24 + l] = newA;
+    rc = need_c ? n : 0;
+  }
+  __syncwarp();
+  if (need_s) {  // spatial floor: rare (eigenvalues ~ v^2 / 12 against eps_s = 2)
+    double cs[3] = {X[21], X[22], X[23]};
+    rs = clamp_sym2<double>(cs, eps_s);
+    __syncwarp(__activemask());
+    if (l < 3) X[21 + l] = cs[l];
+  }
+  __syncwarp();
+
+  // 4. Pack: colour cofactors and the spatial determinant (lanes 0-6):
+  //    0 c00 1 c01 2 c02 3 c11 4 c12 5 c22 6 ds (indices into M = X[21..29]).
+  if (l < 7) {
+    const double* M = X + 21;
+    X[30 + l] = fma(M[nib(0x0343456ull, l)], M[nib(0x2658778ull, l)],
+                    -M[nib(0x1435547ull, l)] * M[nib(0x1475687ull, l)]);
+  }
+  __syncwarp();
+  const double dc = fma(X[24], X[30], fma(X[25], X[31], X[26] * X[32]));
+  const double ds = X[36];
+  const bool pd = dpos(X[21]) && dpos(ds) && dpos(X[24]) && dpos(X[35]) && dpos(dc);
+  const double idet = rcp64((l & 1) ? (dpos(dc) ? dc : 1.0) : (dpos(ds) ? ds : 1.0));
+  const double ids = __shfl_sync(kFull, idet, 0, 16), idc = __shfl_sync(kFull, idet, 1, 16);
+  // Coefficient lane l in 5..13: factor * numerator, numerators
+  //   5 yy 6 xy 7 xx (from M) | 8 c00 9 c11 10 c22 11 c01 12 c02 13 c12 (from X[30..])
+  float out = 0.f;
+  {
+    const int li = l < 5 ? 5 : (l > 13 ? 13 : l);
+    const int j = li - 5;
+    const bool spatial = j < 3;
+    const double num = spatial ? X[21 + nib(0x012ull, j)] : X[30 + nib(0x421530ull, j - 3 < 0 ? 0 : j - 3)];
+    const double mult = spatial ? (j == 1 ? -2.0 : 1.0) : (j >= 6 ? 2.0 : 1.0);
+    const double coef = (-0.5 * Num<double>::kLog2e * mult) * (spatial ? ids : idc) * num;
+    if (l >= 5 && l <= 13) out = float(coef);
+  }
+  if (l < 5) out = float(mu_l - org);
+  if (l == 14)
+    out = -0.5f * (Num<double>::log2_(dpos(ds) ? ds : 1.0) + Num<double>::log2_(dpos(dc) ? dc : 1.0)) -
+          float(Num<double>::kHalfD_Log2_2Pi);
+  if (live && pd) {
+    G[l] = out;
+    // theta: [0..4] mu, [5..7] Sigma_s, [8..13] Sigma_c (= M in order)
+    if (l < 14) theta[(long long)kk * kTheta + l] = (l < 5) ? mu_l : X[21 + (l - 5)];
+  }
+  unsigned dead = (valid && !live && l == 0) ? 1u : 0u;
+  unsigned urs = (live && l == 0) ? unsigned(rs) : 0u, urc = (live && l == 0) ? unsigned(rc) : 0u;
+  dead = __reduce_add_sync(kFull, dead);
+  urs = __reduce_add_sync(kFull, urs);
+  urc = __reduce_add_sync(kFull, urc);
+  if ((threadIdx.x & 31) == 0) {
+    if (dead) atomicAdd(&counters[CNT_DEAD], (unsigned long long)dead);
+    if (urs) atomicAdd(&counters[CNT_RAISED_S], (unsigned long long)urs);
+    if (urc) atomicAdd(&counters[CNT_RAISED_C], (unsigned long long)urc);
+  }
+}
+
 __global__ void __launch_bounds__(kFinThreads) k_ll_reduce(const double* __restrict__ cell_ll, int n,
                                                            double* blk, unsigned* ticket, double* out) {
-  block_ll_sum<double>(cell_ll, 1, n, blk, ticket, out);
+  pdl_wait();
+  pdl_trigger();
+  block_ll_sum<double, kFinThreads>(cell_ll, 1, n, blk, ticket, out);
 }
 
 // ---------------------------------------------------------------- launchers
 static int ll_blocks(const Geom& g) { return (g.K + kFinThreads - 1) / kFinThreads; }
 
-size_t finalize_workspace_doubles(const Geom& g) { return size_t(ll_blocks(g)) + 1; }
+// Superpixel count up to which the 16-lane finalize is used.
+constexpr int kFin16MaxK = 4096;
+
+size_t finalize_workspace_doubles(const Geom& g) {
+  const size_t b16 = size_t((g.K + kFin16Threads / 16 - 1) / (kFin16Threads / 16));
+  return (b16 > size_t(ll_blocks(g)) ? b16 : size_t(ll_blocks(g))) + 1;
+}
 
 template <typename PT, bool SHIFT, int WPC, class Src>
 static cudaError_t em_pass_impl(Src lab, const Geom& g, const float* gp, PT* partials,
@@ -480,8 +778,8 @@ static cudaError_t em_pass_impl(Src lab, const Geom& g, const float* gp, PT* par
   }
   constexpr int cpb = kEmWarps / WPC;
   const int blocks = (g.ncells + cpb - 1) / cpb;
-  k_em_pass<PT, SHIFT, WPC, Src><<<blocks, kEmWarps * 32, smem, s>>>(lab, g, gp, partials);
-  return cudaGetLastError();
+  return launch_pdl(k_em_pass<PT, SHIFT, WPC, Src>, dim3(blocks), dim3(kEmWarps * 32), smem, s, lab, g,
+                    gp, partials);
 }
 
 template <typename PT, bool SHIFT, class Src>
@@ -506,15 +804,15 @@ template <class Src>
 cudaError_t launch_label_pass(Src lab, const Geom& g, const float* gp, int32_t* labels,
                               double* cell_ll, cudaStream_t s) {
   const int blocks = (g.ncells + kEmWarps - 1) / kEmWarps;
-  k_label_pass<Src><<<blocks, kEmWarps * 32, 0, s>>>(lab, g, gp, labels, cell_ll);
-  return cudaGetLastError();
+  return launch_pdl(k_label_pass<Src>, dim3(blocks), dim3(kEmWarps * 32), 0, s, lab, g, gp, labels,
+                    cell_ll);
 }
 
-template cudaError_t launch_em_pass<LabPacked>(LabPacked, const Geom&, const float*, void*, int, int,
+template cudaError_t launch_em_pass<LabPlanar>(LabPlanar, const Geom&, const float*, void*, int, int,
                                                cudaStream_t);
 template cudaError_t launch_em_pass<LabPitched>(LabPitched, const Geom&, const float*, void*, int, int,
                                                 cudaStream_t);
-template cudaError_t launch_label_pass<LabPacked>(LabPacked, const Geom&, const float*, int32_t*, double*,
+template cudaError_t launch_label_pass<LabPlanar>(LabPlanar, const Geom&, const float*, int32_t*, double*,
                                                   cudaStream_t);
 template cudaError_t launch_label_pass<LabPitched>(LabPitched, const Geom&, const float*, int32_t*,
                                                    double*, cudaStream_t);
@@ -523,20 +821,25 @@ cudaError_t launch_finalize(const Geom& g, const void* partials, double* theta, 
                             double eps_s, double eps_c, double* llk_out, double* ws,
                             unsigned* ticket, unsigned long long* counters, int precision,
                             cudaStream_t s) {
+  if (precision != 1 && g.K <= kFin16MaxK) {
+    const int blocks16 = (g.K + kFin16Threads / 16 - 1) / (kFin16Threads / 16);
+    return launch_pdl(k_finalize_l16, dim3(blocks16), dim3(kFin16Threads), 0, s, g,
+                      static_cast<const double*>(partials), theta, gp, eps_s, eps_c, llk_out, ws, ticket,
+                      counters);
+  }
   const int blocks = ll_blocks(g);
   if (precision == 1)
-    k_finalize<float><<<blocks, kFinThreads, 0, s>>>(g, static_cast<const float*>(partials), theta, gp,
-                                                     eps_s, eps_c, llk_out, ws, ticket, counters);
-  else
-    k_finalize<double><<<blocks, kFinThreads, 0, s>>>(g, static_cast<const double*>(partials), theta,
-                                                      gp, eps_s, eps_c, llk_out, ws, ticket, counters);
-  return cudaGetLastError();
+    return launch_pdl(k_finalize<float>, dim3(blocks), dim3(kFinThreads), 0, s, g,
+                      static_cast<const float*>(partials), theta, gp, eps_s, eps_c, llk_out, ws, ticket,
+                      counters);
+  return launch_pdl(k_finalize<double>, dim3(blocks), dim3(kFinThreads), 0, s, g,
+                    static_cast<const double*>(partials), theta, gp, eps_s, eps_c, llk_out, ws, ticket,
+                    counters);
 }
 
 cudaError_t launch_ll_reduce(const double* cell_ll, int n, double* out, double* ws, unsigned* ticket,
                              const Geom& g, cudaStream_t s) {
-  k_ll_reduce<<<ll_blocks(g), kFinThreads, 0, s>>>(cell_ll, n, ws, ticket, out);
-  return cudaGetLastError();
+  return launch_pdl(k_ll_reduce, dim3(ll_blocks(g)), dim3(kFinThreads), 0, s, cell_ll, n, ws, ticket, out);
 }
 
 }  // namespace gmmsp

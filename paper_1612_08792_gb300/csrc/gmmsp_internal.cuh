@@ -52,10 +52,14 @@ struct Geom {
 };
 
 // Where the kernels read the CIELAB colour of pixel (x, y) from.
-struct LabPacked {  // the context's image: one float4 (L, a, b, 0) per pixel
-  const float4* p;
+struct LabPlanar {  // the context's image: three float32 planes L, a, b of W H pixels
+  const float* p;     // plane L; plane a at p + plane, plane b at p + 2 plane
+  long long plane;
   int W;
-  __device__ __forceinline__ float4 load(int x, int y) const { return __ldg(p + (long long)y * W + x); }
+  __device__ __forceinline__ float4 load(int x, int y) const {
+    const long long i = (long long)y * W + x;
+    return make_float4(__ldg(p + i), __ldg(p + plane + i), __ldg(p + 2 * plane + i), 0.f);
+  }
 };
 struct LabPitched {  // a caller's image: rows of (L, a, b) float32, row pitch in bytes
   const char* p;
@@ -66,13 +70,41 @@ struct LabPitched {  // a caller's image: rows of (L, a, b) float32, row pitch i
   }
 };
 
+// Programmatic dependent launch.  Kernels of the pipeline are launched with
+// cudaLaunchAttributeProgrammaticStreamSerialization: each one lets its
+// successor start launching at entry (pdl_trigger), and waits for its
+// predecessor's completion and memory (pdl_wait, griddepcontrol.wait, a
+// hardware wait) just before it reads what the predecessor wrote.  Without a
+// programmatic predecessor pdl_wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+bool pdl_enabled();  // true only when GMMSP_PDL=1 is set in the environment
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Device counters (unsigned long long): dead, raised_s, raised_c, nonfinite input.
 enum : int { CNT_DEAD = 0, CNT_RAISED_S = 1, CNT_RAISED_C = 2, CNT_NONFINITE = 3, CNT_N = 4 };
 
 // ---- launchers (each returns the launch's cudaError_t) ----
-cudaError_t launch_rgb2lab(const uint8_t* img, long long pitch, const Geom& g, float4* lab,
+// lab: three planes of W H floats (L, a, b), plane stride W H.
+cudaError_t launch_rgb2lab(const uint8_t* img, long long pitch, const Geom& g, float* lab,
                            unsigned long long* counters, cudaStream_t s);
-cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float4* lab,
+cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float* lab,
                          unsigned long long* counters, cudaStream_t s);
 template <class Src>
 cudaError_t launch_init_theta(Src lab, const Geom& g, double lambda_c, double* theta, float* gp,

@@ -39,7 +39,7 @@ constexpr size_t kOffPart = kOffGp + up(size_t(GMMSP_NOALLOC_MAX_CELLS) * gmmsp:
 constexpr size_t kOffCellLl = kOffPart + up(size_t(GMMSP_NOALLOC_MAX_CELLS) * gmmsp::kPartStride * sizeof(double));
 constexpr size_t kOffLlk = kOffCellLl + up(size_t(GMMSP_NOALLOC_MAX_CELLS) * sizeof(double));
 constexpr size_t kOffWs = kOffLlk + up(sizeof(double));
-constexpr size_t kOffTicket = kOffWs + up((GMMSP_NOALLOC_MAX_CELLS / 32 + 2) * sizeof(double));
+constexpr size_t kOffTicket = kOffWs + up((GMMSP_NOALLOC_MAX_CELLS / 4 + 2) * sizeof(double));
 constexpr size_t kOffCounters = kOffTicket + up(sizeof(unsigned));
 constexpr size_t kScratchBytes = kOffCounters + up(sizeof(unsigned long long) * gmmsp::CNT_N);
 static_assert(kScratchBytes <= GMMSP_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the documented size");
@@ -147,7 +147,6 @@ extern "C" gmmsp_status gmmsp_segment_lab_noalloc(const float* lab_dev, int widt
   float* gp = reinterpret_cast<float*>(b + kOffGp);
   double* partials = reinterpret_cast<double*>(b + kOffPart);
   double* cell_ll = reinterpret_cast<double*>(b + kOffCellLl);
-  double* llk = reinterpret_cast<double*>(b + kOffLlk);
   double* ws = reinterpret_cast<double*>(b + kOffWs);
   unsigned* ticket = reinterpret_cast<unsigned*>(b + kOffTicket);
   unsigned long long* counters = reinterpret_cast<unsigned long long*>(b + kOffCounters);
@@ -161,7 +160,7 @@ extern "C" gmmsp_status gmmsp_segment_lab_noalloc(const float* lab_dev, int widt
   for (int t = 0; t < iters && e == cudaSuccess; ++t) {
     e = gmmsp::launch_em_pass(src, g, gp, partials, GMMSP_PREC_MIXED, wpc, s);
     if (e == cudaSuccess)
-      e = gmmsp::launch_finalize(g, partials, theta, gp, p->eps_s, p->eps_c, llk, ws, ticket, counters,
+      e = gmmsp::launch_finalize(g, partials, theta, gp, p->eps_s, p->eps_c, nullptr, ws, ticket, counters,
                                  GMMSP_PREC_MIXED, s);
   }
   if (e == cudaSuccess) e = gmmsp::launch_label_pass(src, g, gp, labels_dev, cell_ll, s);

@@ -1,13 +1,13 @@
 // Input preparation and initial parameters.
 //
-//  * k_rgb2lab: sRGB uint8 -> CIELAB float4 (L, a, b, 0) per pixel.  The
+//  * k_rgb2lab: sRGB uint8 -> CIELAB as three float32 planes (L, a, b).  The
 //    paper runs in CIELAB (Sec. IV, first paragraph) without fixing the RGB
 //    space or the white; this library reads the input as sRGB with the D65
 //    white.  The RGB -> XYZ matrix is not a literal table: the host derives
 //    it from the sRGB primaries and the white point (see api), and the
 //    kernel applies the sRGB transfer curve (through a 256-entry table built
 //    per block with powf) and the CIE 1976 L*a*b* formulas.
-//  * k_lab32: repacks a caller's float32 L,a,b image into float4 and counts
+//  * k_lab32: repacks a caller's float32 L,a,b image into planes and counts
 //    non-finite values.
 //  * k_init_theta: Sec. III-C initialisation: mu_k = z of the centre pixel of
 //    cell k, Sigma_s = diag(v^2, v^2), Sigma_c = lambda_c^2 I.
@@ -33,13 +33,15 @@ __device__ __forceinline__ float cielab_f(float t) {
 }
 
 __global__ void __launch_bounds__(256) k_rgb2lab(const uint8_t* __restrict__ img, long long pitch,
-                                                 int W, int H, float4* __restrict__ lab,
+                                                 int W, int H, float* __restrict__ lab,
                                                  Rgb2LabConst k) {
   __shared__ float lin[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     const float c = float(i) * (1.f / 255.f);
     lin[i] = c <= 0.04045f ? c * (1.f / 12.92f) : powf((c + 0.055f) * (1.f / 1.055f), 2.4f);
   }
+  pdl_wait();  // the CIELAB buffer may still be read by the previous pipeline run
+  pdl_trigger();
   __syncthreads();
   const long long N = (long long)W * H;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
@@ -52,15 +54,19 @@ __global__ void __launch_bounds__(256) k_rgb2lab(const uint8_t* __restrict__ img
     const float Y = fmaf(m[3], r, fmaf(m[4], g, m[5] * b)) * k.inv_white[1];
     const float Z = fmaf(m[6], r, fmaf(m[7], g, m[8] * b)) * k.inv_white[2];
     const float fx = cielab_f(X), fy = cielab_f(Y), fz = cielab_f(Z);
-    lab[idx] = make_float4(116.f * fy - 16.f, 500.f * (fx - fy), 200.f * (fy - fz), 0.f);
+    lab[idx] = 116.f * fy - 16.f;
+    lab[N + idx] = 500.f * (fx - fy);
+    lab[2 * N + idx] = 200.f * (fy - fz);
   }
 }
 
 __global__ void __launch_bounds__(256) k_lab32(const float* __restrict__ img, long long pitch, int W,
-                                               int H, float4* __restrict__ lab,
+                                               int H, float* __restrict__ lab,
                                                unsigned long long* __restrict__ counters) {
   const long long N = (long long)W * H;
   unsigned bad = 0;
+  pdl_wait();
+  pdl_trigger();
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
        idx += (long long)gridDim.x * blockDim.x) {
     const int y = int(idx / W), x = int(idx - (long long)y * W);
@@ -68,7 +74,9 @@ __global__ void __launch_bounds__(256) k_lab32(const float* __restrict__ img, lo
                                                     (long long)y * pitch) + 3LL * x;
     const float L = p[0], a = p[1], b = p[2];
     bad += !(isfinite(L) && isfinite(a) && isfinite(b));
-    lab[idx] = make_float4(L, a, b, 0.f);
+    lab[idx] = L;
+    lab[N + idx] = a;
+    lab[2 * N + idx] = b;
   }
   bad = __reduce_add_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&counters[CNT_NONFINITE], (unsigned long long)bad);
@@ -78,6 +86,8 @@ template <class Src>
 __global__ void k_init_theta(Src lab, Geom g, double lambda_c, double* __restrict__ theta,
                              float* __restrict__ gp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (k >= g.K) return;
   const int kx = k % g.nx, ky = k / g.nx;
   const int x = kx * g.v + g.v / 2, y = ky * g.v + g.v / 2;
@@ -147,30 +157,27 @@ static Rgb2LabConst make_rgb2lab_const() {
   return k;
 }
 
-cudaError_t launch_rgb2lab(const uint8_t* img, long long pitch, const Geom& g, float4* lab,
+cudaError_t launch_rgb2lab(const uint8_t* img, long long pitch, const Geom& g, float* lab,
                            unsigned long long* counters, cudaStream_t s) {
   (void)counters;
   static const Rgb2LabConst k = make_rgb2lab_const();
   const long long N = (long long)g.W * g.H;
-  k_rgb2lab<<<grid_for(N, 256), 256, 0, s>>>(img, pitch, g.W, g.H, lab, k);
-  return cudaGetLastError();
+  return launch_pdl(k_rgb2lab, dim3(grid_for(N, 256)), dim3(256), 0, s, img, pitch, g.W, g.H, lab, k);
 }
 
-cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float4* lab,
+cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float* lab,
                          unsigned long long* counters, cudaStream_t s) {
   const long long N = (long long)g.W * g.H;
-  k_lab32<<<grid_for(N, 256), 256, 0, s>>>(img, pitch, g.W, g.H, lab, counters);
-  return cudaGetLastError();
+  return launch_pdl(k_lab32, dim3(grid_for(N, 256)), dim3(256), 0, s, img, pitch, g.W, g.H, lab, counters);
 }
 
 template <class Src>
 cudaError_t launch_init_theta(Src lab, const Geom& g, double lambda_c, double* theta, float* gp,
                               cudaStream_t s) {
-  k_init_theta<Src><<<(g.K + 63) / 64, 64, 0, s>>>(lab, g, lambda_c, theta, gp);
-  return cudaGetLastError();
+  return launch_pdl(k_init_theta<Src>, dim3((g.K + 63) / 64), dim3(64), 0, s, lab, g, lambda_c, theta, gp);
 }
 
-template cudaError_t launch_init_theta<LabPacked>(LabPacked, const Geom&, double, double*, float*,
+template cudaError_t launch_init_theta<LabPlanar>(LabPlanar, const Geom&, double, double*, float*,
                                                   cudaStream_t);
 template cudaError_t launch_init_theta<LabPitched>(LabPitched, const Geom&, double, double*, float*,
                                                    cudaStream_t);
