@@ -210,6 +210,47 @@ gmmsp_status gmmsp_get_launch(gmmsp_ctx c, int *warps_per_cell);
 gmmsp_status gmmsp_autotune(gmmsp_ctx c, int reps, int *best, double *times_ms);
 
 /*
+ * Batches: many images of uneven sizes segmented together, Algorithm 1,
+ * steps 1-7, for every image, with one kernel launch per step for the whole
+ * batch (persistent blocks walk the batch's cells / superpixels), the step
+ * sequence captured into one CUDA graph on the first call (per iteration
+ * count) and replayed afterwards.  The paper segments one image at a time;
+ * batching is this library's way of filling the GPU with small images.
+ *
+ * gmmsp_batch_create: n images with sizes widths[i] x heights[i] (host
+ *   arrays), shared parameters p (spacing or K per image as for gmmsp_init,
+ *   format, precision), work queued on `stream`.  Allocates one device block
+ *   for all images' CIELAB planes, parameters and partial sums.  Errors as
+ *   for gmmsp_init.
+ * gmmsp_batch_segment: images_dev[i] (device rows, pitches[i] bytes each) in,
+ *   labels_dev[i] (device int32 W H) out; host arrays of n pointers / pitches.
+ *   loglik_host NULL or n doubles: L(theta_iters) of each image (the label
+ *   pass' log-likelihood); when non-NULL the call synchronises.  The image
+ *   table is copied to the device on every call, so the pointers may change
+ *   between calls without a new capture.
+ * gmmsp_batch_get_params: theta of image i (layout of gmmsp_get_params);
+ *   synchronises.
+ * gmmsp_batch_autotune: times the batch E + M-partial pass for persistent
+ *   grids of 2..6 blocks per SM (`reps` launches each, on the given images),
+ *   keeps the fastest; times_ms NULL or 5 doubles.  Synchronises.
+ * gmmsp_batch_set_launch: blocks per SM of the persistent grid (1..16).
+ * gmmsp_batch_info: totals over the batch (any pointer may be NULL).
+ */
+typedef struct gmmsp_batch_s *gmmsp_batch;
+gmmsp_status gmmsp_batch_create(gmmsp_batch *out, int n, const int *widths, const int *heights,
+                                const gmmsp_params *p, void *stream);
+gmmsp_status gmmsp_batch_segment(gmmsp_batch b, const void *const *images_dev, const int *pitches,
+                                 int iters, int32_t *const *labels_dev, double *loglik_host);
+gmmsp_status gmmsp_batch_get_params(gmmsp_batch b, int i, double *mu_host, double *cov_s_host,
+                                    double *cov_c_host);
+gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void *const *images_dev, const int *pitches,
+                                  int32_t *const *labels_dev, int reps, int *best, double *times_ms);
+gmmsp_status gmmsp_batch_set_launch(gmmsp_batch b, int blocks_per_sm);
+gmmsp_status gmmsp_batch_info(gmmsp_batch b, long long *total_pixels, int *total_k, int *total_cells);
+const char *gmmsp_batch_last_error(gmmsp_batch b);
+void gmmsp_batch_destroy(gmmsp_batch b);
+
+/*
  * Allocation-free segmentation (the paper has no counterpart; this serves
  * callers that cannot allocate device memory where they run: code inside a
  * memory pool or a caching allocator that owns all device memory, code that

@@ -25,7 +25,9 @@ __all__ = [
     "gmmsp_default_params", "gmmsp_init", "gmmsp_reinit", "gmmsp_em_iters", "gmmsp_labels",
     "gmmsp_segment", "gmmsp_get_lab", "gmmsp_get_grid", "gmmsp_get_params", "gmmsp_set_params", "gmmsp_get_stats",
     "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_set_timing", "gmmsp_get_timing", "gmmsp_set_launch", "gmmsp_get_launch",
-    "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "gmmsp_status_string", "gmmsp_destroy",
+    "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "SuperpixelsBatch",
+    "gmmsp_batch_create", "gmmsp_batch_segment", "gmmsp_batch_get_params", "gmmsp_batch_autotune",
+    "gmmsp_batch_set_launch", "gmmsp_batch_info", "gmmsp_batch_destroy", "gmmsp_status_string", "gmmsp_destroy",
 ]
 
 GMMSP_RGB8, GMMSP_LAB32 = 0, 1
@@ -280,6 +282,143 @@ def gmmsp_segment_lab_noalloc(lab, width: int, height: int, pitch_bytes: int, pa
            _dptr(labels), _stream_handle(stream), err, 256)
     if st != 0:
         raise GmmspError(st, err.value.decode())
+
+
+
+def _batch_lib():
+    lib = load_library()
+    if not getattr(lib, "_batch_sigs", False):
+        P, I = ctypes.c_void_p, ctypes.c_int
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        pint = ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "gmmsp_batch_create": (I, [PP, I, P, P, ctypes.POINTER(gmmsp_params), P]),
+            "gmmsp_batch_segment": (I, [P, P, P, I, P, P]),
+            "gmmsp_batch_get_params": (I, [P, I, P, P, P]),
+            "gmmsp_batch_autotune": (I, [P, P, P, P, I, pint, P]),
+            "gmmsp_batch_set_launch": (I, [P, I]),
+            "gmmsp_batch_info": (I, [P, ctypes.POINTER(ctypes.c_longlong), pint, pint]),
+            "gmmsp_batch_last_error": (ctypes.c_char_p, [P]),
+            "gmmsp_batch_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        lib._batch_sigs = True
+    return lib
+
+
+def _bcheck(b, st):
+    if st != 0:
+        msg = (_batch_lib().gmmsp_batch_last_error(b) or b"").decode() if b else ""
+        raise GmmspError(st, msg)
+
+
+def gmmsp_batch_create(widths, heights, params: gmmsp_params, stream=None):
+    n = len(widths)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    h = np.ascontiguousarray(heights, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _bcheck(None, _batch_lib().gmmsp_batch_create(ctypes.byref(out), n, w.ctypes.data_as(ctypes.c_void_p),
+                                                  h.ctypes.data_as(ctypes.c_void_p), ctypes.byref(params),
+                                                  _stream_handle(stream)))
+    return out
+
+
+def _ptr_array(tensors):
+    return (ctypes.c_void_p * len(tensors))(*[_dptr(t) for t in tensors])
+
+
+def gmmsp_batch_segment(b, images, pitches, iters, labels, want_loglik=False):
+    n = len(images)
+    pit = np.ascontiguousarray(pitches, dtype=np.int32)
+    ll = np.zeros(n) if want_loglik else None
+    _bcheck(b, _batch_lib().gmmsp_batch_segment(b, _ptr_array(images), pit.ctypes.data_as(ctypes.c_void_p),
+                                                int(iters), _ptr_array(labels),
+                                                ll.ctypes.data_as(ctypes.c_void_p) if ll is not None else None))
+    return ll
+
+
+def gmmsp_batch_get_params(b, i, K):
+    mu, cs, cc = np.zeros((K, 5)), np.zeros((K, 3)), np.zeros((K, 6))
+    _bcheck(b, _batch_lib().gmmsp_batch_get_params(b, int(i), mu.ctypes.data_as(ctypes.c_void_p),
+                                                   cs.ctypes.data_as(ctypes.c_void_p),
+                                                   cc.ctypes.data_as(ctypes.c_void_p)))
+    return mu, cs, cc
+
+
+def gmmsp_batch_autotune(b, images, pitches, labels, reps=3):
+    pit = np.ascontiguousarray(pitches, dtype=np.int32)
+    best = ctypes.c_int()
+    times = np.zeros(5)
+    _bcheck(b, _batch_lib().gmmsp_batch_autotune(b, _ptr_array(images), pit.ctypes.data_as(ctypes.c_void_p),
+                                                 _ptr_array(labels), int(reps), ctypes.byref(best),
+                                                 times.ctypes.data_as(ctypes.c_void_p)))
+    return best.value, dict(zip((2, 3, 4, 5, 6), times.tolist()))
+
+
+def gmmsp_batch_set_launch(b, blocks_per_sm: int) -> None:
+    _bcheck(b, _batch_lib().gmmsp_batch_set_launch(b, int(blocks_per_sm)))
+
+
+def gmmsp_batch_info(b):
+    pix, K, cells = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+    _bcheck(b, _batch_lib().gmmsp_batch_info(b, ctypes.byref(pix), ctypes.byref(K), ctypes.byref(cells)))
+    return pix.value, K.value, cells.value
+
+
+def gmmsp_batch_destroy(b) -> None:
+    _batch_lib().gmmsp_batch_destroy(b)
+
+
+class SuperpixelsBatch:
+    """A batch context over lists of (H, W, 3) uint8 RGB (or float32 CIELAB) CUDA tensors."""
+
+    def __init__(self, shapes, K: int = 0, spacing: int = 0, eps_s: float = 2.0, eps_c: float = 8.0,
+                 lambda_c: float = 8.0, precision: int = GMMSP_PREC_MIXED, lab_input: bool = False,
+                 stream=None):
+        import torch
+        p = gmmsp_default_params()
+        p.spacing, p.K, p.eps_s, p.eps_c, p.lambda_c = int(spacing), int(K), eps_s, eps_c, lambda_c
+        p.input_format = GMMSP_LAB32 if lab_input else GMMSP_RGB8
+        p.precision = int(precision)
+        self.shapes = [(int(h), int(w)) for (h, w) in shapes]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.b = gmmsp_batch_create([w for _, w in self.shapes], [h for h, _ in self.shapes], p, self.stream)
+        self.labels = [torch.empty((h, w), dtype=torch.int32, device="cuda") for h, w in self.shapes]
+
+    @staticmethod
+    def _pitch(t) -> int:
+        return int(t.stride(0) * t.element_size())
+
+    def segment(self, images, iters: int = 10, want_loglik: bool = False):
+        ll = gmmsp_batch_segment(self.b, images, [self._pitch(t) for t in images], iters, self.labels,
+                                 want_loglik)
+        return (self.labels, ll) if want_loglik else self.labels
+
+    def autotune(self, images, reps: int = 3):
+        return gmmsp_batch_autotune(self.b, images, [self._pitch(t) for t in images], self.labels, reps)
+
+    def set_launch(self, blocks_per_sm: int) -> None:
+        gmmsp_batch_set_launch(self.b, blocks_per_sm)
+
+    def info(self):
+        return gmmsp_batch_info(self.b)
+
+    def get_params(self, i: int, K: int):
+        return gmmsp_batch_get_params(self.b, i, K)
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            gmmsp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gmmsp_last_error(ctx) -> str:

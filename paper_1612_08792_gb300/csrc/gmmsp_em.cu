@@ -258,22 +258,15 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
   }
 }
 
+// One cell of the fused pass, run by the WPC warps of cell slot `slot` of the
+// block (all threads of the block call it together when WPC > 1).
 template <typename PT, bool SHIFT, int WPC, class Src>
-__global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(Src lab, Geom g, const float* __restrict__ gp,
-                                                           PT* __restrict__ partials) {
-  constexpr int kCellsPerBlock = kEmWarps / WPC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  EmSmem<WPC>& sm = *reinterpret_cast<EmSmem<WPC>*>(smem_raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int slot = warp / WPC;       // cell slot within the block
-  const int wic = warp % WPC;        // warp index within the cell
-  const int t = wic * 32 + lane;     // thread index within the cell
-  const int cell = blockIdx.x * kCellsPerBlock + slot;
-  const bool active = cell < g.ncells;  // inactive threads still reach every barrier
+__device__ __forceinline__ void em_cell_block(const Src& lab, const Geom& g, const float* __restrict__ gp,
+                                              PT* __restrict__ partials, int cell, bool active,
+                                              EmSmem<WPC>& sm, int warp, int lane, int slot, int wic,
+                                              int t) {
   Cell c = {};
   if (active) c = make_cell(g, cell);
-  pdl_wait();  // gp and the image are written by the preceding kernels
-  pdl_trigger();
   if (active) {
     for (int i = t; i < kSlots * 4; i += 32 * WPC) {
       const int s = i >> 2, q = i & 3;
@@ -322,6 +315,60 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(Src lab, Geom g, cons
       out[o] = (o < kSlots * kStats) ? PT(v) : PT(v) * PT(0.69314718055994530942);
     }
   }
+  if (WPC == 1) __syncwarp(); else __syncthreads();  // the slot's buffers are reused next
+}
+
+template <typename PT, bool SHIFT, int WPC, class Src>
+__global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(Src lab, Geom g, const float* __restrict__ gp,
+                                                           PT* __restrict__ partials) {
+  constexpr int kCellsPerBlock = kEmWarps / WPC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EmSmem<WPC>& sm = *reinterpret_cast<EmSmem<WPC>*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slot = warp / WPC;       // cell slot within the block
+  const int wic = warp % WPC;        // warp index within the cell
+  const int t = wic * 32 + lane;     // thread index within the cell
+  const int cell = blockIdx.x * kCellsPerBlock + slot;
+  const bool active = cell < g.ncells;  // inactive threads still reach every barrier
+  pdl_wait();  // gp and the image are written by the preceding kernels
+  pdl_trigger();
+  em_cell_block<PT, SHIFT, WPC, Src>(lab, g, gp, partials, cell, active, sm, warp, lane, slot, wic, t);
+}
+
+// ---------------------------------------------------------------- batches
+// Many images in one launch per phase.  Image i owns the cells
+// [cell_off, cell_off + ncells), the superpixels [k_off, k_off + K) and the
+// pixels [pix_off, pix_off + W H) of the batch (its CIELAB planes start at
+// lab + 3 pix_off).  Work items are found by a binary search over these
+// prefix offsets; warps (threads for per-superpixel work) loop over the
+// batch's items with the grid's stride, so the grid is sized to the machine
+// (persistent blocks) rather than to the work.
+__device__ __forceinline__ int find_image(const BatchImage* __restrict__ imgs, int n, int item,
+                                          int which /*0 cells, 1 superpixels*/) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    const int off = which == 0 ? imgs[mid].cell_off : imgs[mid].k_off;
+    if (off <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename PT, bool SHIFT>
+__global__ void __launch_bounds__(kEmWarps * 32) k_em_pass_batch(const BatchImage* __restrict__ imgs, int n,
+                                                                 int total_cells, const float* __restrict__ lab,
+                                                                 const float* __restrict__ gp,
+                                                                 PT* __restrict__ partials) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EmSmem<1>& sm = *reinterpret_cast<EmSmem<1>*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int cell = blockIdx.x * kEmWarps + warp; cell < total_cells; cell += gridDim.x * kEmWarps) {
+    const BatchImage& im = imgs[find_image(imgs, n, cell, 0)];
+    const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
+    em_cell_block<PT, SHIFT, 1, LabPlanar>(src, im.g, gp + (long long)im.k_off * kGP,
+                                           partials + (long long)im.cell_off * kPartStride,
+                                           cell - im.cell_off, true, sm, warp, lane, warp, 0, lane);
+  }
 }
 
 // Label pass: argmax posterior per pixel (ties to the smaller k, i.e. the
@@ -359,6 +406,23 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
   }
 }
 
+// One cell of the label pass, run by one warp.
+template <class Src>
+__device__ __forceinline__ void label_cell_warp(const Src& lab, const Geom& g, const float* __restrict__ gp,
+                                                int32_t* __restrict__ labels, double* __restrict__ cell_ll,
+                                                int cell, float4* sp, int lane) {
+  const Cell c = make_cell(g, cell);
+  stage_params(g, c, gp, sp, lane);
+  float ll = 0.f;
+  if (c.mask == 0x1ffu)
+    label_cell_pixels<true, Src>(lab, g, c, sp, lane, labels, ll);
+  else
+    label_cell_pixels<false, Src>(lab, g, c, sp, lane, labels, ll);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+  if (lane == 0) cell_ll[cell] = double(ll) * 0.69314718055994530942;
+}
+
 template <class Src>
 __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass(Src lab, Geom g, const float* __restrict__ gp,
                                                               int32_t* __restrict__ labels,
@@ -369,17 +433,23 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass(Src lab, Geom g, c
   pdl_wait();
   pdl_trigger();
   if (cell >= g.ncells) return;
-  const Cell c = make_cell(g, cell);
-  float4* sp = sp_all[warp];
-  stage_params(g, c, gp, sp, lane);
-  float ll = 0.f;
-  if (c.mask == 0x1ffu)
-    label_cell_pixels<true, Src>(lab, g, c, sp, lane, labels, ll);
-  else
-    label_cell_pixels<false, Src>(lab, g, c, sp, lane, labels, ll);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
-  if (lane == 0) cell_ll[cell] = double(ll) * 0.69314718055994530942;
+  label_cell_warp<Src>(lab, g, gp, labels, cell_ll, cell, sp_all[warp], lane);
+}
+
+__global__ void __launch_bounds__(kEmWarps * 32) k_label_pass_batch(const BatchImage* __restrict__ imgs, int n,
+                                                                    int total_cells,
+                                                                    const float* __restrict__ lab,
+                                                                    const float* __restrict__ gp,
+                                                                    double* __restrict__ cell_ll) {
+  __shared__ float4 sp_all[kEmWarps][kSlots * 4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int cell = blockIdx.x * kEmWarps + warp; cell < total_cells; cell += gridDim.x * kEmWarps) {
+    const BatchImage& im = imgs[find_image(imgs, n, cell, 0)];
+    const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
+    label_cell_warp<LabPlanar>(src, im.g, gp + (long long)im.k_off * kGP, im.labels,
+                               cell_ll + im.cell_off, cell - im.cell_off, sp_all[warp], lane);
+    __syncwarp();
+  }
 }
 
 // ---------------------------------------------------------------- finalize
@@ -427,6 +497,80 @@ __device__ void block_ll_sum(const PT* vals, long long stride, int n, double* bl
   }
 }
 
+// Update of superpixel k from the partial sums of its <= 9 cells (see the
+// header comment); the counters are incremented by the caller.
+template <typename PT>
+__device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__ partials,
+                                           double* __restrict__ theta, float* __restrict__ gp,
+                                           double eps_s, double eps_c, int k, unsigned& dead,
+                                           unsigned& rs, unsigned& rc) {
+  using T = PT;  // arithmetic type of the update: double, or float for the FP32 variant
+  constexpr bool kShifted = sizeof(PT) == 8;
+  const int kx = k % g.nx, ky = k / g.nx;
+  T S[kStats];
+#pragma unroll
+  for (int j = 0; j < kStats; ++j) S[j] = T(0);
+  // The cells (kx+dx, ky+dy) hold k in slot (1-dy)*3 + (1-dx); fixed order.
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) {
+    const int cy = ky + dy;
+    if (cy < 0 || cy >= g.ncy) continue;
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int cx = kx + dx;
+      if (cx < 0 || cx >= g.ncx) continue;
+      const PT* P = partials + (long long)(cy * g.ncx + cx) * kPartStride + ((1 - dy) * 3 + (1 - dx)) * kStats;
+#pragma unroll
+      for (int j = 0; j < kStats; ++j) S[j] += P[j];
+    }
+  }
+  const T Wk = S[ST_W];
+  if (!(Wk >= T(1e-8))) {
+    dead = 1;  // reading: a superpixel with no weight keeps theta_k
+  } else {
+    float* G = gp + (long long)k * kGP;
+    const T iw = Num<T>::rcp(Wk);
+    T mu[5], cs[3], cc[6];
+    const T ox = T(kx * g.v), oy = T(ky * g.v);  // origin of k's cell
+    // Moments about r: Sigma = S2 / W - d d^T with d = S1 / W.  The shifted
+    // path has r = mu_ref, the FP32 mean the E-step subtracted (spatial part
+    // relative to the cell origin); the raw path has r = 0.
+    T dl[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) dl[j] = S[ST_S1 + j] * iw;
+    cs[0] = fma(-dl[0], dl[0], S[ST_S2S + 0] * iw);
+    cs[1] = fma(-dl[0], dl[1], S[ST_S2S + 1] * iw);
+    cs[2] = fma(-dl[1], dl[1], S[ST_S2S + 2] * iw);
+    cc[0] = fma(-dl[2], dl[2], S[ST_S2C + 0] * iw);
+    cc[1] = fma(-dl[2], dl[3], S[ST_S2C + 1] * iw);
+    cc[2] = fma(-dl[2], dl[4], S[ST_S2C + 2] * iw);
+    cc[3] = fma(-dl[3], dl[3], S[ST_S2C + 3] * iw);
+    cc[4] = fma(-dl[3], dl[4], S[ST_S2C + 4] * iw);
+    cc[5] = fma(-dl[4], dl[4], S[ST_S2C + 5] * iw);
+    if (kShifted) {
+      mu[0] = ox + (T(G[0]) + dl[0]);
+      mu[1] = oy + (T(G[1]) + dl[1]);
+#pragma unroll
+      for (int j = 2; j < 5; ++j) mu[j] = T(G[j]) + dl[j];
+    } else {
+      mu[0] = ox + dl[0];
+      mu[1] = oy + dl[1];
+#pragma unroll
+      for (int j = 2; j < 5; ++j) mu[j] = dl[j];
+    }
+    rs = clamp_sym2<T>(cs, T(eps_s));
+    rc = clamp_sym3<T>(cc, T(eps_c));
+    double* th = theta + (long long)k * kTheta;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) th[j] = double(mu[j]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) th[5 + j] = double(cs[j]);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) th[8 + j] = double(cc[j]);
+    pack_gp<T>(mu, cs, cc, ox, oy, G);
+  }
+}
+
 template <typename PT>
 __global__ void __launch_bounds__(kFinThreads) k_finalize(Geom g, const PT* __restrict__ partials,
                                                           double* __restrict__ theta,
@@ -434,8 +578,6 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Geom g, const PT* __re
                                                           double eps_c, double* llk_out,
                                                           double* blk, unsigned* ticket,
                                                           unsigned long long* counters) {
-  using T = PT;  // arithmetic type of the update: double, or float for the FP32 variant
-  constexpr bool kShifted = sizeof(PT) == 8;
   pdl_wait();
   pdl_trigger();
   if (llk_out)
@@ -443,69 +585,32 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Geom g, const PT* __re
 
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned dead = 0, rs = 0, rc = 0;
-  if (k < g.K) {
-    const int kx = k % g.nx, ky = k / g.nx;
-    T S[kStats];
-#pragma unroll
-    for (int j = 0; j < kStats; ++j) S[j] = T(0);
-    // The cells (kx+dx, ky+dy) hold k in slot (1-dy)*3 + (1-dx); fixed order.
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int cy = ky + dy;
-      if (cy < 0 || cy >= g.ncy) continue;
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int cx = kx + dx;
-        if (cx < 0 || cx >= g.ncx) continue;
-        const PT* P = partials + (long long)(cy * g.ncx + cx) * kPartStride + ((1 - dy) * 3 + (1 - dx)) * kStats;
-#pragma unroll
-        for (int j = 0; j < kStats; ++j) S[j] += P[j];
-      }
-    }
-    const T Wk = S[ST_W];
-    if (!(Wk >= T(1e-8))) {
-      dead = 1;  // reading: a superpixel with no weight keeps theta_k
-    } else {
-      float* G = gp + (long long)k * kGP;
-      const T iw = Num<T>::rcp(Wk);
-      T mu[5], cs[3], cc[6];
-      const T ox = T(kx * g.v), oy = T(ky * g.v);  // origin of k's cell
-      // Moments about r: Sigma = S2 / W - d d^T with d = S1 / W.  The shifted
-      // path has r = mu_ref, the FP32 mean the E-step subtracted (spatial part
-      // relative to the cell origin); the raw path has r = 0.
-      T dl[5];
-#pragma unroll
-      for (int j = 0; j < 5; ++j) dl[j] = S[ST_S1 + j] * iw;
-      cs[0] = fma(-dl[0], dl[0], S[ST_S2S + 0] * iw);
-      cs[1] = fma(-dl[0], dl[1], S[ST_S2S + 1] * iw);
-      cs[2] = fma(-dl[1], dl[1], S[ST_S2S + 2] * iw);
-      cc[0] = fma(-dl[2], dl[2], S[ST_S2C + 0] * iw);
-      cc[1] = fma(-dl[2], dl[3], S[ST_S2C + 1] * iw);
-      cc[2] = fma(-dl[2], dl[4], S[ST_S2C + 2] * iw);
-      cc[3] = fma(-dl[3], dl[3], S[ST_S2C + 3] * iw);
-      cc[4] = fma(-dl[3], dl[4], S[ST_S2C + 4] * iw);
-      cc[5] = fma(-dl[4], dl[4], S[ST_S2C + 5] * iw);
-      if (kShifted) {
-        mu[0] = ox + (T(G[0]) + dl[0]);
-        mu[1] = oy + (T(G[1]) + dl[1]);
-#pragma unroll
-        for (int j = 2; j < 5; ++j) mu[j] = T(G[j]) + dl[j];
-      } else {
-        mu[0] = ox + dl[0];
-        mu[1] = oy + dl[1];
-#pragma unroll
-        for (int j = 2; j < 5; ++j) mu[j] = dl[j];
-      }
-      rs = clamp_sym2<T>(cs, T(eps_s));
-      rc = clamp_sym3<T>(cc, T(eps_c));
-      double* th = theta + (long long)k * kTheta;
-#pragma unroll
-      for (int j = 0; j < 5; ++j) th[j] = double(mu[j]);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) th[5 + j] = double(cs[j]);
-#pragma unroll
-      for (int j = 0; j < 6; ++j) th[8 + j] = double(cc[j]);
-      pack_gp<T>(mu, cs, cc, ox, oy, G);
+  if (k < g.K) finalize_k<PT>(g, partials, theta, gp, eps_s, eps_c, k, dead, rs, rc);
+  dead = __reduce_add_sync(0xffffffffu, dead);
+  rs = __reduce_add_sync(0xffffffffu, rs);
+  rc = __reduce_add_sync(0xffffffffu, rc);
+  if ((threadIdx.x & 31) == 0) {
+    if (dead) atomicAdd(&counters[CNT_DEAD], (unsigned long long)dead);
+    if (rs) atomicAdd(&counters[CNT_RAISED_S], (unsigned long long)rs);
+    if (rc) atomicAdd(&counters[CNT_RAISED_C], (unsigned long long)rc);
+  }
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(kFinThreads) k_finalize_batch(const BatchImage* __restrict__ imgs, int n,
+                                                                int total_k, const PT* __restrict__ partials,
+                                                                double* __restrict__ theta,
+                                                                float* __restrict__ gp, double eps_s,
+                                                                double eps_c,
+                                                                unsigned long long* counters) {
+  unsigned dead = 0, rs = 0, rc = 0;
+  const int stride = gridDim.x * kFinThreads;
+  for (int base = blockIdx.x * kFinThreads; base < total_k; base += stride) {
+    const int k = base + threadIdx.x;
+    if (k < total_k) {
+      const BatchImage& im = imgs[find_image(imgs, n, k, 1)];
+      finalize_k<PT>(im.g, partials + (long long)im.cell_off * kPartStride, theta + (long long)im.k_off * kTheta,
+                     gp + (long long)im.k_off * kGP, eps_s, eps_c, k - im.k_off, dead, rs, rc);
     }
   }
   dead = __reduce_add_sync(0xffffffffu, dead);
@@ -840,6 +945,44 @@ cudaError_t launch_finalize(const Geom& g, const void* partials, double* theta, 
 cudaError_t launch_ll_reduce(const double* cell_ll, int n, double* out, double* ws, unsigned* ticket,
                              const Geom& g, cudaStream_t s) {
   return launch_pdl(k_ll_reduce, dim3(ll_blocks(g)), dim3(kFinThreads), 0, s, cell_ll, n, ws, ticket, out);
+}
+
+}  // namespace gmmsp
+
+// ---------------------------------------------------------------- batch launchers
+namespace gmmsp {
+
+cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
+                                 const float* gp, void* partials, int precision, int blocks,
+                                 cudaStream_t s) {
+  constexpr int smem = em_smem_bytes<1>();
+  if (precision == 1)
+    k_em_pass_batch<float, false><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                    static_cast<float*>(partials));
+  else
+    k_em_pass_batch<double, true><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                    static_cast<double*>(partials));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(const BatchImage* imgs, int n, int total_k, const void* partials,
+                                  double* theta, float* gp, double eps_s, double eps_c,
+                                  unsigned long long* counters, int precision, int blocks,
+                                  cudaStream_t s) {
+  if (precision == 1)
+    k_finalize_batch<float><<<blocks, kFinThreads, 0, s>>>(imgs, n, total_k, static_cast<const float*>(partials),
+                                                           theta, gp, eps_s, eps_c, counters);
+  else
+    k_finalize_batch<double><<<blocks, kFinThreads, 0, s>>>(imgs, n, total_k,
+                                                            static_cast<const double*>(partials), theta, gp,
+                                                            eps_s, eps_c, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_label_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
+                                    const float* gp, double* cell_ll, int blocks, cudaStream_t s) {
+  k_label_pass_batch<<<blocks, kEmWarps * 32, 0, s>>>(imgs, n, total_cells, lab, gp, cell_ll);
+  return cudaGetLastError();
 }
 
 }  // namespace gmmsp

@@ -97,6 +97,18 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// One image of a batch (device-side table, one entry per image, ordered).
+struct BatchImage {
+  Geom g;
+  const void* image;   // this call's input rows (RGB8 or LAB32)
+  long long pitch;     // its row pitch in bytes
+  int32_t* labels;     // output labels, W H int32
+  long long pix_off;   // first pixel of the image in the batch (CIELAB planes at lab + 3 pix_off)
+  int row_off;         // first row of the image in the batch's list of rows
+  int cell_off;        // first cell of the image in the batch
+  int k_off;           // first superpixel of the image in the batch
+};
+
 // Device counters (unsigned long long): dead, raised_s, raised_c, nonfinite input.
 enum : int { CNT_DEAD = 0, CNT_RAISED_S = 1, CNT_RAISED_C = 2, CNT_NONFINITE = 3, CNT_N = 4 };
 
@@ -127,5 +139,24 @@ cudaError_t launch_ll_reduce(const double* cell_ll, int n, double* out, double* 
                              const Geom& g, cudaStream_t s);
 size_t finalize_workspace_doubles(const Geom& g);
 cudaError_t launch_pack_theta(const Geom& g, double* theta, float* gp, int* bad, cudaStream_t s);
+
+// Batches: the same steps over all images of a BatchImage table in one launch
+// each; `blocks` is the persistent grid size.
+cudaError_t launch_prepare_batch(const BatchImage* imgs, int n, long long total_pix, int input_format,
+                                 float* lab, unsigned long long* counters, int blocks, cudaStream_t s);
+cudaError_t launch_init_batch(const BatchImage* imgs, int n, int total_k, const float* lab,
+                              double lambda_c, double* theta, float* gp, int blocks, cudaStream_t s);
+cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
+                                 const float* gp, void* partials, int precision, int blocks,
+                                 cudaStream_t s);
+cudaError_t launch_finalize_batch(const BatchImage* imgs, int n, int total_k, const void* partials,
+                                  double* theta, float* gp, double eps_s, double eps_c,
+                                  unsigned long long* counters, int precision, int blocks,
+                                  cudaStream_t s);
+cudaError_t launch_label_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
+                                    const float* gp, double* cell_ll, int blocks, cudaStream_t s);
+// ll_out[i] = sum of image i's per-cell log-likelihoods (fixed order).
+cudaError_t launch_ll_per_image(const BatchImage* imgs, int n, const double* cell_ll, double* ll_out,
+                                cudaStream_t s);
 
 }  // namespace gmmsp

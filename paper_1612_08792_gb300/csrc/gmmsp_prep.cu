@@ -82,13 +82,10 @@ __global__ void __launch_bounds__(256) k_lab32(const float* __restrict__ img, lo
   if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&counters[CNT_NONFINITE], (unsigned long long)bad);
 }
 
+// Sec. III-C initialisation of superpixel k.
 template <class Src>
-__global__ void k_init_theta(Src lab, Geom g, double lambda_c, double* __restrict__ theta,
-                             float* __restrict__ gp) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  pdl_wait();
-  pdl_trigger();
-  if (k >= g.K) return;
+__device__ __forceinline__ void init_k(const Src& lab, const Geom& g, double lambda_c,
+                                       double* __restrict__ theta, float* __restrict__ gp, int k) {
   const int kx = k % g.nx, ky = k / g.nx;
   const int x = kx * g.v + g.v / 2, y = ky * g.v + g.v / 2;
   const float4 c = lab.load(x, y);
@@ -102,6 +99,16 @@ __global__ void k_init_theta(Src lab, Geom g, double lambda_c, double* __restric
   for (int i = 0; i < 6; ++i) th[8 + i] = cc[i];
   th[14] = th[15] = 0.0;
   pack_gp<double>(mu, cs, cc, double(kx * g.v), double(ky * g.v), gp + (long long)k * kGP);
+}
+
+template <class Src>
+__global__ void k_init_theta(Src lab, Geom g, double lambda_c, double* __restrict__ theta,
+                             float* __restrict__ gp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
+  if (k >= g.K) return;
+  init_k<Src>(lab, g, lambda_c, theta, gp, k);
 }
 
 __global__ void k_pack_theta(Geom g, const double* __restrict__ theta, float* __restrict__ gp,
@@ -184,6 +191,117 @@ template cudaError_t launch_init_theta<LabPitched>(LabPitched, const Geom&, doub
 
 cudaError_t launch_pack_theta(const Geom& g, double* theta, float* gp, int* bad, cudaStream_t s) {
   k_pack_theta<<<(g.K + 63) / 64, 64, 0, s>>>(g, theta, gp, bad);
+  return cudaGetLastError();
+}
+
+}  // namespace gmmsp
+
+// ---------------------------------------------------------------- batches
+namespace gmmsp {
+
+// Image of batch row `row` (binary search over the images' first rows).
+__device__ __forceinline__ int find_row_image(const BatchImage* __restrict__ imgs, int n, int row) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (imgs[mid].row_off <= row) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// CIELAB conversion of every image of a batch: one warp per image row, rows
+// of all images taken in turn by the persistent warps.
+__global__ void __launch_bounds__(256) k_prepare_batch(const BatchImage* __restrict__ imgs, int n,
+                                                       int total_rows, int input_format,
+                                                       float* __restrict__ lab, Rgb2LabConst k,
+                                                       unsigned long long* __restrict__ counters) {
+  __shared__ float lin[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    const float c = float(i) * (1.f / 255.f);
+    lin[i] = c <= 0.04045f ? c * (1.f / 12.92f) : powf((c + 0.055f) * (1.f / 1.055f), 2.4f);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  unsigned bad = 0;
+  for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < total_rows; row += warps) {
+    const BatchImage& im = imgs[find_row_image(imgs, n, row)];
+    const int W = im.g.W, y = row - im.row_off;
+    const long long N = (long long)W * im.g.H;
+    float* P = lab + 3 * im.pix_off;
+    const char* src = static_cast<const char*>(im.image) + (long long)y * im.pitch;
+    for (int x = lane; x < W; x += 32) {
+      float L, a, b;
+      if (input_format == 0) {
+        const uint8_t* p = reinterpret_cast<const uint8_t*>(src) + 3LL * x;
+        const float r = lin[p[0]], g = lin[p[1]], bl = lin[p[2]];
+        const float* m = k.m;
+        const float X = fmaf(m[0], r, fmaf(m[1], g, m[2] * bl)) * k.inv_white[0];
+        const float Y = fmaf(m[3], r, fmaf(m[4], g, m[5] * bl)) * k.inv_white[1];
+        const float Z = fmaf(m[6], r, fmaf(m[7], g, m[8] * bl)) * k.inv_white[2];
+        const float fx = cielab_f(X), fy = cielab_f(Y), fz = cielab_f(Z);
+        L = 116.f * fy - 16.f; a = 500.f * (fx - fy); b = 200.f * (fy - fz);
+      } else {
+        const float* p = reinterpret_cast<const float*>(src) + 3LL * x;
+        L = p[0]; a = p[1]; b = p[2];
+        bad += !(isfinite(L) && isfinite(a) && isfinite(b));
+      }
+      const long long q = (long long)y * W + x;
+      P[q] = L; P[N + q] = a; P[2 * N + q] = b;
+    }
+  }
+  bad = __reduce_add_sync(0xffffffffu, bad);
+  if (lane == 0 && bad) atomicAdd(&counters[CNT_NONFINITE], (unsigned long long)bad);
+}
+
+__global__ void __launch_bounds__(128) k_init_batch(const BatchImage* __restrict__ imgs, int n, int total_k,
+                                                    const float* __restrict__ lab, double lambda_c,
+                                                    double* __restrict__ theta, float* __restrict__ gp) {
+  for (int kg = blockIdx.x * blockDim.x + threadIdx.x; kg < total_k; kg += gridDim.x * blockDim.x) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (imgs[mid].k_off <= kg) lo = mid; else hi = mid;
+    }
+    const BatchImage& im = imgs[lo];
+    const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
+    init_k<LabPlanar>(src, im.g, lambda_c, theta + (long long)im.k_off * kTheta,
+                      gp + (long long)im.k_off * kGP, kg - im.k_off);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_ll_per_image(const BatchImage* __restrict__ imgs,
+                                                      const double* __restrict__ cell_ll,
+                                                      double* __restrict__ out) {
+  __shared__ double red[128];
+  const BatchImage& im = imgs[blockIdx.x];
+  double s = 0.0;
+  for (int c = threadIdx.x; c < im.g.ncells; c += 128) s += cell_ll[im.cell_off + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+cudaError_t launch_prepare_batch(const BatchImage* imgs, int n, long long total_rows, int input_format,
+                                 float* lab, unsigned long long* counters, int blocks, cudaStream_t s) {
+  static const Rgb2LabConst k = make_rgb2lab_const();
+  k_prepare_batch<<<blocks, 256, 0, s>>>(imgs, n, int(total_rows), input_format, lab, k, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_batch(const BatchImage* imgs, int n, int total_k, const float* lab,
+                              double lambda_c, double* theta, float* gp, int blocks, cudaStream_t s) {
+  k_init_batch<<<blocks, 128, 0, s>>>(imgs, n, total_k, lab, lambda_c, theta, gp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ll_per_image(const BatchImage* imgs, int n, const double* cell_ll, double* ll_out,
+                                cudaStream_t s) {
+  k_ll_per_image<<<n, 128, 0, s>>>(imgs, cell_ll, ll_out);
   return cudaGetLastError();
 }
 

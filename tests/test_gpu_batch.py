@@ -1,0 +1,98 @@
+"""Batched segmentation (gmmsp_batch_*) against the single-image path and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import voronoi_image
+from synth.voronoi import batch_regions
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(37, 23), (320, 240), (70, 52), (481, 321), (97, 61), (150, 110)]
+
+
+@pytest.fixture(scope="module")
+def gm():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    torch.cuda.set_device(0)
+    return gm
+
+
+def make_labs(sizes, seed0=100):
+    labs = []
+    for i, (W, H) in enumerate(sizes):
+        img = voronoi_image(W, H, batch_regions(W, H), 8.0, seed0 + i)
+        labs.append(oracle.rgb2lab(img).astype(np.float32))
+    return labs
+
+
+def test_batch_matches_single_images_and_oracle(gm):
+    import torch
+    spacing, T = 8, 10
+    labs = make_labs(SIZES)
+    dev = [torch.from_numpy(x).cuda() for x in labs]
+    bt = gm.SuperpixelsBatch([(H, W) for (W, H) in SIZES], spacing=spacing, lab_input=True)
+    labels, ll = bt.segment(dev, iters=T, want_loglik=True)
+    torch.cuda.synchronize()
+    for i, (W, H) in enumerate(SIZES):
+        sp = gm.Superpixels(dev[i], spacing=spacing)
+        sp.set_launch(1)
+        sp.em_iters(T)
+        ref_labels, ref_ll = sp.labels(want_loglik=True)
+        mu_s, cs_s, cc_s = sp.get_params()
+        K = sp.grid.K
+        sp.close()
+        mu_b, cs_b, cc_b = bt.get_params(i, K)
+        assert parity.mean_rel_err(mu_b, mu_s) < 1e-6
+        assert parity.cov_rel_err(cc_b, cc_s) < 1e-6
+        agree = (labels[i].cpu().numpy() == ref_labels.cpu().numpy()).mean()
+        assert agree >= 0.9999, (i, agree)
+        assert abs(ll[i] - ref_ll) <= 1e-6 * abs(ref_ll)
+        if i in (0, 3):  # and against the oracle
+            ref = oracle.em(labs[i].astype(np.float64), W, H, spacing=spacing, T=T)
+            assert parity.mean_rel_err(mu_b, ref.theta.mu) <= parity.MEAN_TOL
+            assert parity.cov_rel_err(cc_b, ref.theta.cc) <= parity.COV_TOL
+            a, nd, worst = parity.label_report(labels[i].cpu().numpy(), ref.labels, ref.margin)
+            assert a >= parity.LABEL_AGREE and worst < parity.MARGIN_TOL, (a, nd, worst)
+    bt.close()
+
+
+def test_batch_rgb_input_graph_replay_and_autotune(gm):
+    import torch
+    sizes = [(320, 240), (481, 321), (640, 480), (320, 240)]
+    imgs = [torch.from_numpy(voronoi_image(W, H, batch_regions(W, H), 8.0, 7 + i)).cuda()
+            for i, (W, H) in enumerate(sizes)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        bt = gm.SuperpixelsBatch([(H, W) for (W, H) in sizes], spacing=15, stream=stream)
+        best, times = bt.autotune(imgs, reps=2)
+        assert best in times and all(t > 0 for t in times.values())
+        first = [x.clone() for x in bt.segment(imgs, iters=10)]   # captures
+        again, ll = bt.segment(imgs, iters=10, want_loglik=True)  # replays (new capture for ll)
+        third = bt.segment(imgs, iters=10)                         # replays
+        stream.synchronize()
+    for a, b, c in zip(first, again, third):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
+        torch.testing.assert_close(a, c, rtol=0, atol=0)
+    pix, K, cells = bt.info()
+    assert pix == sum(W * H for W, H in sizes)
+    assert np.all(np.isfinite(ll))
+    # single-image RGB path on the third image
+    sp = gm.Superpixels(imgs[2], spacing=15)
+    sp.set_launch(1)
+    sp.em_iters(10)
+    ref = sp.labels().cpu().numpy()
+    sp.close()
+    assert (third[2].cpu().numpy() == ref).mean() >= 0.9999
+    bt.close()
+
+
+def test_batch_rejects_bad_arguments(gm):
+    p = gm.gmmsp_default_params()
+    p.spacing = 12
+    with pytest.raises(gm.GmmspError):
+        gm.gmmsp_batch_create([320, 5], [240, 5], p)  # second image smaller than the spacing
