@@ -28,6 +28,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -320,6 +322,107 @@ def run_gmmsp(args):
     return 0
 
 
+def _timed_steps(step, stream, steps, flush, clk_index):
+    """Per-step CUDA-event times (ms) with L2 flushed before every step, and the clock record."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(clk_index) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(steps):
+                flush.fill_(i & 0xff)
+                starts[i].record(stream)
+                step()
+                ends[i].record(stream)
+        torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)], clk.summary()
+
+
+def run_other_workload(args):
+    """Secondary workloads (not the headline line): `batch256` -- 256 images of
+    uneven sizes in one batch context -- and `3840x2160` -- one 4K image."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    from synth import voronoi_image
+    from synth.voronoi import batch_regions, batch_sizes
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    if args.workload == "batch256":
+        sizes = batch_sizes(256)
+        cache = {}
+        imgs = []
+        for i, (Wi, Hi) in enumerate(sizes):  # 4 distinct seeded images per size, reused
+            key = (Wi, Hi, i % 4)
+            if key not in cache:
+                cache[key] = torch.from_numpy(voronoi_image(Wi, Hi, batch_regions(Wi, Hi), 8.0, seed=i % 4)).cuda()
+            imgs.append(cache[key])
+        with torch.cuda.stream(stream):
+            bt = gm.SuperpixelsBatch([(h, w) for (w, h) in sizes], spacing=15, stream=stream)
+            bps, tune = bt.autotune(imgs, reps=3)
+        pix, K, cells = bt.info()
+        em_ms = tune[bps]
+        units = sum(candidate_units(w, h, 15, w // 15, h // 15) for (w, h) in sizes)
+        step = lambda: bt.segment(imgs, ITERS)
+        for _ in range(max(args.warmup, 3)):
+            with torch.cuda.stream(stream):
+                step()
+        step_ms, clocks = _timed_steps(step, stream, args.steps, flush, 0)
+        with torch.cuda.stream(stream):
+            _, ll = bt.segment(imgs, ITERS, want_loglik=True)
+        config = {"workload": f"batch of 256 synthetic Voronoi sRGB images, sizes uniform over "
+                              f"320x240/481x321/640x480/1280x720/1920x1080 (regions proportional to area, "
+                              f"sigma 8), spacing 15, {ITERS} plain-EM iterations, one batch context",
+                  "images": 256, "pixels": pix, "K": K, "cells": cells, "blocks_per_sm": bps,
+                  "l2": "flushed between timed steps (256 MiB memset)"}
+        launches = 2 + 2 * ITERS + 1
+        extra = {"loglik_mean_per_pixel": float(np.sum(ll)) / pix, "em_pass_autotune_ms": tune}
+        bt.close()
+    else:
+        Wd, Hd = 3840, 2160
+        img = torch.from_numpy(voronoi_image(Wd, Hd, 2000, 6.0, seed=0)).cuda()
+        labels = torch.empty((Hd, Wd), dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(stream):
+            sp = gm.Superpixels(img, K=20000, stream=stream)
+            sp.em_iters(2)
+            wpc, _ = sp.autotune(reps=3)
+        v, nx, ny, K = sp.grid.v, sp.grid.nx, sp.grid.ny, sp.grid.K
+        pix = Wd * Hd
+        step = lambda: sp.segment(img, ITERS, out=labels)
+        for _ in range(max(args.warmup, 3)):
+            with torch.cuda.stream(stream):
+                step()
+        step_ms, clocks = _timed_steps(step, stream, args.steps, flush, 0)
+        with torch.cuda.stream(stream):
+            _, ll = sp.segment(img, ITERS, out=labels, want_loglik=True)
+            em_ms = sp.profile_kernel(gm.GMMSP_KERNEL_EM_PASS, reps=10)
+            fin_ms = sp.profile_kernel(gm.GMMSP_KERNEL_FINALIZE, reps=10)
+        units = candidate_units(Wd, Hd, v, nx, ny)
+        config = {"workload": f"{Wd}x{Hd} synthetic Voronoi sRGB (2000 regions, sigma 6), K=20000 requested "
+                              f"-> v={v}, K={K}; {ITERS} plain-EM iterations", "W": Wd, "H": Hd, "K": K, "v": v,
+                  "warps_per_cell": wpc, "l2": "flushed between timed steps (256 MiB memset)"}
+        launches = 2 + 2 * ITERS + 1
+        extra = {"loglik_per_pixel": float(ll[-1]) / pix, "kernel_ms": {"em_pass": em_ms, "finalize": fin_ms}}
+        sp.close()
+    ms = sum(step_ms) / len(step_ms)
+    flops = units * FLOPS_PER_CAND
+    achieved = flops / (em_ms * 1e-3) / 1e12
+    line = {"metric": METRIC, "value": round(pix / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+            "data": "synthetic", "config": config,
+            "roofline": {"kernel": "E + M-partial pass", "bound": "alu", "achieved": round(achieved, 3),
+                         "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                         "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                         "em_pass_ms": round(em_ms, 4)},
+            "gpu_launches": launches * args.steps, "clocks": clocks, **extra}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """A short run for ncu captures: the bench workload, 4 EM iterations and the
     label pass, no timing (`--profile-case`)."""
@@ -355,11 +458,14 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run a short untimed case for ncu captures and exit")
     ap.add_argument("--warps-per-cell", type=int, default=0, help="with --profile-case: launch shape")
-    ap.add_argument("--workload", default="481x321", choices=["481x321", "3840x2160"],
-                    help="with --profile-case: image (481x321 K=1000, or 3840x2160 K=20000)")
+    ap.add_argument("--workload", default="481x321", choices=["481x321", "3840x2160", "batch256"],
+                    help="481x321 (the headline line); 3840x2160 or batch256 (secondary lines); "
+                         "with --profile-case the image to profile")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
+    if args.workload != "481x321" and args.impl == "gmmsp":
+        return run_other_workload(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gmmsp(args)
