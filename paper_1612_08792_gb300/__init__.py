@@ -372,6 +372,123 @@ def gmmsp_batch_destroy(b) -> None:
     _batch_lib().gmmsp_batch_destroy(b)
 
 
+def _net_lib():
+    lib = load_library()
+    if not getattr(lib, "_net_sigs", False):
+        P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        LL = ctypes.c_longlong
+        PD = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "gmmsp_net_param_count": (LL, []),
+            "gmmsp_net_create": (I, [PP, I, P]),
+            "gmmsp_net_set_weights": (I, [P, P, LL]),
+            "gmmsp_net_get_weights": (I, [P, P, LL]),
+            "gmmsp_net_forward": (I, [P, P, I, I, I, P]),
+            "gmmsp_net_grad": (I, [P, P, I, I, I, P, P, PD]),
+            "gmmsp_net_adam": (I, [P, F, F, F, F]),
+            "gmmsp_net_train_step": (I, [P, P, I, I, I, P, F, PD]),
+            "gmmsp_net_check": (I, [P]),
+            "gmmsp_net_get_activation": (I, [P, I, P, LL]),
+            "gmmsp_net_last_error": (ctypes.c_char_p, [P]),
+            "gmmsp_net_destroy": (None, [P]),
+            "gmmsp_init_from_net": (I, [P, P]),
+            "gmmsp_batch_set_init_net": (I, [P, P]),
+            "gmmsp_batch_lab": (I, [P, PP]),
+            "gmmsp_batch_targets": (I, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        lib._net_sigs = True
+    return lib
+
+
+def _ncheck(n, st):
+    if st != 0:
+        msg = (_net_lib().gmmsp_net_last_error(n) or b"").decode() if n else ""
+        raise GmmspError(st, msg)
+
+
+def gmmsp_net_param_count() -> int:
+    return int(_net_lib().gmmsp_net_param_count())
+
+
+def gmmsp_net_create(spacing: int, stream=None):
+    out = ctypes.c_void_p()
+    _ncheck(None, _net_lib().gmmsp_net_create(ctypes.byref(out), int(spacing), _stream_handle(stream)))
+    return out
+
+
+def gmmsp_net_set_weights(n, weights) -> None:
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _ncheck(n, _net_lib().gmmsp_net_set_weights(n, w.ctypes.data_as(ctypes.c_void_p), w.size))
+
+
+def gmmsp_net_get_weights(n):
+    w = np.zeros(gmmsp_net_param_count(), dtype=np.float32)
+    _ncheck(n, _net_lib().gmmsp_net_get_weights(n, w.ctypes.data_as(ctypes.c_void_p), w.size))
+    return w
+
+
+def gmmsp_net_forward(n, lab_ptr: int, B: int, W: int, H: int, out) -> None:
+    _ncheck(n, _net_lib().gmmsp_net_forward(n, int(lab_ptr), int(B), int(W), int(H), _dptr(out)))
+
+
+def gmmsp_net_grad(n, lab_ptr: int, B: int, W: int, H: int, target, want_grad: bool = True):
+    g = np.zeros(gmmsp_net_param_count(), dtype=np.float32) if want_grad else None
+    loss = ctypes.c_double()
+    _ncheck(n, _net_lib().gmmsp_net_grad(n, int(lab_ptr), int(B), int(W), int(H), _dptr(target),
+                                         g.ctypes.data_as(ctypes.c_void_p) if g is not None else None,
+                                         ctypes.byref(loss)))
+    return loss.value, g
+
+
+def gmmsp_net_adam(n, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+    _ncheck(n, _net_lib().gmmsp_net_adam(n, lr, beta1, beta2, eps))
+
+
+def gmmsp_net_train_step(n, lab_ptr: int, B: int, W: int, H: int, target, lr: float,
+                         want_loss: bool = True):
+    loss = ctypes.c_double()
+    _ncheck(n, _net_lib().gmmsp_net_train_step(n, int(lab_ptr), int(B), int(W), int(H), _dptr(target),
+                                               float(lr), ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def gmmsp_net_get_activation(n, layer: int, cells: int):
+    a = np.zeros((cells, 32), dtype=np.float32)
+    _ncheck(n, _net_lib().gmmsp_net_get_activation(n, int(layer), a.ctypes.data_as(ctypes.c_void_p), a.size))
+    return a
+
+
+def gmmsp_net_check(n) -> None:
+    _ncheck(n, _net_lib().gmmsp_net_check(n))
+
+
+def gmmsp_net_destroy(n) -> None:
+    _net_lib().gmmsp_net_destroy(n)
+
+
+def gmmsp_init_from_net(ctx, n) -> None:
+    _check(ctx, _net_lib().gmmsp_init_from_net(ctx, n))
+
+
+def gmmsp_batch_set_init_net(b, n) -> None:
+    _bcheck(b, _net_lib().gmmsp_batch_set_init_net(b, n))
+
+
+def gmmsp_batch_lab(b) -> int:
+    p = ctypes.c_void_p()
+    _bcheck(b, _net_lib().gmmsp_batch_lab(b, ctypes.byref(p)))
+    return int(p.value or 0)
+
+
+def gmmsp_batch_targets(b, target) -> None:
+    _bcheck(b, _net_lib().gmmsp_batch_targets(b, _dptr(target)))
+
+
 class SuperpixelsBatch:
     """A batch context over lists of (H, W, 3) uint8 RGB (or float32 CIELAB) CUDA tensors."""
 
@@ -408,6 +525,19 @@ class SuperpixelsBatch:
 
     def get_params(self, i: int, K: int):
         return gmmsp_batch_get_params(self.b, i, K)
+
+    def set_init_net(self, net) -> None:
+        """Start every later segment from the network's theta_0 (None: the paper's start)."""
+        gmmsp_batch_set_init_net(self.b, net.n if net is not None else None)
+        self._net = net
+
+    def lab_ptr(self) -> int:
+        """Device address of the batch's CIELAB planes (filled by segment)."""
+        return gmmsp_batch_lab(self.b)
+
+    def targets(self, out) -> None:
+        """Training targets from the current theta into out (float32 CUDA, B K x 10)."""
+        gmmsp_batch_targets(self.b, out)
 
     def close(self) -> None:
         if getattr(self, "b", None):
@@ -530,6 +660,10 @@ class Superpixels:
 
     def get_lab(self):
         return gmmsp_get_lab(self.ctx, self.H, self.W)
+
+    def init_from_net(self, net) -> None:
+        """Replace theta by the network's theta_0 for the current image."""
+        gmmsp_init_from_net(self.ctx, net.n)
 
     def get_params(self):
         return gmmsp_get_params(self.ctx)

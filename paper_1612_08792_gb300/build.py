@@ -37,7 +37,7 @@ def _sources():
 def _fingerprint() -> str:
     h = hashlib.sha256()
     files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
-        os.path.join(ROOT, "include", "gmmsp.h"), os.path.join(ROOT, "include", "gmmsp_probe.h"),
+        *sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))),
         os.path.abspath(__file__)]
     for f in files:
         h.update(f.encode())

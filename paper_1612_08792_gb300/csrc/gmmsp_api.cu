@@ -21,6 +21,8 @@
 #include <vector>
 
 #include "../../include/gmmsp.h"
+#include "../../include/gmmsp_cnn.h"
+#include "gmmsp_cnn_internal.cuh"
 #include "gmmsp_internal.cuh"
 
 using gmmsp::Geom;
@@ -508,6 +510,21 @@ gmmsp_status gmmsp_set_params(gmmsp_ctx c, const double* mu_host, const double* 
     c->err = std::to_string(bad) + " superpixels with non-finite or non-SPD parameters";
     return GMMSP_E_NUMERIC;  // theta is left as given; the caller should set valid parameters
   }
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_init_from_net(gmmsp_ctx c, gmmsp_net n) {
+  gmmsp_status st = check_ready(c);
+  if (st != GMMSP_OK) return st;
+  if (!n) return fail(c, GMMSP_E_INVALID, "null network");
+  std::string why;
+  st = gmmsp::net_reserve(n, 1, c->g, &why);
+  if (st != GMMSP_OK) {
+    c->err = why;  // the network's failure: the context stays usable
+    return st;
+  }
+  GM_CHECK(c, gmmsp::net_enqueue_init(n, c->lab, 1, c->g, c->p.lambda_c, c->p.eps_s, c->p.eps_c, c->theta, c->gp,
+                                      c->counters, c->stream));
   return GMMSP_OK;
 }
 

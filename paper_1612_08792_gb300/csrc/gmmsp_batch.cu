@@ -19,6 +19,8 @@
 #include <vector>
 
 #include "../../include/gmmsp.h"
+#include "../../include/gmmsp_cnn.h"
+#include "gmmsp_cnn_internal.cuh"
 #include "gmmsp_internal.cuh"
 
 using gmmsp::BatchImage;
@@ -42,10 +44,14 @@ struct gmmsp_batch_s {
   double* img_ll = nullptr;
   BatchImage* table = nullptr;
   unsigned long long* counters = nullptr;
+  gmmsp_net net = nullptr;         // learned initialiser (null: Sec. III-C start)
+  bool uniform = true;             // all images of one size
   cudaGraphExec_t exec = nullptr;
   int g_iters = -1;
   bool g_ll = false;
   int g_bps = -1;
+  gmmsp_net g_net = nullptr;
+  long long g_gen = -1;
   std::string err;
   gmmsp_status state = GMMSP_OK;
 };
@@ -109,9 +115,14 @@ gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
   const int prep_blocks = int(std::min<long long>((b->total_rows + 7) / 8, (long long)b->sm_count * 8));
   GB_CHECK(b, gmmsp::launch_prepare_batch(b->table, n, b->total_rows, b->p.input_format, b->lab, b->counters,
                                           prep_blocks, s));
-  const int kblocks = int(std::min<long long>((b->total_k + 127) / 128, (long long)b->sm_count * 8));
-  GB_CHECK(b, gmmsp::launch_init_batch(b->table, n, b->total_k, b->lab, b->p.lambda_c, b->theta, b->gp,
-                                       kblocks, s));
+  if (b->net) {
+    GB_CHECK(b, gmmsp::net_enqueue_init(b->net, b->lab, n, b->host[0].g, b->p.lambda_c, b->p.eps_s, b->p.eps_c,
+                                        b->theta, b->gp, b->counters, s));
+  } else {
+    const int kblocks = int(std::min<long long>((b->total_k + 127) / 128, (long long)b->sm_count * 8));
+    GB_CHECK(b, gmmsp::launch_init_batch(b->table, n, b->total_k, b->lab, b->p.lambda_c, b->theta, b->gp,
+                                         kblocks, s));
+  }
   const int eb = em_blocks(b);
   const int fblocks = int(std::min<long long>((b->total_k + 31) / 32, (long long)b->sm_count * 16));
   for (int t = 0; t < iters; ++t) {
@@ -182,6 +193,7 @@ gmmsp_status gmmsp_batch_create(gmmsp_batch* out, int n, const int* widths, cons
     im.row_off = int(rows);
     im.cell_off = int(cells);
     im.k_off = int(ks);
+    if (g.W != b->host[0].g.W || g.H != b->host[0].g.H) b->uniform = false;
     pix += (long long)g.W * g.H;
     rows += g.H;
     cells += g.ncells;
@@ -253,7 +265,9 @@ gmmsp_status gmmsp_batch_segment(gmmsp_batch b, const void* const* images_dev, c
     st = enqueue_batch(b, iters, want_ll);
     if (st != GMMSP_OK) return st;
   } else {
-    if (!(b->exec && b->g_iters == iters && b->g_ll == want_ll && b->g_bps == b->blocks_per_sm)) {
+    const long long gen = gmmsp::net_generation(b->net);
+    if (!(b->exec && b->g_iters == iters && b->g_ll == want_ll && b->g_bps == b->blocks_per_sm &&
+          b->g_net == b->net && b->g_gen == gen)) {
       drop_graph(b);
       GB_CHECK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       st = enqueue_batch(b, iters, want_ll);
@@ -273,6 +287,8 @@ gmmsp_status gmmsp_batch_segment(gmmsp_batch b, const void* const* images_dev, c
       b->g_iters = iters;
       b->g_ll = want_ll;
       b->g_bps = b->blocks_per_sm;
+      b->g_net = b->net;
+      b->g_gen = gen;
     }
     GB_CHECK(b, cudaGraphLaunch(b->exec, b->stream));
   }
@@ -348,6 +364,32 @@ gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void* const* images_dev, 
   cudaEventDestroy(e1);
   b->blocks_per_sm = best_c;
   if (best) *best = best_c;
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_batch_set_init_net(gmmsp_batch b, gmmsp_net net) {
+  if (!b) return GMMSP_E_INVALID;
+  if (net) {
+    if (!b->uniform) return bfail(b, GMMSP_E_INVALID, "a learned start needs images of one size");
+    std::string why;
+    const gmmsp_status st = gmmsp::net_reserve(net, b->n, b->host[0].g, &why);
+    if (st != GMMSP_OK) return bfail(b, st == GMMSP_E_INVALID ? GMMSP_E_INVALID : st, why);
+  }
+  b->net = net;
+  drop_graph(b);
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_batch_lab(gmmsp_batch b, const float** lab_dev) {
+  if (!b || !lab_dev) return GMMSP_E_INVALID;
+  *lab_dev = b->lab;
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_batch_targets(gmmsp_batch b, float* target_dev) {
+  if (!b || !target_dev) return GMMSP_E_INVALID;
+  if (!b->uniform) return bfail(b, GMMSP_E_INVALID, "targets need images of one size");
+  GB_CHECK(b, gmmsp::launch_targets(b->theta, b->lab, b->n, b->host[0].g, b->p.lambda_c, target_dev, b->stream));
   return GMMSP_OK;
 }
 

@@ -1,0 +1,35 @@
+// Library-internal entry points of the learned initialiser, used by the
+// single-image context and the batch context.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/gmmsp.h"
+#include "../../include/gmmsp_cnn.h"
+#include "gmmsp_internal.cuh"
+
+namespace gmmsp {
+
+// Checks that the network fits B images of geometry g (same spacing) and
+// reserves its inference workspace.  Must not be called during stream capture.
+gmmsp_status net_reserve(gmmsp_net n, int B, const Geom& g, std::string* why);
+
+// Changes whenever the network's workspace moves (captured graphs must be
+// re-captured then).
+long long net_generation(gmmsp_net n);
+
+// Enqueues the network on B CIELAB images (planes of W H floats, image after
+// image) and writes theta_0 and the packed coefficients of all B K
+// superpixels.  A non-finite theta_0 counts into counters[CNT_NONFINITE].
+cudaError_t net_enqueue_init(gmmsp_net n, const float* lab, int B, const Geom& g, double lambda_c, double eps_s,
+                             double eps_c, double* theta, float* gp, unsigned long long* counters,
+                             cudaStream_t s);
+
+// Training targets (GMMSP_NET_OUTPUTS floats per superpixel) from fitted
+// parameters theta of B images of geometry g.
+cudaError_t launch_targets(const double* theta, const float* lab, int B, const Geom& g, double lambda_c,
+                           float* target, cudaStream_t s);
+
+}  // namespace gmmsp

@@ -65,3 +65,16 @@ def test_null_context_calls(lib):
     assert lib.gmmsp_em_iters(None, 1, None) == 1
     assert lib.gmmsp_labels(None, None, None) == 1
     lib.gmmsp_destroy(None)
+
+
+def test_network_host_checks(lib):
+    # parameter count without a device; bad spacings and null handles rejected on the host
+    assert lib.gmmsp_net_param_count() == 34480
+    out = ctypes.c_void_p(1234)
+    for sp in (0, 2, 14, 36):
+        assert lib.gmmsp_net_create(ctypes.byref(out), sp, None) == 1
+        assert out.value is None
+    assert lib.gmmsp_net_set_weights(None, None, 0) == 1
+    assert lib.gmmsp_net_check(None) == 1
+    assert lib.gmmsp_batch_set_init_net(None, None) == 1
+    assert lib.gmmsp_init_from_net(None, None) == 1
