@@ -1,18 +1,24 @@
 #!/usr/bin/env python
 """End-to-end throughput of GMM superpixel EM (Ban, Liu, Cao, arXiv 1612.08792) on one GB300.
 
-A step is Algorithm 1, steps 1-7, on one synthetic 481x321 sRGB image
-(150 Voronoi regions, noise sigma 8; K = 1000 requested -> v = 12, K = 1040),
-10 EM iterations: CIELAB conversion, initialisation, 10 x (fused E-step +
-M-step partial sums, FP64 finalize with the eigenvalue floor), label pass
-with its log-likelihood.  The step is one CUDA-graph launch of the library
-(`gmmsp_segment`).  `value` is device time with the image already in HBM
-and L2 flushed (256 MiB memset) between timed steps; `e2e` adds the pinned
-host->device copy of the image and the device->host copy of the labels.
+Headline line (default, `--workload learned481`): the learned initialiser
+against plain EM at equal log-likelihood.  A step is Algorithm 1 on a batch
+of 256 held-out synthetic 481x321 sRGB images (150 Voronoi regions, noise
+sigma 8, seeds 1,000,000 + i) at spacing 15: CIELAB conversion, the trained
+network's theta_0, 2 EM iterations (fused E-step + M-step partial sums, FP64
+finalize with the eigenvalue floor), label pass -- one CUDA-graph launch of
+the batch context.  The same images also run through plain EM (Sec. III-C
+start, 10 iterations) for the ratio and the log-likelihood comparison.
+`value` is device time with the images already in HBM and L2 flushed
+(256 MiB memset) between timed steps; `e2e` adds the pinned host->device copy
+of the images and the device->host copy of the labels.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmmsp|reference]
+Other lines: `--workload 481x321` (one image, K = 1000 -> v = 12, plain EM,
+10 iterations), `batch256` (256 images of uneven sizes), `3840x2160`.
 
-With N > 1 (torchrun) each rank runs an independent replica on its own image
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmmsp|reference] [--workload ...]
+
+With N > 1 (torchrun) each rank runs an independent replica on its own images
 (no collective on the data path: the images are independent problems);
 `value` is all ranks' pixels over the slowest rank's time.
 `--impl reference` times the FP64 CPU oracle on the host cores instead.
@@ -423,6 +429,253 @@ def run_other_workload(args):
     return 0
 
 
+# ---------------------------------------------------------------- learned start
+LEARN_IMAGES, LEARN_V, LEARN_T, HELD_OUT0 = 256, 15, 2, 1_000_000
+# Algorithmic tensor-core work of the network per 481 x 321 image at spacing 15
+# (32 x 21 cells, 5 x 5 patches each): two 1 x 1 layers per patch (27 -> 32,
+# 32 -> 32) and four 3 x 3 layers per cell (288 -> 32 three times, 288 -> 16).
+NET_FLOPS_PER_PATCH = 2 * (27 * 32 + 32 * 32)
+NET_FLOPS_PER_CELL = 2 * (3 * 288 * 32 + 288 * 16)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def learned_config(n, bps):
+    return {
+        "workload": f"{n} held-out synthetic {W}x{H} Voronoi sRGB images per step ({REGIONS} regions, noise "
+                    f"sigma {SIGMA:g}, seeds {HELD_OUT0}+i), spacing {LEARN_V} (32x21 = 672 superpixels); "
+                    f"learned theta_0 + {LEARN_T} EM iterations vs the Sec. III-C start + {ITERS} iterations",
+        "images": n, "W": W, "H": H, "v": LEARN_V, "K": 672, "iters_learned": LEARN_T, "iters_plain": ITERS,
+        "network": "6-layer conv initialiser, BF16 weights/activations, FP32 accumulation (tcgen05)",
+        "precision": "FP32 E-step, FP64 sufficient statistics / floor / inversion",
+        "l2": "flushed between timed steps (256 MiB memset, outside the timed interval); inputs > L2",
+        "blocks_per_sm": bps,
+    }
+
+
+def oracle_learned_sample(weights, seconds, seed0=HELD_OUT0):
+    """The oracle as it stands on the learned workload: FP64 CIELAB, the FP64
+    network, its theta_0 and 2 EM iterations, image after image until about
+    `seconds` of that work (image generation not counted).  Returns
+    (Mpixel/s, threads, images, seconds)."""
+    import oracle
+    from oracle import cnn as ocnn
+    from synth import voronoi_image
+    threads = oracle.max_threads()
+    n, el = 0, 0.0
+    while True:
+        img = voronoi_image(W, H, REGIONS, SIGMA, seed0 + n)
+        t0 = time.perf_counter()
+        lab = oracle.rgb2lab(img)
+        planes = lab.transpose(2, 0, 1)
+        out, _ = ocnn.forward(weights, planes[None], LEARN_V)
+        mu, cs, cc = ocnn.theta0_from_outputs(out[0].reshape(-1, 16), planes, LEARN_V)
+        oracle.em(lab, W, H, spacing=LEARN_V, T=LEARN_T, theta0=oracle.Theta(mu, cs, cc))
+        el += time.perf_counter() - t0
+        n += 1
+        if el >= seconds:
+            break
+    return W * H * n / el / 1e6, threads, n, el
+
+
+def run_learned(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    from paper_1612_08792_gb300.learned_init import load_pretrained, pretrained_path
+    from synth.voronoi_torch import voronoi_batch
+
+    n = args.images
+    N = W * H
+    seeds = range(HELD_OUT0 + rank * n, HELD_OUT0 + (rank + 1) * n)
+    buf = voronoi_batch(W, H, REGIONS, SIGMA, seeds)
+    imgs = [buf[i] for i in range(n)]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        net = load_pretrained(LEARN_V, stream=stream)
+        plain = gm.SuperpixelsBatch([(H, W)] * n, spacing=LEARN_V, stream=stream)
+        bps, tune = plain.autotune(imgs, reps=3)
+        learned = gm.SuperpixelsBatch([(H, W)] * n, spacing=LEARN_V, stream=stream)
+        learned.set_launch(bps)
+        learned.set_init_net(net)
+    step_l = lambda: learned.segment(imgs, LEARN_T)  # noqa: E731
+    step_p = lambda: plain.segment(imgs, ITERS)  # noqa: E731
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step_l()
+            step_p()
+    stream.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    barrier()
+    ms_l, clocks = _timed_steps(step_l, stream, args.steps, flush, local)
+    barrier()
+    ms_p, clocks_p = _timed_steps(step_p, stream, max(3, args.steps // 3), flush, local)
+    barrier()
+    t_l = max_over_ranks(sum(ms_l) / len(ms_l))
+    t_p = max_over_ranks(sum(ms_p) / len(ms_p))
+    value = world * n * N / (t_l * 1e-3) / 1e6
+    plain_value = world * n * N / (t_p * 1e-3) / 1e6
+
+    # log-likelihood (equal-log-lik check) and label agreement with plain EM
+    with torch.cuda.stream(stream):
+        lab_l, ll_l = learned.segment(imgs, LEARN_T, want_loglik=True)
+        lab_l = [x.clone() for x in lab_l]
+        lab_p, ll_p = plain.segment(imgs, ITERS, want_loglik=True)
+        agree = float(sum(int((a == b).sum().item()) for a, b in zip(lab_l, lab_p))) / (n * N)
+        _, ll_p2 = plain.segment(imgs, LEARN_T, want_loglik=True)
+    llpp_l, llpp_p, llpp_p2 = (float(np.mean(x)) / N for x in (ll_l, ll_p, ll_p2))
+    gap = abs(llpp_l - llpp_p) / abs(llpp_p)
+
+    # the network alone (events on its stream) and the E + M pass at the chosen launch shape
+    lab_ptr = learned.lab_ptr()
+    with torch.cuda.stream(stream):
+        learned.segment(imgs, LEARN_T)
+        out = net.forward(lab_ptr, n, W, H)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        e0.record(stream)
+        reps = 20
+        for _ in range(reps):
+            gm.gmmsp_net_forward(net.n, lab_ptr, n, W, H, out)
+        e1.record(stream)
+    stream.synchronize()
+    net_ms = e0.elapsed_time(e1) / reps
+    net.check()
+    net_flops = n * (672 * 25 * NET_FLOPS_PER_PATCH + 672 * NET_FLOPS_PER_CELL)
+    em_ms = tune[bps]
+    units = n * candidate_units(W, H, LEARN_V, W // LEARN_V, H // LEARN_V)
+    flops = units * FLOPS_PER_CAND + n * N * FLOPS_PER_PIXEL
+    achieved = flops / (em_ms * 1e-3) / 1e12
+
+    # end to end through the public API: pinned host images in, host labels out
+    host_imgs = buf.cpu().pin_memory()
+    host_labels = torch.empty((n, H, W), dtype=torch.int32).pin_memory()
+    dev_in = torch.empty_like(buf)
+    dev_list = [dev_in[i] for i in range(n)]
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            dev_in.copy_(host_imgs, non_blocking=True)
+            labs = learned.segment(dev_list, LEARN_T)
+            for i in range(n):
+                host_labels[i].copy_(labs[i], non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 4)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = world * n * N * e2e_steps / e2e_s / 1e6
+
+    peaks = measured_peaks()
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    net_tflops = net_flops / (net_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(t_l, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 (EM), bf16 (net)",
+        "data": "synthetic", "config": dict(learned_config(n, bps), parallelism=f"replicas x{world}"),
+        "plain_em": {"value": round(plain_value, 3), "unit": UNIT, "ms_per_step": round(t_p, 5),
+                     "iters": ITERS, "steps": len(ms_p)},
+        "speedup_vs_plain": round(value / plain_value, 3),
+        "loglik_per_pixel": {"learned": llpp_l, "plain": llpp_p, f"plain_{LEARN_T}_iters": llpp_p2,
+                             "rel_gap": gap, "target": 0.005},
+        "label_agreement_with_plain": round(agree, 5),
+        "roofline": {"kernel": "k_em_pass_batch (fused E-step + M-step partials)", "bound": "alu",
+                     "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "em_pass_ms": round(em_ms, 5), "flops_per_launch": flops,
+                     "timing": "batch E+M pass alone, mean of repeated launches (autotuner)"},
+        "net_roofline": {"kernels": "k_pix + 4 x k_gemm (forward)", "bound": "tensor",
+                         "achieved": round(net_tflops, 3), "peak": bf16_peak, "unit": "TFLOP/s",
+                         "frac": round(net_tflops / bf16_peak, 5), "ms": round(net_ms, 5),
+                         "flops_per_launch": net_flops,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else "fallback"},
+        "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": n * N * 3,
+                "d2h_bytes_per_step": n * N * 4},
+        "gpu_launches": (1 + 5 + 1 + 2 * LEARN_T + 1) * args.steps,
+        "clocks": clocks, "clocks_plain": clocks_p,
+        "weights": os.path.relpath(pretrained_path(LEARN_V), ROOT),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        w = np.load(pretrained_path(LEARN_V))["weights"]
+        mpx, threads, imgs_done, el = oracle_learned_sample(w, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": round(mpx, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{imgs_done} held-out images of the workload in {el:.1f} s (FP64 CIELAB, "
+                                          f"FP64 network, theta_0, {LEARN_T} EM iterations, labels; C oracle "
+                                          f"with OpenMP {threads} threads, numpy network)"}
+    learned.close()
+    plain.close()
+    net.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference_learned(args):
+    """The oracle on the learned workload, each step one held-out image."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_1612_08792_gb300.learned_init import pretrained_path
+    w = np.load(pretrained_path(LEARN_V))["weights"]
+    oracle_learned_sample(w, 0.0, HELD_OUT0 + 10_000)      # warm-up (one image)
+    el = 0.0
+    for i in range(args.steps):
+        el += oracle_learned_sample(w, 0.0, HELD_OUT0 + i)[3]
+    import oracle
+    threads = oracle.max_threads()
+    value = W * H * args.steps / el / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": learned_config(1, None),
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} steps of one held-out {W}x{H} image each (FP64 CIELAB, FP64 "
+                                   f"network, theta_0, {LEARN_T} EM iterations, labels)"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """A short run for ncu captures: the bench workload, 4 EM iterations and the
     label pass, no timing (`--profile-case`)."""
@@ -431,6 +684,23 @@ def run_profile_case(args):
     __graft_entry__.build()
     import paper_1612_08792_gb300 as gm
     from synth import voronoi_image
+    if args.workload == "learned481":
+        # `--images` held-out images through the learned start + 2 iterations, twice
+        from paper_1612_08792_gb300.learned_init import load_pretrained
+        from synth.voronoi_torch import voronoi_batch
+        buf = voronoi_batch(W, H, REGIONS, SIGMA, range(HELD_OUT0, HELD_OUT0 + args.images))
+        imgs = [buf[i] for i in range(args.images)]
+        net = load_pretrained(LEARN_V)
+        bt = gm.SuperpixelsBatch([(H, W)] * args.images, spacing=LEARN_V)
+        bt.set_init_net(net)
+        for _ in range(2):
+            bt.segment(imgs, LEARN_T)
+        torch.cuda.synchronize()
+        net.check()
+        bt.close()
+        net.close()
+        print("profile case done", args.images)
+        return 0
     if args.workload == "3840x2160":
         img = torch.from_numpy(voronoi_image(3840, 2160, 2000, 6.0, seed=0)).cuda()
         sp = gm.Superpixels(img, K=20000)
@@ -458,12 +728,16 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run a short untimed case for ncu captures and exit")
     ap.add_argument("--warps-per-cell", type=int, default=0, help="with --profile-case: launch shape")
-    ap.add_argument("--workload", default="481x321", choices=["481x321", "3840x2160", "batch256"],
-                    help="481x321 (the headline line); 3840x2160 or batch256 (secondary lines); "
-                         "with --profile-case the image to profile")
+    ap.add_argument("--workload", default="learned481",
+                    choices=["learned481", "481x321", "3840x2160", "batch256"],
+                    help="learned481 (the headline line); 481x321, 3840x2160 or batch256 (other lines); "
+                         "with --profile-case the case to profile")
+    ap.add_argument("--images", type=int, default=LEARN_IMAGES, help="learned481: images per step")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
+    if args.workload == "learned481":
+        return run_reference_learned(args) if args.impl == "reference" else run_learned(args)
     if args.workload != "481x321" and args.impl == "gmmsp":
         return run_other_workload(args)
     if args.impl == "reference":
