@@ -53,6 +53,18 @@ FLOPS_PER_CAND = 61
 FLOPS_PER_PIXEL = 1
 # FP32 peak derived from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# The binding roofline of the E + M pass is the FP32 pipe's instruction rate (most of
+# its operations are single adds and multiplies, so flops understate the work):
+# algorithmic FP32-pipe lane-instructions per (pixel, candidate), from the formulas --
+#   E: d = z - mu (5), the two quadratic forms (14), running max (1), exponent
+#      shift (1), sum (1), normalisation (1)                                  -> 23
+#   M: d = z - mu_old (5), W += R (1), R d (5), S1 += R d (5), the 9 block
+#      second moments (9)                                                      -> 25
+# plus 2 per pixel (log-likelihood adds); MUFU (ex2 per candidate, rcp and lg2 per
+# pixel) runs on its own pipe.  Peak: 152 SMs x 128 FP32 lanes x 2.07 GHz.
+INSTR_PER_CAND = 48
+INSTR_PER_PIXEL = 2
+FP32_PEAK_TINST = 152 * 128 * 2.070e9 / 1e12
 
 
 def workload_config(v, nx, ny, K):
@@ -436,6 +448,10 @@ LEARN_IMAGES, LEARN_V, LEARN_T, HELD_OUT0 = 256, 15, 2, 1_000_000
 # 32 -> 32) and four 3 x 3 layers per cell (288 -> 32 three times, 288 -> 16).
 NET_FLOPS_PER_PATCH = 2 * (27 * 32 + 32 * 32)
 NET_FLOPS_PER_CELL = 2 * (3 * 288 * 32 + 288 * 16)
+# DRAM bytes per 481 x 321 image of one batched E + M pass, from the ncu capture of
+# k_em_pass_batch on 96 such images (dram__bytes_read.sum + dram__bytes_write.sum =
+# 182.04 MB + 52.66 MB), scaled per image (traffic grows with the image count).
+EM_BATCH_TRAFFIC_PER_IMAGE = int((182.039296e6 + 52.660480e6) / 96)
 
 
 def measured_peaks():
@@ -510,8 +526,11 @@ def run_learned(args):
         plain = gm.SuperpixelsBatch([(H, W)] * n, spacing=LEARN_V, stream=stream)
         bps, tune = plain.autotune(imgs, reps=3)
         learned = gm.SuperpixelsBatch([(H, W)] * n, spacing=LEARN_V, stream=stream)
+        learned.autotune(imgs, reps=3)
         learned.set_launch(bps)
         learned.set_init_net(net)
+        tuning = {"plain": plain.tuning(), "learned": learned.tuning(),
+                  "em_pass_ms_by_blocks_per_sm": {str(k): round(v_, 5) for k, v_ in tune.items()}}
     step_l = lambda: learned.segment(imgs, LEARN_T)  # noqa: E731
     step_p = lambda: plain.segment(imgs, ITERS)  # noqa: E731
     with torch.cuda.stream(stream):
@@ -573,6 +592,8 @@ def run_learned(args):
     units = n * candidate_units(W, H, LEARN_V, W // LEARN_V, H // LEARN_V)
     flops = units * FLOPS_PER_CAND + n * N * FLOPS_PER_PIXEL
     achieved = flops / (em_ms * 1e-3) / 1e12
+    instr = units * INSTR_PER_CAND + n * N * INSTR_PER_PIXEL
+    achieved_i = instr / (em_ms * 1e-3) / 1e12
 
     # end to end through the public API: pinned host images in, host labels out
     host_imgs = buf.cpu().pin_memory()
@@ -613,11 +634,16 @@ def run_learned(args):
                              "rel_gap": gap, "target": 0.005},
         "label_agreement_with_plain": round(agree, 5),
         "roofline": {"kernel": "k_em_pass_batch (fused E-step + M-step partials)", "bound": "alu",
-                     "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                     "em_pass_ms": round(em_ms, 5), "flops_per_launch": flops,
+                     "achieved": round(achieved_i, 3), "peak": round(FP32_PEAK_TINST, 3),
+                     "unit": "T FP32-lane-instr/s", "frac": round(achieved_i / FP32_PEAK_TINST, 4),
+                     "traffic": EM_BATCH_TRAFFIC_PER_IMAGE * n if bps < 6 else None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (one FP32 instruction per "
+                                    "lane per clock)",
+                     "em_pass_ms": round(em_ms, 5), "instr_per_launch": instr,
+                     "flops": {"achieved_tflops": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                               "frac": round(achieved / FP32_PEAK_TFLOPS, 4)},
                      "timing": "batch E+M pass alone, mean of repeated launches (autotuner)"},
+        "tuning": tuning,
         "net_roofline": {"kernels": "k_pix + 4 x k_gemm (forward)", "bound": "tensor",
                          "achieved": round(net_tflops, 3), "peak": bf16_peak, "unit": "TFLOP/s",
                          "frac": round(net_tflops / bf16_peak, 5), "ms": round(net_ms, 5),

@@ -246,6 +246,11 @@ gmmsp_status gmmsp_batch_get_params(gmmsp_batch b, int i, double *mu_host, doubl
 gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void *const *images_dev, const int *pitches,
                                   int32_t *const *labels_dev, int reps, int *best, double *times_ms);
 gmmsp_status gmmsp_batch_set_launch(gmmsp_batch b, int blocks_per_sm);
+/* Launch choices of b: blocks per SM of the E + M pass, whether the finalize
+ * runs 16 lanes per superpixel (1) or one thread per superpixel (0), and the
+ * two finalize times the autotuner measured (ms; 0 before gmmsp_batch_autotune).
+ * Any pointer may be NULL. */
+gmmsp_status gmmsp_batch_get_tuning(gmmsp_batch b, int *blocks_per_sm, int *finalize16, double *finalize_ms);
 gmmsp_status gmmsp_batch_info(gmmsp_batch b, long long *total_pixels, int *total_k, int *total_cells);
 const char *gmmsp_batch_last_error(gmmsp_batch b);
 void gmmsp_batch_destroy(gmmsp_batch b);

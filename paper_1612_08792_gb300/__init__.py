@@ -298,6 +298,7 @@ def _batch_lib():
             "gmmsp_batch_autotune": (I, [P, P, P, P, I, pint, P]),
             "gmmsp_batch_set_launch": (I, [P, I]),
             "gmmsp_batch_info": (I, [P, ctypes.POINTER(ctypes.c_longlong), pint, pint]),
+            "gmmsp_batch_get_tuning": (I, [P, pint, pint, P]),
             "gmmsp_batch_last_error": (ctypes.c_char_p, [P]),
             "gmmsp_batch_destroy": (None, [P]),
         }
@@ -366,6 +367,15 @@ def gmmsp_batch_info(b):
     pix, K, cells = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
     _bcheck(b, _batch_lib().gmmsp_batch_info(b, ctypes.byref(pix), ctypes.byref(K), ctypes.byref(cells)))
     return pix.value, K.value, cells.value
+
+
+def gmmsp_batch_get_tuning(b):
+    bps, f16 = ctypes.c_int(), ctypes.c_int()
+    ms = np.zeros(2)
+    _bcheck(b, _batch_lib().gmmsp_batch_get_tuning(b, ctypes.byref(bps), ctypes.byref(f16),
+                                                   ms.ctypes.data_as(ctypes.c_void_p)))
+    return {"blocks_per_sm": bps.value, "finalize16": bool(f16.value),
+            "finalize_ms": {"16_lanes": float(ms[0]), "thread_per_superpixel": float(ms[1])}}
 
 
 def gmmsp_batch_destroy(b) -> None:
@@ -522,6 +532,9 @@ class SuperpixelsBatch:
 
     def info(self):
         return gmmsp_batch_info(self.b)
+
+    def tuning(self):
+        return gmmsp_batch_get_tuning(self.b)
 
     def get_params(self, i: int, K: int):
         return gmmsp_batch_get_params(self.b, i, K)

@@ -31,7 +31,10 @@ struct gmmsp_batch_s {
   gmmsp_params p{};
   cudaStream_t stream = nullptr;
   int sm_count = 152;
-  int blocks_per_sm = 4;           // persistent grid of the per-cell passes (autotuned)
+  int blocks_per_sm = 4;           // persistent grid of the E + M pass (autotuned)
+  int label_blocks_per_sm = 4;     // persistent grid of the label pass (its occupancy)
+  bool fin16 = true;               // finalize with 16 lanes per superpixel (autotuned)
+  double fin_ms[2] = {0.0, 0.0};   // autotuned finalize times: 16 lanes, one thread per superpixel
   std::vector<BatchImage> host;    // the table as last uploaded
   long long total_pix = 0;
   int total_rows = 0, total_cells = 0, total_k = 0;
@@ -127,12 +130,14 @@ gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
   const int fblocks = int(std::min<long long>((b->total_k + 31) / 32, (long long)b->sm_count * 16));
   for (int t = 0; t < iters; ++t) {
     GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, n, b->total_cells, b->lab, b->gp, b->partials,
-                                            b->p.precision, eb, s));
+                                            b->p.precision, eb, b->blocks_per_sm, s));
     GB_CHECK(b, gmmsp::launch_finalize_batch(b->table, n, b->total_k, b->partials, b->theta, b->gp,
                                              b->p.eps_s, b->p.eps_c, b->counters, b->p.precision,
-                                             fblocks, s));
+                                             b->fin16 ? 0 : fblocks, s));
   }
-  GB_CHECK(b, gmmsp::launch_label_pass_batch(b->table, n, b->total_cells, b->lab, b->gp, b->cell_ll, eb, s));
+  const long long lneed = (b->total_cells + 3) / 4;
+  const int lb = int(std::min<long long>(lneed, (long long)b->sm_count * b->label_blocks_per_sm));
+  GB_CHECK(b, gmmsp::launch_label_pass_batch(b->table, n, b->total_cells, b->lab, b->gp, b->cell_ll, lb, s));
   if (want_ll) GB_CHECK(b, gmmsp::launch_ll_per_image(b->table, n, b->cell_ll, b->img_ll, s));
   return GMMSP_OK;
 }
@@ -214,6 +219,7 @@ gmmsp_status gmmsp_batch_create(gmmsp_batch* out, int n, const int* widths, cons
     return GMMSP_E_CUDA;
   }
   b->sm_count = prop.multiProcessorCount;
+  b->label_blocks_per_sm = std::max(1, gmmsp::label_pass_batch_occupancy());
   const size_t pbytes = size_t(cells) * gmmsp::kPartStride * (p->precision == GMMSP_PREC_FP32 ? 4 : 8);
   size_t off = 0;
   const size_t o_lab = off;   off += up256(3 * size_t(pix) * sizeof(float));
@@ -241,6 +247,17 @@ gmmsp_status gmmsp_batch_create(gmmsp_batch* out, int n, const int* widths, cons
   b->table = reinterpret_cast<BatchImage*>(base + o_tab);
   b->counters = reinterpret_cast<unsigned long long*>(base + o_cnt);
   *out = b;
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_batch_get_tuning(gmmsp_batch b, int* blocks_per_sm, int* finalize16, double* finalize_ms) {
+  if (!b) return GMMSP_E_INVALID;
+  if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+  if (finalize16) *finalize16 = (b->fin16 && b->p.precision != GMMSP_PREC_FP32) ? 1 : 0;
+  if (finalize_ms) {
+    finalize_ms[0] = b->fin_ms[0];
+    finalize_ms[1] = b->fin_ms[1];
+  }
   return GMMSP_OK;
 }
 
@@ -347,11 +364,11 @@ gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void* const* images_dev, 
     b->blocks_per_sm = cand[i];
     const int eb = em_blocks(b);
     GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, b->n, b->total_cells, b->lab, b->gp, b->partials,
-                                            b->p.precision, eb, b->stream));  // warm-up
+                                            b->p.precision, eb, b->blocks_per_sm, b->stream));  // warm-up
     GB_CHECK(b, cudaEventRecord(e0, b->stream));
     for (int r = 0; r < reps; ++r)
       GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, b->n, b->total_cells, b->lab, b->gp, b->partials,
-                                              b->p.precision, eb, b->stream));
+                                              b->p.precision, eb, b->blocks_per_sm, b->stream));
     GB_CHECK(b, cudaEventRecord(e1, b->stream));
     GB_CHECK(b, cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -360,9 +377,36 @@ gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void* const* images_dev, 
     if (times_ms) times_ms[i] = per;
     if (per < best_ms) { best_ms = per; best_c = cand[i]; }
   }
+  b->blocks_per_sm = best_c;
+  if (b->p.precision != GMMSP_PREC_FP32) {
+    // finalize: 16 lanes per superpixel against one thread per superpixel
+    // (theta changes here; every segment starts again from theta_0)
+    const int fblocks = int(std::min<long long>((b->total_k + 31) / 32, (long long)b->sm_count * 16));
+    double fin_ms[2] = {0.0, 0.0};
+    for (int variant = 0; variant < 2; ++variant) {
+      const int blocks = variant == 0 ? 0 : fblocks;
+      GB_CHECK(b, gmmsp::launch_finalize_batch(b->table, b->n, b->total_k, b->partials, b->theta, b->gp,
+                                               b->p.eps_s, b->p.eps_c, b->counters, b->p.precision, blocks,
+                                               b->stream));
+      GB_CHECK(b, cudaEventRecord(e0, b->stream));
+      for (int r = 0; r < reps; ++r)
+        GB_CHECK(b, gmmsp::launch_finalize_batch(b->table, b->n, b->total_k, b->partials, b->theta, b->gp,
+                                                 b->p.eps_s, b->p.eps_c, b->counters, b->p.precision, blocks,
+                                                 b->stream));
+      GB_CHECK(b, cudaEventRecord(e1, b->stream));
+      GB_CHECK(b, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      GB_CHECK(b, cudaEventElapsedTime(&ms, e0, e1));
+      fin_ms[variant] = double(ms) / reps;
+    }
+    b->fin16 = fin_ms[0] <= fin_ms[1];
+    b->fin_ms[0] = fin_ms[0];
+    b->fin_ms[1] = fin_ms[1];
+    GB_CHECK(b, cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * gmmsp::CNT_N, b->stream));
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->blocks_per_sm = best_c;
+  drop_graph(b);
   if (best) *best = best_c;
   return GMMSP_OK;
 }

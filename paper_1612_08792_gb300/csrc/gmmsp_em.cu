@@ -354,11 +354,14 @@ __device__ __forceinline__ int find_image(const BatchImage* __restrict__ imgs, i
   return lo;
 }
 
-template <typename PT, bool SHIFT>
-__global__ void __launch_bounds__(kEmWarps * 32) k_em_pass_batch(const BatchImage* __restrict__ imgs, int n,
-                                                                 int total_cells, const float* __restrict__ lab,
-                                                                 const float* __restrict__ gp,
-                                                                 PT* __restrict__ partials) {
+// MINB caps the registers so that MINB blocks fit on an SM: 5 (at most 102
+// registers, no spills) or 6 (80 registers, a few spills); the autotuner's
+// choice of blocks per SM picks the variant.
+template <typename PT, bool SHIFT, int MINB>
+__global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch(const BatchImage* __restrict__ imgs, int n,
+                                                                       int total_cells, const float* __restrict__ lab,
+                                                                       const float* __restrict__ gp,
+                                                                       PT* __restrict__ partials) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EmSmem<1>& sm = *reinterpret_cast<EmSmem<1>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -379,11 +382,21 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
                                                   int32_t* __restrict__ labels, float& ll) {
   const int npx = c.cw * c.ch;
   const float inv_cw = 1.f / float(c.cw);
+  // the colour of this lane's next pixel is loaded one batch ahead
+  float4 zn = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (lane < npx) {
+    const int ry = __float2int_rz((float(lane) + 0.5f) * inv_cw);
+    zn = lab.load(c.x0 + lane - ry * c.cw, c.y0 + ry);
+  }
   for (int p = lane; p < npx; p += 32) {
-    const int ry = __float2int_rz((float(p) + 0.5f) * inv_cw);
+    const int ry = __float2int_rz((float(p) + 0.5f) * inv_cw);  // exact floor(p / cw)
     const int rx = p - ry * c.cw;
     const int x = c.x0 + rx, y = c.y0 + ry;
-    const float4 z = lab.load(x, y);
+    const float4 z = zn;
+    if (p + 32 < npx) {
+      const int ry1 = __float2int_rz((float(p + 32) + 0.5f) * inv_cw);
+      zn = lab.load(c.x0 + p + 32 - ry1 * c.cw, c.y0 + ry1);
+    }
     float fxs[3], fys[3];
     rel_coords(rx, ry, g.v, fxs, fys);
     float e[kSlots];
@@ -658,25 +671,17 @@ __device__ __forceinline__ double rcp64(double x) {
 // x > 0 for a finite double, tested on its bits (integer pipe, not FP64).
 __device__ __forceinline__ bool dpos(double x) { return __double_as_longlong(x) > 0; }
 
-__global__ void __launch_bounds__(kFin16Threads) k_finalize_l16(Geom g, const double* __restrict__ partials,
-                                                              double* __restrict__ theta,
-                                                              float* __restrict__ gp, double eps_s,
-                                                              double eps_c, double* llk_out, double* blk,
-                                                              unsigned* ticket,
-                                                              unsigned long long* counters) {
-  __shared__ double sh[kFin16Threads / 16][48];
-  __shared__ float shf[kFin16Threads / 16][8];
-  pdl_wait();
-  pdl_trigger();
-  if (llk_out)
-    block_ll_sum<double, kFin16Threads>(partials + kSlots * kStats, kPartStride, g.ncells, blk, ticket,
-                                        llk_out);
+// One superpixel per half-warp (lane l = threadIdx.x & 15): superpixel k of
+// the image with geometry g, partials, theta and gp; all 32 lanes of the warp
+// call it together (valid = false for a half-warp without a superpixel).
+// X (48 doubles) and F (8 floats) are the half-warp's shared scratch.
+__device__ __forceinline__ void finalize_l16_body(const Geom& g, const double* __restrict__ partials,
+                                                  double* __restrict__ theta, float* __restrict__ gp,
+                                                  double eps_s, double eps_c, int k, bool valid, double* X,
+                                                  float* F, unsigned long long* counters) {
   constexpr unsigned kFull = 0xffffffffu;
-  const int l = threadIdx.x & 15, q = threadIdx.x >> 4;
-  double* X = sh[q];   // [0..14] sums, [16..20] d, [21..29] M, [30..36] products, [37..45] scratch
-  float* F = shf[q];
-  const int k = blockIdx.x * (kFin16Threads / 16) + q;
-  const bool valid = k < g.K;
+  const int l = threadIdx.x & 15;
+  // X: [0..14] sums, [16..20] d, [21..29] M, [30..36] products, [37..45] scratch
   const int kk = valid ? k : 0;
   const int kx = kk % g.nx, ky = kk / g.nx;
 
@@ -851,6 +856,42 @@ __global__ void __launch_bounds__(kFin16Threads) k_finalize_l16(Geom g, const do
   }
 }
 
+__global__ void __launch_bounds__(kFin16Threads) k_finalize_l16(Geom g, const double* __restrict__ partials,
+                                                              double* __restrict__ theta,
+                                                              float* __restrict__ gp, double eps_s,
+                                                              double eps_c, double* llk_out, double* blk,
+                                                              unsigned* ticket,
+                                                              unsigned long long* counters) {
+  __shared__ double sh[kFin16Threads / 16][48];
+  __shared__ float shf[kFin16Threads / 16][8];
+  pdl_wait();
+  pdl_trigger();
+  if (llk_out)
+    block_ll_sum<double, kFin16Threads>(partials + kSlots * kStats, kPartStride, g.ncells, blk, ticket,
+                                        llk_out);
+  const int q = threadIdx.x >> 4;
+  const int k = blockIdx.x * (kFin16Threads / 16) + q;
+  finalize_l16_body(g, partials, theta, gp, eps_s, eps_c, k, k < g.K, sh[q], shf[q], counters);
+}
+
+// The same over a batch: half-warp q of block b takes superpixel 4 b + q of
+// the batch, found in its image by a binary search over the offsets.
+__global__ void __launch_bounds__(kFin16Threads) k_finalize_l16_batch(const BatchImage* __restrict__ imgs, int n,
+                                                                    int total_k, const double* __restrict__ partials,
+                                                                    double* __restrict__ theta,
+                                                                    float* __restrict__ gp, double eps_s,
+                                                                    double eps_c, unsigned long long* counters) {
+  __shared__ double sh[kFin16Threads / 16][48];
+  __shared__ float shf[kFin16Threads / 16][8];
+  const int q = threadIdx.x >> 4;
+  const int kg = blockIdx.x * (kFin16Threads / 16) + q;
+  const bool valid = kg < total_k;
+  const BatchImage& im = imgs[find_image(imgs, n, valid ? kg : 0, 1)];
+  finalize_l16_body(im.g, partials + (long long)im.cell_off * kPartStride, theta + (long long)im.k_off * kTheta,
+                    gp + (long long)im.k_off * kGP, eps_s, eps_c, valid ? kg - im.k_off : 0, valid, sh[q], shf[q],
+                    counters);
+}
+
 __global__ void __launch_bounds__(kFinThreads) k_ll_reduce(const double* __restrict__ cell_ll, int n,
                                                            double* blk, unsigned* ticket, double* out) {
   pdl_wait();
@@ -953,15 +994,24 @@ cudaError_t launch_ll_reduce(const double* cell_ll, int n, double* out, double* 
 namespace gmmsp {
 
 cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
-                                 const float* gp, void* partials, int precision, int blocks,
+                                 const float* gp, void* partials, int precision, int blocks, int minb,
                                  cudaStream_t s) {
   constexpr int smem = em_smem_bytes<1>();
-  if (precision == 1)
-    k_em_pass_batch<float, false><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                    static_cast<float*>(partials));
-  else
-    k_em_pass_batch<double, true><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                    static_cast<double*>(partials));
+  if (precision == 1) {
+    if (minb >= 6)
+      k_em_pass_batch<float, false, 6><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                         static_cast<float*>(partials));
+    else
+      k_em_pass_batch<float, false, 5><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                         static_cast<float*>(partials));
+  } else {
+    if (minb >= 6)
+      k_em_pass_batch<double, true, 6><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                         static_cast<double*>(partials));
+    else
+      k_em_pass_batch<double, true, 5><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                         static_cast<double*>(partials));
+  }
   return cudaGetLastError();
 }
 
@@ -969,6 +1019,12 @@ cudaError_t launch_finalize_batch(const BatchImage* imgs, int n, int total_k, co
                                   double* theta, float* gp, double eps_s, double eps_c,
                                   unsigned long long* counters, int precision, int blocks,
                                   cudaStream_t s) {
+  if (precision != 1 && blocks == 0) {  // 16 lanes per superpixel
+    const int nb = (total_k + kFin16Threads / 16 - 1) / (kFin16Threads / 16);
+    k_finalize_l16_batch<<<nb, kFin16Threads, 0, s>>>(imgs, n, total_k, static_cast<const double*>(partials), theta,
+                                                     gp, eps_s, eps_c, counters);
+    return cudaGetLastError();
+  }
   if (precision == 1)
     k_finalize_batch<float><<<blocks, kFinThreads, 0, s>>>(imgs, n, total_k, static_cast<const float*>(partials),
                                                            theta, gp, eps_s, eps_c, counters);
@@ -977,6 +1033,15 @@ cudaError_t launch_finalize_batch(const BatchImage* imgs, int n, int total_k, co
                                                             static_cast<const double*>(partials), theta, gp,
                                                             eps_s, eps_c, counters);
   return cudaGetLastError();
+}
+
+int label_pass_batch_occupancy() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_label_pass_batch, kEmWarps * 32, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 4;
+  }
+  return nb;
 }
 
 cudaError_t launch_label_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,

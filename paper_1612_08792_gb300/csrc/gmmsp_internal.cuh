@@ -70,12 +70,13 @@ struct LabPitched {  // a caller's image: rows of (L, a, b) float32, row pitch i
   }
 };
 
-// Programmatic dependent launch.  Kernels of the pipeline are launched with
-// cudaLaunchAttributeProgrammaticStreamSerialization: each one lets its
-// successor start launching at entry (pdl_trigger), and waits for its
-// predecessor's completion and memory (pdl_wait, griddepcontrol.wait, a
-// hardware wait) just before it reads what the predecessor wrote.  Without a
-// programmatic predecessor pdl_wait returns at once.
+// Programmatic dependent launch (off unless GMMSP_PDL=1: measured slower on
+// this pipeline of short dependent kernels).  When on, the single-image
+// kernels are launched with cudaLaunchAttributeProgrammaticStreamSerialization;
+// each waits for its predecessor's completion and memory (pdl_wait,
+// griddepcontrol.wait, a hardware wait) and then lets its successor start
+// launching (pdl_trigger).  Without a programmatic predecessor pdl_wait
+// returns at once.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
@@ -142,19 +143,24 @@ cudaError_t launch_pack_theta(const Geom& g, double* theta, float* gp, int* bad,
 
 // Batches: the same steps over all images of a BatchImage table in one launch
 // each; `blocks` is the persistent grid size.
-cudaError_t launch_prepare_batch(const BatchImage* imgs, int n, long long total_pix, int input_format,
+cudaError_t launch_prepare_batch(const BatchImage* imgs, int n, long long total_rows, int input_format,
                                  float* lab, unsigned long long* counters, int blocks, cudaStream_t s);
 cudaError_t launch_init_batch(const BatchImage* imgs, int n, int total_k, const float* lab,
                               double lambda_c, double* theta, float* gp, int blocks, cudaStream_t s);
+// minb >= 6: the register-capped variant that fits 6 blocks per SM.
 cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
-                                 const float* gp, void* partials, int precision, int blocks,
+                                 const float* gp, void* partials, int precision, int blocks, int minb,
                                  cudaStream_t s);
+// blocks == 0 (mixed precision only): 16 lanes per superpixel, one block per
+// 4 superpixels; otherwise one thread per superpixel on `blocks` blocks.
 cudaError_t launch_finalize_batch(const BatchImage* imgs, int n, int total_k, const void* partials,
                                   double* theta, float* gp, double eps_s, double eps_c,
                                   unsigned long long* counters, int precision, int blocks,
                                   cudaStream_t s);
 cudaError_t launch_label_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
                                     const float* gp, double* cell_ll, int blocks, cudaStream_t s);
+// Resident 128-thread blocks per SM of the batch label pass.
+int label_pass_batch_occupancy();
 // ll_out[i] = sum of image i's per-cell log-likelihoods (fixed order).
 cudaError_t launch_ll_per_image(const BatchImage* imgs, int n, const double* cell_ll, double* ll_out,
                                 cudaStream_t s);
