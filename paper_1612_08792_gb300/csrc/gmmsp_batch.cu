@@ -33,7 +33,7 @@ struct gmmsp_batch_s {
   int sm_count = 152;
   int blocks_per_sm = 4;           // persistent grid of the E + M pass (autotuned)
   int label_blocks_per_sm = 4;     // persistent grid of the label pass (its occupancy)
-  bool fin16 = true;               // finalize with 16 lanes per superpixel (autotuned)
+  bool fin16 = false;              // finalize with 16 lanes per superpixel (autotuned)
   double fin_ms[2] = {0.0, 0.0};   // autotuned finalize times: 16 lanes, one thread per superpixel
   std::vector<BatchImage> host;    // the table as last uploaded
   long long total_pix = 0;

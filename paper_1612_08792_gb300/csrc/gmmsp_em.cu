@@ -376,46 +376,80 @@ __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch(const Bat
 
 // Label pass: argmax posterior per pixel (ties to the smaller k, i.e. the
 // smaller slot) and the per-cell log-likelihood.
+// Each lane takes kLabelPPL pixels per step (p, p + 32, ...), so that every
+// candidate's parameters, read from shared memory once, serve all of them;
+// the colours of the next step are loaded one step ahead.
+constexpr int kLabelPPL = 2;
+
 template <bool FULL, class Src>
 __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
                                                   const Cell& c, const float4* sp, int lane,
                                                   int32_t* __restrict__ labels, float& ll) {
   const int npx = c.cw * c.ch;
   const float inv_cw = 1.f / float(c.cw);
-  // the colour of this lane's next pixel is loaded one batch ahead
-  float4 zn = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (lane < npx) {
-    const int ry = __float2int_rz((float(lane) + 0.5f) * inv_cw);
-    zn = lab.load(c.x0 + lane - ry * c.cw, c.y0 + ry);
-  }
-  for (int p = lane; p < npx; p += 32) {
-    const int ry = __float2int_rz((float(p) + 0.5f) * inv_cw);  // exact floor(p / cw)
-    const int rx = p - ry * c.cw;
-    const int x = c.x0 + rx, y = c.y0 + ry;
-    const float4 z = zn;
-    if (p + 32 < npx) {
-      const int ry1 = __float2int_rz((float(p + 32) + 0.5f) * inv_cw);
-      zn = lab.load(c.x0 + p + 32 - ry1 * c.cw, c.y0 + ry1);
+  auto locate = [&](int p, int& rx, int& ry) {
+    ry = __float2int_rz((float(p) + 0.5f) * inv_cw);  // exact floor(p / cw)
+    rx = p - ry * c.cw;
+  };
+  float4 zn[kLabelPPL];
+#pragma unroll
+  for (int j = 0; j < kLabelPPL; ++j) {
+    zn[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int p = lane + 32 * j;
+    if (p < npx) {
+      int rx, ry;
+      locate(p, rx, ry);
+      zn[j] = lab.load(c.x0 + rx, c.y0 + ry);
     }
-    float fxs[3], fys[3];
-    rel_coords(rx, ry, g.v, fxs, fys);
-    float e[kSlots];
-    float m = -INFINITY;
-    int best = 0;
+  }
+  for (int p0 = lane; p0 - lane < npx; p0 += 32 * kLabelPPL) {
+    float4 z[kLabelPPL];
+    float fxs[kLabelPPL][3], fys[kLabelPPL][3];
+    int rx[kLabelPPL], ry[kLabelPPL];
+#pragma unroll
+    for (int j = 0; j < kLabelPPL; ++j) {
+      z[j] = zn[j];
+      const int pn = p0 + 32 * (j + kLabelPPL);
+      if (pn < npx) {
+        int x1, y1;
+        locate(pn, x1, y1);
+        zn[j] = lab.load(c.x0 + x1, c.y0 + y1);
+      }
+      locate(p0 + 32 * j, rx[j], ry[j]);
+      rel_coords(rx[j], ry[j], g.v, fxs[j], fys[j]);
+    }
+    float e[kLabelPPL][kSlots];
+    float m[kLabelPPL];
+    int best[kLabelPPL];
+#pragma unroll
+    for (int j = 0; j < kLabelPPL; ++j) {
+      m[j] = -INFINITY;
+      best[j] = 0;
+    }
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
-      e[s] = 0.f;
       if (FULL || ((c.mask >> s) & 1u)) {
-        e[s] = log2_density(sp + 4 * s, fxs[s % 3], fys[s / 3], z);
-        if (e[s] > m) { m = e[s]; best = s; }
+#pragma unroll
+        for (int j = 0; j < kLabelPPL; ++j) {
+          e[j][s] = log2_density(sp + 4 * s, fxs[j][s % 3], fys[j][s / 3], z[j]);
+          if (e[j][s] > m[j]) { m[j] = e[j][s]; best[j] = s; }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kLabelPPL; ++j) e[j][s] = 0.f;
       }
     }
-    float sum = 0.f;
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s)
-      if (FULL || ((c.mask >> s) & 1u)) sum += ex2_approx(e[s] - m);
-    ll += m + lg2_approx(sum);
-    labels[(long long)y * g.W + x] = (c.cy - 1 + best / 3) * g.nx + (c.cx - 1 + best % 3);
+    for (int j = 0; j < kLabelPPL; ++j) {
+      if (p0 + 32 * j >= npx) continue;
+      float sum = 0.f;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s)
+        if (FULL || ((c.mask >> s) & 1u)) sum += ex2_approx(e[j][s] - m[j]);
+      ll += m[j] + lg2_approx(sum);
+      labels[(long long)(c.y0 + ry[j]) * g.W + (c.x0 + rx[j])] =
+          (c.cy - 1 + best[j] / 3) * g.nx + (c.cx - 1 + best[j] % 3);
+    }
   }
 }
 
