@@ -448,10 +448,13 @@ LEARN_IMAGES, LEARN_V, LEARN_T, HELD_OUT0 = 256, 15, 2, 1_000_000
 # 32 -> 32) and four 3 x 3 layers per cell (288 -> 32 three times, 288 -> 16).
 NET_FLOPS_PER_PATCH = 2 * (27 * 32 + 32 * 32)
 NET_FLOPS_PER_CELL = 2 * (3 * 288 * 32 + 288 * 16)
-# DRAM bytes per 481 x 321 image of one batched E + M pass, from the ncu capture of
-# k_em_pass_batch on 96 such images (dram__bytes_read.sum + dram__bytes_write.sum =
-# 182.04 MB + 52.66 MB), scaled per image (traffic grows with the image count).
-EM_BATCH_TRAFFIC_PER_IMAGE = int((182.039296e6 + 52.660480e6) / 96)
+# DRAM bytes per 481 x 321 image of one batched E + M pass, from the ncu captures on
+# 96 such images (dram__bytes_read.sum + dram__bytes_write.sum), scaled per image
+# (traffic grows with the image count), per launch variant (blocks per SM):
+#   5: persistent k_em_pass_batch, 182.04 MB + 52.66 MB;
+#   7: one-cell-per-warp k_em_pass_batch_flat, 182.05 MB + 56.58 MB (spills included).
+EM_BATCH_TRAFFIC_PER_IMAGE = {5: int((182.039296e6 + 52.660480e6) / 96),
+                              7: int((182.051328e6 + 56.577536e6) / 96)}
 
 
 def measured_peaks():
@@ -636,7 +639,7 @@ def run_learned(args):
         "roofline": {"kernel": "k_em_pass_batch (fused E-step + M-step partials)", "bound": "alu",
                      "achieved": round(achieved_i, 3), "peak": round(FP32_PEAK_TINST, 3),
                      "unit": "T FP32-lane-instr/s", "frac": round(achieved_i / FP32_PEAK_TINST, 4),
-                     "traffic": EM_BATCH_TRAFFIC_PER_IMAGE * n if bps < 6 else None,
+                     "traffic": EM_BATCH_TRAFFIC_PER_IMAGE[bps] * n if bps in EM_BATCH_TRAFFIC_PER_IMAGE else None,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (one FP32 instruction per "
                                     "lane per clock)",
                      "em_pass_ms": round(em_ms, 5), "instr_per_launch": instr,

@@ -230,10 +230,14 @@ gmmsp_status gmmsp_autotune(gmmsp_ctx c, int reps, int *best, double *times_ms);
  *   between calls without a new capture.
  * gmmsp_batch_get_params: theta of image i (layout of gmmsp_get_params);
  *   synchronises.
- * gmmsp_batch_autotune: times the batch E + M-partial pass for persistent
- *   grids of 2..6 blocks per SM (`reps` launches each, on the given images),
- *   keeps the fastest; times_ms NULL or 5 doubles.  Synchronises.
- * gmmsp_batch_set_launch: blocks per SM of the persistent grid (1..16).
+ * gmmsp_batch_autotune: times the batch E + M-partial pass at 3, 4, 5, 6 and
+ *   7 blocks per SM (`reps` launches each, on the given images; 3-5: a
+ *   persistent grid of that many blocks per SM; 6, 7: one cell per warp with
+ *   the registers capped for that occupancy), keeps the fastest, then times
+ *   the two finalize kernels and keeps the faster; times_ms NULL or 5
+ *   doubles (E + M pass, in candidate order).  Synchronises.
+ * gmmsp_batch_set_launch: blocks per SM of the E + M pass (1..16; >= 6
+ *   selects the one-cell-per-warp kernel).
  * gmmsp_batch_info: totals over the batch (any pointer may be NULL).
  */
 typedef struct gmmsp_batch_s *gmmsp_batch;

@@ -356,7 +356,7 @@ def gmmsp_batch_autotune(b, images, pitches, labels, reps=3):
     _bcheck(b, _batch_lib().gmmsp_batch_autotune(b, _ptr_array(images), pit.ctypes.data_as(ctypes.c_void_p),
                                                  _ptr_array(labels), int(reps), ctypes.byref(best),
                                                  times.ctypes.data_as(ctypes.c_void_p)))
-    return best.value, dict(zip((2, 3, 4, 5, 6), times.tolist()))
+    return best.value, dict(zip((3, 4, 5, 6, 7), times.tolist()))
 
 
 def gmmsp_batch_set_launch(b, blocks_per_sm: int) -> None:

@@ -354,7 +354,7 @@ gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void* const* images_dev, 
   const int kblocks = int(std::min<long long>((b->total_k + 127) / 128, (long long)b->sm_count * 8));
   GB_CHECK(b, gmmsp::launch_init_batch(b->table, b->n, b->total_k, b->lab, b->p.lambda_c, b->theta, b->gp,
                                        kblocks, b->stream));
-  const int cand[5] = {2, 3, 4, 5, 6};
+  const int cand[5] = {3, 4, 5, 6, 7};
   cudaEvent_t e0, e1;
   GB_CHECK(b, cudaEventCreate(&e0));
   GB_CHECK(b, cudaEventCreate(&e1));

@@ -354,9 +354,8 @@ __device__ __forceinline__ int find_image(const BatchImage* __restrict__ imgs, i
   return lo;
 }
 
-// MINB caps the registers so that MINB blocks fit on an SM: 5 (at most 102
-// registers, no spills) or 6 (80 registers, a few spills); the autotuner's
-// choice of blocks per SM picks the variant.
+// MINB caps the registers so that MINB blocks fit on an SM (5: at most 102
+// registers, no spills).
 template <typename PT, bool SHIFT, int MINB>
 __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch(const BatchImage* __restrict__ imgs, int n,
                                                                        int total_cells, const float* __restrict__ lab,
@@ -372,6 +371,28 @@ __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch(const Bat
                                            partials + (long long)im.cell_off * kPartStride,
                                            cell - im.cell_off, true, sm, warp, lane, warp, 0, lane);
   }
+}
+
+// Non-persistent variant: one cell per warp over a grid sized to the work,
+// registers capped so that MINB blocks fit on an SM (6: 80 registers and 8
+// bytes of spill; 7: 72 registers and some spill); the autotuner's choice of
+// 6 or 7 blocks per SM selects it.
+template <typename PT, bool SHIFT, int MINB>
+__global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch_flat(const BatchImage* __restrict__ imgs, int n,
+                                                                      int total_cells,
+                                                                      const float* __restrict__ lab,
+                                                                      const float* __restrict__ gp,
+                                                                      PT* __restrict__ partials) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EmSmem<1>& sm = *reinterpret_cast<EmSmem<1>*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * kEmWarps + warp;
+  if (cell >= total_cells) return;  // whole warps only; a warp works alone on its cell
+  const BatchImage& im = imgs[find_image(imgs, n, cell, 0)];
+  const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
+  em_cell_block<PT, SHIFT, 1, LabPlanar>(src, im.g, gp + (long long)im.k_off * kGP,
+                                         partials + (long long)im.cell_off * kPartStride, cell - im.cell_off, true,
+                                         sm, warp, lane, warp, 0, lane);
 }
 
 // Label pass: argmax posterior per pixel (ties to the smaller k, i.e. the
@@ -1031,21 +1052,25 @@ cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells,
                                  const float* gp, void* partials, int precision, int blocks, int minb,
                                  cudaStream_t s) {
   constexpr int smem = em_smem_bytes<1>();
-  if (precision == 1) {
-    if (minb >= 6)
-      k_em_pass_batch<float, false, 6><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                         static_cast<float*>(partials));
+  if (minb >= 6) {  // one cell per warp over a grid sized to the work
+    const int nb = (total_cells + kEmWarps - 1) / kEmWarps;
+    if (precision == 1)
+      k_em_pass_batch_flat<float, false, 6><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                          static_cast<float*>(partials));
+    else if (minb >= 7)
+      k_em_pass_batch_flat<double, true, 7><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                          static_cast<double*>(partials));
     else
-      k_em_pass_batch<float, false, 5><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                         static_cast<float*>(partials));
-  } else {
-    if (minb >= 6)
-      k_em_pass_batch<double, true, 6><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                         static_cast<double*>(partials));
-    else
-      k_em_pass_batch<double, true, 5><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                         static_cast<double*>(partials));
+      k_em_pass_batch_flat<double, true, 6><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                          static_cast<double*>(partials));
+    return cudaGetLastError();
   }
+  if (precision == 1)
+    k_em_pass_batch<float, false, 5><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                       static_cast<float*>(partials));
+  else
+    k_em_pass_batch<double, true, 5><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                       static_cast<double*>(partials));
   return cudaGetLastError();
 }
 

@@ -147,7 +147,9 @@ cudaError_t launch_prepare_batch(const BatchImage* imgs, int n, long long total_
                                  float* lab, unsigned long long* counters, int blocks, cudaStream_t s);
 cudaError_t launch_init_batch(const BatchImage* imgs, int n, int total_k, const float* lab,
                               double lambda_c, double* theta, float* gp, int blocks, cudaStream_t s);
-// minb >= 6: the register-capped variant that fits 6 blocks per SM.
+// minb >= 6: the non-persistent variant (one cell per warp, registers capped
+// for 6 blocks per SM; `blocks` is then ignored); otherwise the persistent
+// kernel on `blocks` blocks.
 cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
                                  const float* gp, void* partials, int precision, int blocks, int minb,
                                  cudaStream_t s);

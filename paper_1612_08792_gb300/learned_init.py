@@ -176,28 +176,43 @@ def train(steps: int = 2000, batch: int = 32, lr: float = 3e-3, lr_final: float 
 
 def evaluate(net: InitNet, n_images: int = 64, seed0: int = HELD_OUT_SEED0, plain_iters=(2, 3, 10),
              learned_iters=(2,), batch: int = 64):
-    """Mean per-pixel log-likelihood L(theta_T) / (W H) on held-out images for the
-    paper's start (plain) and the network's start (learned)."""
+    """Held-out images: mean per-pixel log-likelihood L(theta_T) / (W H) for the
+    paper's start (plain) and the network's start (learned), and the fraction of
+    pixels whose label after each learned run equals the label after the longest
+    plain run."""
     import torch
     W, H, v = TRAIN["W"], TRAIN["H"], TRAIN["spacing"]
     res = {f"plain{t}": [] for t in plain_iters}
     res.update({f"learned{t}": [] for t in learned_iters})
-    buf = torch.empty((min(batch, n_images), H, W, 3), dtype=torch.uint8, device="cuda")
-    bt = SuperpixelsBatch([(H, W)] * buf.shape[0], spacing=v)
-    for s0 in range(0, n_images, buf.shape[0]):
-        seeds = [seed0 + s0 + i for i in range(buf.shape[0])]
+    agree = {f"learned{t}": 0 for t in learned_iters}
+    ref_t = max(plain_iters)
+    nb = min(batch, n_images)
+    buf = torch.empty((nb, H, W, 3), dtype=torch.uint8, device="cuda")
+    bt = SuperpixelsBatch([(H, W)] * nb, spacing=v)
+    done = 0
+    for s0 in range(0, n_images, nb):
+        seeds = [seed0 + s0 + i for i in range(nb)]
         imgs = _images(seeds, buf)
+        take = min(nb, n_images - s0)
         bt.set_init_net(None)
+        ref_labels = None
         for t in plain_iters:
-            _, ll = bt.segment(imgs, iters=t, want_loglik=True)
-            res[f"plain{t}"] += list(ll / (W * H))
+            labels, ll = bt.segment(imgs, iters=t, want_loglik=True)
+            res[f"plain{t}"] += list(ll[:take] / (W * H))
+            if t == ref_t:
+                ref_labels = [x.clone() for x in labels[:take]]
         bt.set_init_net(net)
         for t in learned_iters:
-            _, ll = bt.segment(imgs, iters=t, want_loglik=True)
-            res[f"learned{t}"] += list(ll / (W * H))
+            labels, ll = bt.segment(imgs, iters=t, want_loglik=True)
+            res[f"learned{t}"] += list(ll[:take] / (W * H))
+            agree[f"learned{t}"] += sum(int((a == b).sum().item()) for a, b in zip(labels[:take], ref_labels))
         bt.set_init_net(None)
+        done += take
     bt.close()
-    return {k: float(np.mean(v[:n_images])) for k, v in res.items()}
+    out = {k: float(np.mean(v_)) for k, v_ in res.items()}
+    out.update({f"label_agreement_{k}_vs_plain{ref_t}": a / (done * W * H) for k, a in agree.items()})
+    out["images"] = done
+    return out
 
 
 def main(argv=None):

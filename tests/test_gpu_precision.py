@@ -1,0 +1,90 @@
+"""Precision study on the 481x321 workload (K = 1000 requested -> v = 12, K = 1040,
+10 iterations): every output of the mixed-precision path (FP32 E-step, FP64
+statistics from the per-cell partial on, FP64 floor and inversion) and of the
+all-FP32 variant against the FP64 oracle on the same FP32 CIELAB input.
+
+The mixed path must meet the parity bar; the FP32 variant's errors are recorded
+(bounded loosely here).  With GMMSP_PRECISION_OUT set, the per-output errors are
+written there as JSON.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import voronoi_image
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    torch.cuda.set_device(0)
+    return gm
+
+
+def errors(run, ref, N):
+    """Per-output errors of one GPU run against the oracle."""
+    mu_abs = np.abs(run["mu"] - ref.theta.mu)
+    mu_rel = mu_abs / np.maximum(np.abs(ref.theta.mu), 1.0)
+    A_s, B_s = parity.unpack(run["cs"]), parity.unpack(ref.theta.cs)
+    A_c, B_c = parity.unpack(run["cc"]), parity.unpack(ref.theta.cc)
+    es = np.sqrt(((A_s - B_s) ** 2).sum((-1, -2))) / np.sqrt((B_s ** 2).sum((-1, -2)))
+    ec = np.sqrt(((A_c - B_c) ** 2).sum((-1, -2))) / np.sqrt((B_c ** 2).sum((-1, -2)))
+    agree, ndiff, worst = parity.label_report(run["labels"], ref.labels, ref.margin)
+    ll_rel = np.abs(run["ll"] - ref.loglik) / np.abs(ref.loglik)
+    return {
+        "mean_spatial_rel": {"max": float(mu_rel[:, :2].max()), "median": float(np.median(mu_rel[:, :2]))},
+        "mean_colour_rel": {"max": float(mu_rel[:, 2:].max()), "median": float(np.median(mu_rel[:, 2:]))},
+        "cov_spatial_rel_frobenius": {"max": float(es.max()), "median": float(np.median(es))},
+        "cov_colour_rel_frobenius": {"max": float(ec.max()), "median": float(np.median(ec))},
+        "labels": {"agreement": float(agree), "disagreements": ndiff, "max_oracle_margin_at_disagreement": worst},
+        "loglik_rel_per_estep": {"max": float(ll_rel.max()), "last": float(ll_rel[-1])},
+        "loglik_per_pixel": {"gpu": float(run["ll"][-1] / N), "oracle": float(ref.loglik[-1] / N)},
+    }
+
+
+def run_gpu(gm, lab32, precision):
+    import torch
+    sp = gm.Superpixels(torch.from_numpy(lab32).cuda(), K=1000, precision=precision)
+    ll = list(sp.em_iters(10, want_loglik=True))
+    labels, ll_last = sp.labels(want_loglik=True)
+    mu, cs, cc = sp.get_params()
+    sp.close()
+    return dict(labels=labels.cpu().numpy(), ll=np.array(ll + [ll_last]), mu=mu, cs=cs, cc=cc)
+
+
+def test_precision_study_481x321(gm):
+    W, H = 481, 321
+    report = {"workload": "481x321 synthetic Voronoi (150 regions, sigma 8, seeds 0-2), K=1000 -> v=12, "
+                          "K=1040, 10 EM iterations; both sides fed the same FP32 CIELAB",
+              "seeds": {}}
+    for seed in (0, 1, 2):
+        img = voronoi_image(W, H, 150, 8.0, seed)
+        lab32 = oracle.rgb2lab(img).astype(np.float32)
+        ref = oracle.em(lab32.astype(np.float64), W, H, K=1000, T=10)
+        mixed = errors(run_gpu(gm, lab32, gm.GMMSP_PREC_MIXED), ref, W * H)
+        fp32 = errors(run_gpu(gm, lab32, gm.GMMSP_PREC_FP32), ref, W * H)
+        report["seeds"][str(seed)] = {"mixed": mixed, "fp32": fp32}
+        # the mixed path meets the parity bar on every output
+        assert mixed["mean_spatial_rel"]["max"] <= parity.MEAN_TOL
+        assert mixed["mean_colour_rel"]["max"] <= parity.MEAN_TOL
+        assert mixed["cov_spatial_rel_frobenius"]["max"] <= parity.COV_TOL
+        assert mixed["cov_colour_rel_frobenius"]["max"] <= parity.COV_TOL
+        assert mixed["labels"]["agreement"] >= parity.LABEL_AGREE
+        assert mixed["labels"]["max_oracle_margin_at_disagreement"] < parity.MARGIN_TOL
+        assert mixed["loglik_rel_per_estep"]["max"] <= parity.LL_RTOL
+        # the FP32 variant (raw moments) is recorded; loose sanity bounds only
+        assert fp32["labels"]["agreement"] > 0.95
+        assert fp32["cov_colour_rel_frobenius"]["median"] < 0.05
+    out = os.environ.get("GMMSP_PRECISION_OUT")
+    if out:
+        with open(out, "w") as fh:
+            json.dump(report, fh, indent=1)
