@@ -147,6 +147,28 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest x over the ranks of the default process group (x itself when alone)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seeds(rank: int, n: int):
+    """Held-out image seeds of one replica: each rank its own n images."""
+    return range(HELD_OUT0 + rank * n, HELD_OUT0 + (rank + 1) * n)
+
+
+def whole_job_value(world: int, units_per_rank: float, max_seconds: float) -> float:
+    """Whole-job throughput in millions of units per second: all ranks' units over the
+    slowest rank's time (the ranks do equal, independent work)."""
+    return world * units_per_rank / max_seconds / 1e6
+
+
 def cpu_oracle_run(seconds: float, seed: int = 0):
     """The FP64 CPU oracle as it stands (RGB -> CIELAB -> EM -> labels), on all host
     threads, repeated for about `seconds`.  Returns (Mpixel/s, threads, reps)."""
@@ -518,7 +540,7 @@ def run_learned(args):
 
     n = args.images
     N = W * H
-    seeds = range(HELD_OUT0 + rank * n, HELD_OUT0 + (rank + 1) * n)
+    seeds = replica_seeds(rank, n)
     buf = voronoi_batch(W, H, REGIONS, SIGMA, seeds)
     imgs = [buf[i] for i in range(n)]
     stream = torch.cuda.Stream()
@@ -547,23 +569,15 @@ def run_learned(args):
             import torch.distributed as dist
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     barrier()
     ms_l, clocks = _timed_steps(step_l, stream, args.steps, flush, local)
     barrier()
     ms_p, clocks_p = _timed_steps(step_p, stream, max(3, args.steps // 3), flush, local)
     barrier()
-    t_l = max_over_ranks(sum(ms_l) / len(ms_l))
-    t_p = max_over_ranks(sum(ms_p) / len(ms_p))
-    value = world * n * N / (t_l * 1e-3) / 1e6
-    plain_value = world * n * N / (t_p * 1e-3) / 1e6
+    t_l = max_over_ranks(sum(ms_l) / len(ms_l), world)
+    t_p = max_over_ranks(sum(ms_p) / len(ms_p), world)
+    value = whole_job_value(world, n * N, t_l * 1e-3)
+    plain_value = whole_job_value(world, n * N, t_p * 1e-3)
 
     # log-likelihood (equal-log-lik check) and label agreement with plain EM
     with torch.cuda.stream(stream):
@@ -619,8 +633,8 @@ def run_learned(args):
     e2e_steps = max(3, args.steps // 4)
     for _ in range(e2e_steps):
         e2e_step()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = world * n * N * e2e_steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = whole_job_value(world, n * N * e2e_steps, e2e_s)
 
     peaks = measured_peaks()
     bf16_peak = peaks.get("bf16_tflops", 1900.0)

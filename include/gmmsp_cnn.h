@@ -102,6 +102,14 @@ gmmsp_status gmmsp_net_get_activation(gmmsp_net n, int layer, float *host, long 
  * the network was created. */
 gmmsp_status gmmsp_net_check(gmmsp_net n);
 
+/* Self-test of the bounded device-side waits used by the network kernels:
+ * one block allocates tensor memory, waits on an mbarrier that nothing
+ * arrives on for max_tries polls (1 .. 2^20), frees the tensor memory and
+ * reports.  Returns GMMSP_E_TIMEOUT when the wait gave up, which is the
+ * expected outcome.  The context stays usable.  Synchronises the stream
+ * (cudaStream_t, NULL = legacy default). */
+gmmsp_status gmmsp_tc_wait_selftest(int max_tries, void *stream);
+
 const char *gmmsp_net_last_error(gmmsp_net n);
 void gmmsp_net_destroy(gmmsp_net n);
 

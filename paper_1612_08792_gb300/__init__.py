@@ -28,10 +28,17 @@ __all__ = [
     "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "SuperpixelsBatch",
     "gmmsp_batch_create", "gmmsp_batch_segment", "gmmsp_batch_get_params", "gmmsp_batch_autotune",
     "gmmsp_batch_set_launch", "gmmsp_batch_info", "gmmsp_batch_destroy", "gmmsp_status_string", "gmmsp_destroy",
+    "gmmsp_batch_get_tuning", "gmmsp_batch_set_init_net", "gmmsp_batch_lab", "gmmsp_batch_targets",
+    "gmmsp_net_param_count", "gmmsp_net_create", "gmmsp_net_set_weights", "gmmsp_net_get_weights",
+    "gmmsp_net_forward", "gmmsp_net_grad", "gmmsp_net_adam", "gmmsp_net_train_step", "gmmsp_net_get_activation",
+    "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
+    "GMMSP_OK", "GMMSP_E_INVALID", "GMMSP_E_CUDA", "GMMSP_E_NOMEM", "GMMSP_E_NUMERIC", "GMMSP_E_TIMEOUT",
+    "GMMSP_E_STATE",
 ]
 
 GMMSP_RGB8, GMMSP_LAB32 = 0, 1
 GMMSP_PREC_MIXED, GMMSP_PREC_FP32 = 0, 1
+GMMSP_OK, GMMSP_E_INVALID, GMMSP_E_CUDA, GMMSP_E_NOMEM, GMMSP_E_NUMERIC, GMMSP_E_TIMEOUT, GMMSP_E_STATE = range(7)
 STATUS = {0: "GMMSP_OK", 1: "GMMSP_E_INVALID", 2: "GMMSP_E_CUDA", 3: "GMMSP_E_NOMEM",
           4: "GMMSP_E_NUMERIC", 5: "GMMSP_E_TIMEOUT", 6: "GMMSP_E_STATE"}
 
@@ -400,6 +407,7 @@ def _net_lib():
             "gmmsp_net_train_step": (I, [P, P, I, I, I, P, F, PD]),
             "gmmsp_net_check": (I, [P]),
             "gmmsp_net_get_activation": (I, [P, I, P, LL]),
+            "gmmsp_tc_wait_selftest": (I, [I, P]),
             "gmmsp_net_last_error": (ctypes.c_char_p, [P]),
             "gmmsp_net_destroy": (None, [P]),
             "gmmsp_init_from_net": (I, [P, P]),
@@ -471,6 +479,11 @@ def gmmsp_net_get_activation(n, layer: int, cells: int):
     a = np.zeros((cells, 32), dtype=np.float32)
     _ncheck(n, _net_lib().gmmsp_net_get_activation(n, int(layer), a.ctypes.data_as(ctypes.c_void_p), a.size))
     return a
+
+
+def gmmsp_tc_wait_selftest(max_tries: int = 1024, stream=None) -> int:
+    """Status of the bounded-wait self-test (GMMSP_E_TIMEOUT = 5 is the expected outcome)."""
+    return int(_net_lib().gmmsp_tc_wait_selftest(int(max_tries), _stream_handle(stream)))
 
 
 def gmmsp_net_check(n) -> None:

@@ -646,6 +646,32 @@ __global__ void k_init_from_net(const float* __restrict__ net, const float* __re
   }
 }
 
+// Self-test of the bounded waits: allocates TMEM like the network kernels,
+// waits on an mbarrier that nothing arrives on for max_tries polls, waits
+// once more (bounded), frees the TMEM and records that it gave up.
+__global__ void __launch_bounds__(128) k_wait_selftest(uint32_t max_tries, int* gave_up) {
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_sh;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_sh, 32);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_sh;
+  const bool ok = __syncthreads_and(tc::mbar_wait(&mbar, 0, max_tries)) != 0;
+  if (!ok) {
+    tc::mbar_wait(&mbar, 0, max_tries);
+    if (tid == 0) atomicExch(gave_up, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 32);
+}
+
 int grid_for(long long n, int block) {
   long long b = (n + block - 1) / block;
   b = std::min<long long>(b, 152LL * 16);
@@ -1101,6 +1127,27 @@ gmmsp_status gmmsp_net_get_activation(gmmsp_net n, int layer, float* host, long 
 gmmsp_status gmmsp_net_check(gmmsp_net n) {
   if (!n) return GMMSP_E_INVALID;
   return check_err(n);
+}
+
+gmmsp_status gmmsp_tc_wait_selftest(int max_tries, void* stream) {
+  if (max_tries < 1 || max_tries > (1 << 20)) return GMMSP_E_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return GMMSP_E_NOMEM;
+  }
+  int host = 0;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 128, 0, s>>>(uint32_t(max_tries), flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(flag);
+  if (e != cudaSuccess) return GMMSP_E_CUDA;
+  return host ? GMMSP_E_TIMEOUT : GMMSP_OK;
 }
 
 const char* gmmsp_net_last_error(gmmsp_net n) { return n ? n->msg.c_str() : "null network"; }

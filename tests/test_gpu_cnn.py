@@ -223,3 +223,22 @@ def test_pretrained_start_gain(gm):
     assert ev["learned2"] > ev["plain2"], ev
     assert abs(ev["learned2"] - ev["plain10"]) / abs(ev["plain10"]) <= 0.005, ev
     net.close()
+
+
+def test_bounded_wait_gives_up_and_context_survives(gm):
+    """A tensor-core wait on an mbarrier that nothing arrives on runs out after
+    its bound, frees its tensor memory and reports GMMSP_E_TIMEOUT; the context
+    then runs the network as before."""
+    import torch
+    from paper_1612_08792_gb300.learned_init import InitNet, init_weights
+    assert gm.gmmsp_tc_wait_selftest(256) == gm.GMMSP_E_TIMEOUT
+    assert gm.gmmsp_tc_wait_selftest(4096) == gm.GMMSP_E_TIMEOUT
+    W, H, v = 64, 50, 9
+    lab = lab_planes([60], W, H)
+    w = init_weights(18)
+    net = InitNet(v, weights=w)
+    out = net.forward(torch.from_numpy(lab).cuda().data_ptr(), 1, W, H).cpu().numpy()
+    net.check()
+    ref, _ = ocnn.forward(w, lab, v, emulate_bf16=True)
+    assert rel_l2(out, ref) < 2e-3
+    net.close()
