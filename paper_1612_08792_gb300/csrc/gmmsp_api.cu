@@ -209,7 +209,8 @@ gmmsp_status enqueue_em(gmmsp_ctx c, int iters, int t0, bool want_ll) {
 }
 
 gmmsp_status enqueue_labels(gmmsp_ctx c, int32_t* labels, double* llk_out) {
-  GM_CHECK(c, gmmsp::launch_label_pass(gmmsp::LabPlanar{c->lab, (long long)c->g.W * c->g.H, c->g.W}, c->g, c->gp, labels, c->cell_ll, c->stream));
+  GM_CHECK(c, gmmsp::launch_label_pass(gmmsp::LabPlanar{c->lab, (long long)c->g.W * c->g.H, c->g.W}, c->g, c->gp,
+                                       labels, llk_out ? c->cell_ll : nullptr, c->stream));
   if (llk_out)
     GM_CHECK(c, gmmsp::launch_ll_reduce(c->cell_ll, c->g.ncells, llk_out, c->ws, c->ticket, c->g,
                                         c->stream));

@@ -137,7 +137,8 @@ gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
   }
   const long long lneed = (b->total_cells + 3) / 4;
   const int lb = int(std::min<long long>(lneed, (long long)b->sm_count * b->label_blocks_per_sm));
-  GB_CHECK(b, gmmsp::launch_label_pass_batch(b->table, n, b->total_cells, b->lab, b->gp, b->cell_ll, lb, s));
+  GB_CHECK(b, gmmsp::launch_label_pass_batch(b->table, n, b->total_cells, b->lab, b->gp,
+                                              want_ll ? b->cell_ll : nullptr, lb, s));
   if (want_ll) GB_CHECK(b, gmmsp::launch_ll_per_image(b->table, n, b->cell_ll, b->img_ll, s));
   return GMMSP_OK;
 }

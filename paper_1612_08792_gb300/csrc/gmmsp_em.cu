@@ -232,9 +232,8 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
     XYw[lane] = make_float2(float(rx), float(ry));
     __syncwarp();
     if (m_on) {
-      const int np = min(32, npx - base);
-#pragma unroll 4
-      for (int q = ph; q < np; q += 3) {
+      // statistics of pixel q for this lane's slot
+      auto accumulate = [&](int q) {
         const float r = Rw[q * kRStride + ms];
         const float2 xy = XYw[q];
         const float4 zz = Zw[q];
@@ -252,6 +251,16 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
         acc[12] = fmaf(ra, da, acc[12]);
         acc[13] = fmaf(ra, db, acc[13]);
         acc[14] = fmaf(rb, db, acc[14]);
+      };
+      const int np = min(32, npx - base);
+      if (np == 32) {
+        // a full batch: pixels ph, ph + 3, ..., fixed offsets, no loop control
+#pragma unroll
+        for (int i = 0; i < 10; ++i) accumulate(ph + 3 * i);
+        if (ph < 2) accumulate(ph + 30);
+      } else {
+#pragma unroll 4
+        for (int q = ph; q < np; q += 3) accumulate(q);
       }
     }
     __syncwarp();
@@ -402,7 +411,9 @@ __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch_flat(cons
 // the colours of the next step are loaded one step ahead.
 constexpr int kLabelPPL = 2;
 
-template <bool FULL, class Src>
+// LL = false: argmax only (no log-sum-exp), for callers that want no
+// log-likelihood.
+template <bool FULL, bool LL, class Src>
 __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
                                                   const Cell& c, const float4* sp, int lane,
                                                   int32_t* __restrict__ labels, float& ll) {
@@ -463,11 +474,13 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
 #pragma unroll
     for (int j = 0; j < kLabelPPL; ++j) {
       if (p0 + 32 * j >= npx) continue;
-      float sum = 0.f;
+      if (LL) {
+        float sum = 0.f;
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s)
-        if (FULL || ((c.mask >> s) & 1u)) sum += ex2_approx(e[j][s] - m[j]);
-      ll += m[j] + lg2_approx(sum);
+        for (int s = 0; s < kSlots; ++s)
+          if (FULL || ((c.mask >> s) & 1u)) sum += ex2_approx(e[j][s] - m[j]);
+        ll += m[j] + lg2_approx(sum);
+      }
       labels[(long long)(c.y0 + ry[j]) * g.W + (c.x0 + rx[j])] =
           (c.cy - 1 + best[j] / 3) * g.nx + (c.cx - 1 + best[j] % 3);
     }
@@ -482,10 +495,17 @@ __device__ __forceinline__ void label_cell_warp(const Src& lab, const Geom& g, c
   const Cell c = make_cell(g, cell);
   stage_params(g, c, gp, sp, lane);
   float ll = 0.f;
+  if (!cell_ll) {  // labels only
+    if (c.mask == 0x1ffu)
+      label_cell_pixels<true, false, Src>(lab, g, c, sp, lane, labels, ll);
+    else
+      label_cell_pixels<false, false, Src>(lab, g, c, sp, lane, labels, ll);
+    return;
+  }
   if (c.mask == 0x1ffu)
-    label_cell_pixels<true, Src>(lab, g, c, sp, lane, labels, ll);
+    label_cell_pixels<true, true, Src>(lab, g, c, sp, lane, labels, ll);
   else
-    label_cell_pixels<false, Src>(lab, g, c, sp, lane, labels, ll);
+    label_cell_pixels<false, true, Src>(lab, g, c, sp, lane, labels, ll);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
   if (lane == 0) cell_ll[cell] = double(ll) * 0.69314718055994530942;
@@ -515,7 +535,7 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass_batch(const BatchI
     const BatchImage& im = imgs[find_image(imgs, n, cell, 0)];
     const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
     label_cell_warp<LabPlanar>(src, im.g, gp + (long long)im.k_off * kGP, im.labels,
-                               cell_ll + im.cell_off, cell - im.cell_off, sp_all[warp], lane);
+                               cell_ll ? cell_ll + im.cell_off : nullptr, cell - im.cell_off, sp_all[warp], lane);
     __syncwarp();
   }
 }

@@ -126,6 +126,7 @@ cudaError_t launch_init_theta(Src lab, const Geom& g, double lambda_c, double* t
 template <class Src>
 cudaError_t launch_em_pass(Src lab, const Geom& g, const float* gp, void* partials, int precision,
                            int wpc, cudaStream_t s);
+// cell_ll == nullptr: labels only, no log-likelihood.
 template <class Src>
 cudaError_t launch_label_pass(Src lab, const Geom& g, const float* gp, int32_t* labels,
                               double* cell_ll, cudaStream_t s);

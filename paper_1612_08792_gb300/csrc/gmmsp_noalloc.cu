@@ -146,7 +146,6 @@ extern "C" gmmsp_status gmmsp_segment_lab_noalloc(const float* lab_dev, int widt
   double* theta = reinterpret_cast<double*>(b + kOffTheta);
   float* gp = reinterpret_cast<float*>(b + kOffGp);
   double* partials = reinterpret_cast<double*>(b + kOffPart);
-  double* cell_ll = reinterpret_cast<double*>(b + kOffCellLl);
   double* ws = reinterpret_cast<double*>(b + kOffWs);
   unsigned* ticket = reinterpret_cast<unsigned*>(b + kOffTicket);
   unsigned long long* counters = reinterpret_cast<unsigned long long*>(b + kOffCounters);
@@ -163,7 +162,7 @@ extern "C" gmmsp_status gmmsp_segment_lab_noalloc(const float* lab_dev, int widt
       e = gmmsp::launch_finalize(g, partials, theta, gp, p->eps_s, p->eps_c, nullptr, ws, ticket, counters,
                                  GMMSP_PREC_MIXED, s);
   }
-  if (e == cudaSuccess) e = gmmsp::launch_label_pass(src, g, gp, labels_dev, cell_ll, s);
+  if (e == cudaSuccess) e = gmmsp::launch_label_pass(src, g, gp, labels_dev, nullptr, s);
   if (e != cudaSuccess) {
     set_err(err, err_len, cudaGetErrorString(e));
     return GMMSP_E_CUDA;
