@@ -363,15 +363,25 @@ struct PixArgs {
 // Row r of block b is patch q = r mod f^2 of cell b cpb + r / f^2; the patch
 // covers the pixels (k_x v + 3 (q mod f) + dx, k_y v + 3 (q / f) + dy),
 // dx, dy in {0, 1, 2}; input channel (3 dy + dx) 3 + colour.
-__global__ void __launch_bounds__(128) k_pix(PixArgs a) {
-  __shared__ __align__(1024) unsigned char sA[128 * kC * 2];
-  __shared__ __align__(1024) unsigned char sW[2][kC * kC * 2];
-  __shared__ float sH[128][kC + 1];
+//
+// Shared memory: the A tile (8 KB) and both weight tiles (4 KB) while the
+// MMAs run; the pooling buffer (128 x 33 floats) reuses the same bytes once
+// the second MMA has completed.  Both layers accumulate into the same 32 TMEM
+// columns (the second MMA is issued after every thread has read the first
+// result).
+constexpr int kPixMinBlocks = 8;
+constexpr int kPixSmem = 128 * (kC + 1) * 4;  // >= 8192 + 4096
+
+__global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
+  __shared__ __align__(1024) unsigned char smem[kPixSmem];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_sh;
+  unsigned char* sA = smem;
+  unsigned char (*sW)[kC * kC * 2] = reinterpret_cast<unsigned char (*)[kC * kC * 2]>(smem + 128 * kC * 2);
+  float (*sH)[kC + 1] = reinterpret_cast<float (*)[kC + 1]>(smem);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
-    tc::tmem_alloc(&tmem_sh, 64);
+    tc::tmem_alloc(&tmem_sh, 32);
     tc::tmem_relinquish();
   }
   if (tid == 0) tc::mbar_init(&mbar, 1);
@@ -433,7 +443,7 @@ __global__ void __launch_bounds__(128) k_pix(PixArgs a) {
       const uint32_t b0 = tc::smem_u32(sW[layer]);
 #pragma unroll
       for (int kk = 0; kk < 2; ++kk)
-        tc::mma_bf16(tmem + 32 * layer, tc::smem_desc(a0 + kk * 256, 128, 512),
+        tc::mma_bf16(tmem, tc::smem_desc(a0 + kk * 256, 128, 512),
                      tc::smem_desc(b0 + kk * 256, 128, 512), idesc, kk > 0 ? 1u : 0u);
       tc::mma_commit(&mbar);
     }
@@ -445,7 +455,7 @@ __global__ void __launch_bounds__(128) k_pix(PixArgs a) {
 #pragma unroll
     for (int c0 = 0; c0 < 32; c0 += 16) {
       float v[16];
-      tc::tmem_ld16(tmem + 32 * layer + (uint32_t(warp * 32) << 16) + uint32_t(c0), v);
+      tc::tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), v);
 #pragma unroll
       for (int i = 0; i < 16; ++i) acc[c0 + i] = v[i];
     }
@@ -469,6 +479,7 @@ __global__ void __launch_bounds__(128) k_pix(PixArgs a) {
       __syncthreads();
       tc::fence_after_sync();
     } else {
+      __syncthreads();  // every thread is past the tiles before they are overwritten
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         sH[tid][2 * i] = bf_lo(u[i]);
@@ -491,7 +502,7 @@ __global__ void __launch_bounds__(128) k_pix(PixArgs a) {
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+  if (warp == 0) tc::tmem_dealloc(tmem, 32);
 }
 
 // ------------------------------------------------------------ elementwise
