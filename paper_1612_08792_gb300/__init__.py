@@ -33,7 +33,7 @@ __all__ = [
     "gmmsp_net_forward", "gmmsp_net_grad", "gmmsp_net_adam", "gmmsp_net_train_step", "gmmsp_net_get_activation",
     "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
     "GMMSP_OK", "GMMSP_E_INVALID", "GMMSP_E_CUDA", "GMMSP_E_NOMEM", "GMMSP_E_NUMERIC", "GMMSP_E_TIMEOUT",
-    "GMMSP_E_STATE",
+    "GMMSP_E_STATE", "gmmsp_segmentation_metrics",
 ]
 
 GMMSP_RGB8, GMMSP_LAB32 = 0, 1
@@ -510,6 +510,33 @@ def gmmsp_batch_lab(b) -> int:
 
 def gmmsp_batch_targets(b, target) -> None:
     _bcheck(b, _net_lib().gmmsp_batch_targets(b, _dptr(target)))
+
+
+class gmmsp_seg_metrics(ctypes.Structure):
+    _fields_ = [("br", ctypes.c_double), ("ue", ctypes.c_double), ("asa", ctypes.c_double),
+                ("br_recovered", ctypes.c_longlong), ("br_total", ctypes.c_longlong),
+                ("ue_sum", ctypes.c_longlong), ("asa_sum", ctypes.c_longlong)]
+
+
+def gmmsp_segmentation_metrics(labels, gt, K: int, G: int, radius: int = 2, eps: float = 0.05, stream=None):
+    """BR, UE (Eq. ue) and ASA (Eq. asa) of an (H, W) int32 CUDA label map against an
+    (H, W) int32 CUDA ground truth with ids in [0, G); synchronises."""
+    lib = load_library()
+    f = lib.gmmsp_segmentation_metrics
+    if not getattr(f, "_sig", False):
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                      ctypes.c_int, ctypes.c_double, ctypes.POINTER(gmmsp_seg_metrics), ctypes.c_void_p]
+        f._sig = True
+    H, W = int(labels.shape[0]), int(labels.shape[1])
+    if tuple(gt.shape) != (H, W) or not labels.is_contiguous() or not gt.is_contiguous():
+        raise ValueError("labels and gt must be contiguous (H, W) maps of one size")
+    out = gmmsp_seg_metrics()
+    st = f(_dptr(labels), _dptr(gt), W, H, int(K), int(G), int(radius), float(eps), ctypes.byref(out),
+           _stream_handle(stream))
+    if st != 0:
+        raise GmmspError(st, "segmentation metrics failed (bad arguments or ids out of range)")
+    return {k: getattr(out, k) for k, _ in gmmsp_seg_metrics._fields_}
 
 
 class SuperpixelsBatch:

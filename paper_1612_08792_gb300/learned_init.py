@@ -25,7 +25,7 @@ import numpy as np
 
 from . import (SuperpixelsBatch, gmmsp_net_check, gmmsp_net_create, gmmsp_net_destroy, gmmsp_net_forward,
                gmmsp_net_get_weights, gmmsp_net_grad, gmmsp_net_param_count, gmmsp_net_set_weights,
-               gmmsp_net_train_step)
+               gmmsp_net_train_step, gmmsp_segmentation_metrics)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS_DIR = os.path.join(HERE, "weights")
@@ -128,9 +128,10 @@ def load_pretrained(spacing: int = 15, stream=None) -> InitNet:
     return InitNet.load(pretrained_path(spacing), stream=stream)
 
 
-def _images(seeds, buf):
+def _images(seeds, buf, regions_out=None):
     from synth.voronoi_torch import voronoi_batch
-    voronoi_batch(TRAIN["W"], TRAIN["H"], TRAIN["regions"], TRAIN["sigma"], seeds, out=buf)
+    voronoi_batch(TRAIN["W"], TRAIN["H"], TRAIN["regions"], TRAIN["sigma"], seeds, out=buf,
+                  regions_out=regions_out)
     return [buf[i] for i in range(buf.shape[0])]
 
 
@@ -175,42 +176,61 @@ def train(steps: int = 2000, batch: int = 32, lr: float = 3e-3, lr_final: float 
 
 
 def evaluate(net: InitNet, n_images: int = 64, seed0: int = HELD_OUT_SEED0, plain_iters=(2, 3, 10),
-             learned_iters=(2,), batch: int = 64):
-    """Held-out images: mean per-pixel log-likelihood L(theta_T) / (W H) for the
-    paper's start (plain) and the network's start (learned), and the fraction of
-    pixels whose label after each learned run equals the label after the longest
-    plain run."""
+             learned_iters=(2,), batch: int = 64, accuracy: bool = True):
+    """Held-out images, for the paper's start (plain) and the network's start
+    (learned):
+      * the mean per-pixel log-likelihood L(theta_T) / (W H);
+      * the fraction of pixels whose label after each learned run equals the
+        label after the longest plain run;
+      * with `accuracy`, the mean BR, UE and ASA (Sec. IV) against the
+        generator's regions."""
     import torch
     W, H, v = TRAIN["W"], TRAIN["H"], TRAIN["spacing"]
-    res = {f"plain{t}": [] for t in plain_iters}
-    res.update({f"learned{t}": [] for t in learned_iters})
+    K = (W // v) * (H // v)
+    runs = [f"plain{t}" for t in plain_iters] + [f"learned{t}" for t in learned_iters]
+    res = {r: [] for r in runs}
+    acc = {r: {"br": [], "ue": [], "asa": []} for r in runs}
     agree = {f"learned{t}": 0 for t in learned_iters}
     ref_t = max(plain_iters)
     nb = min(batch, n_images)
     buf = torch.empty((nb, H, W, 3), dtype=torch.uint8, device="cuda")
+    regs = torch.empty((nb, H, W), dtype=torch.int32, device="cuda")
     bt = SuperpixelsBatch([(H, W)] * nb, spacing=v)
     done = 0
+
+    def score(run, labels, take):
+        if not accuracy:
+            return
+        for i in range(take):
+            m = gmmsp_segmentation_metrics(labels[i], regs[i], K, TRAIN["regions"])
+            for key in ("br", "ue", "asa"):
+                acc[run][key].append(m[key])
+
     for s0 in range(0, n_images, nb):
         seeds = [seed0 + s0 + i for i in range(nb)]
-        imgs = _images(seeds, buf)
+        imgs = _images(seeds, buf, regs)
         take = min(nb, n_images - s0)
         bt.set_init_net(None)
         ref_labels = None
         for t in plain_iters:
             labels, ll = bt.segment(imgs, iters=t, want_loglik=True)
             res[f"plain{t}"] += list(ll[:take] / (W * H))
+            score(f"plain{t}", labels, take)
             if t == ref_t:
                 ref_labels = [x.clone() for x in labels[:take]]
         bt.set_init_net(net)
         for t in learned_iters:
             labels, ll = bt.segment(imgs, iters=t, want_loglik=True)
             res[f"learned{t}"] += list(ll[:take] / (W * H))
+            score(f"learned{t}", labels, take)
             agree[f"learned{t}"] += sum(int((a == b).sum().item()) for a, b in zip(labels[:take], ref_labels))
         bt.set_init_net(None)
         done += take
     bt.close()
     out = {k: float(np.mean(v_)) for k, v_ in res.items()}
     out.update({f"label_agreement_{k}_vs_plain{ref_t}": a / (done * W * H) for k, a in agree.items()})
+    if accuracy:
+        out["accuracy"] = {r: {k: float(np.mean(v_)) for k, v_ in d.items()} for r, d in acc.items()}
     out["images"] = done
     return out
 

@@ -24,8 +24,10 @@ def _draws(W: int, H: int, regions: int, seed: int, grad_max: float):
 
 
 def voronoi_batch(W: int, H: int, regions: int, sigma: float, seeds, device="cuda", grad_max: float = 30.0,
-                  out=None):
-    """(B, H, W, 3) uint8 tensor on `device`, image i drawn from seeds[i]."""
+                  out=None, regions_out=None):
+    """(B, H, W, 3) uint8 tensor on `device`, image i drawn from seeds[i].  With
+    regions_out (a (B, H, W) int32 tensor) the region (Voronoi site) map of every
+    image is written there too: the ground truth of the accuracy metrics."""
     import torch
     seeds = list(seeds)
     if out is None:
@@ -54,4 +56,6 @@ def voronoi_batch(W: int, H: int, regions: int, sigma: float, seeds, device="cud
         gen.manual_seed(int(seed))
         img = img + sigma * torch.randn(img.shape, generator=gen, device=device, dtype=torch.float64)
         out[i] = torch.clamp(torch.round(img), 0, 255).to(torch.uint8)
+        if regions_out is not None:
+            regions_out[i] = reg.to(torch.int32)
     return out

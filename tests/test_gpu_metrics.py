@@ -1,0 +1,65 @@
+"""Accuracy metrics (BR, Eq. ue, Eq. asa) on the GPU against the metric oracle: exact."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import metrics as om
+from synth import voronoi_image
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    torch.cuda.set_device(0)
+    return gm
+
+
+def gpu_metrics(gm, labels, gt, K, G, radius=2, eps=0.05):
+    import torch
+    lt = torch.from_numpy(np.ascontiguousarray(labels.astype(np.int32))).cuda()
+    gtt = torch.from_numpy(np.ascontiguousarray(gt.astype(np.int32))).cuda()
+    return gm.gmmsp_segmentation_metrics(lt, gtt, K, G, radius, eps)
+
+
+def check_equal(m, ref):
+    assert m["br_recovered"] == ref["br_recovered"] and m["br_total"] == ref["br_total"]
+    assert m["ue_sum"] == ref["ue_sum"] and m["asa_sum"] == ref["asa_sum"]
+    assert m["br"] == ref["br"] and m["ue"] == ref["ue"] and m["asa"] == ref["asa"]
+
+
+@pytest.mark.parametrize("H,W,K,G,radius,eps", [(12, 9, 7, 4, 2, 0.05), (37, 23, 50, 6, 1, 0.05),
+                                                (64, 80, 300, 12, 2, 0.2), (5, 5, 3, 2, 0, 0.05)])
+def test_random_maps_exact(gm, H, W, K, G, radius, eps):
+    rng = np.random.default_rng(H * W)
+    labels = rng.integers(0, K, (H, W))
+    gt = rng.integers(0, G, (H, W))
+    check_equal(gpu_metrics(gm, labels, gt, K, G, radius, eps), om.all_metrics(labels, gt, radius, eps))
+
+
+def test_em_segmentation_exact(gm):
+    import torch
+    W, H = 481, 321
+    img, reg = voronoi_image(W, H, 150, 8.0, 7, return_regions=True)
+    sp = gm.Superpixels(torch.from_numpy(img).cuda(), spacing=15)
+    sp.em_iters(10)
+    labels = sp.labels().cpu().numpy()
+    K = sp.grid.K
+    sp.close()
+    ref = om.all_metrics(labels, reg, 2, 0.05)
+    check_equal(gpu_metrics(gm, labels, reg, K, 150), ref)
+    assert 0.5 < ref["br"] <= 1.0 and 0.0 <= ref["ue"] and 0.8 < ref["asa"] <= 1.0
+    # identities
+    m = gpu_metrics(gm, reg, reg, 150, 150)
+    assert m["br"] == 1.0 and m["ue"] == 0.0 and m["asa"] == 1.0
+
+
+def test_out_of_range_is_rejected(gm):
+    labels = np.zeros((8, 8), dtype=np.int32)
+    labels[3, 3] = 9
+    with pytest.raises(gm.GmmspError):
+        gpu_metrics(gm, labels, np.zeros((8, 8), dtype=np.int32), 5, 1)
