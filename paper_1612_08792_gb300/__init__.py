@@ -33,7 +33,8 @@ __all__ = [
     "gmmsp_net_forward", "gmmsp_net_grad", "gmmsp_net_adam", "gmmsp_net_train_step", "gmmsp_net_get_activation",
     "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
     "GMMSP_OK", "GMMSP_E_INVALID", "GMMSP_E_CUDA", "GMMSP_E_NOMEM", "GMMSP_E_NUMERIC", "GMMSP_E_TIMEOUT",
-    "GMMSP_E_STATE", "gmmsp_segmentation_metrics",
+    "GMMSP_E_STATE", "gmmsp_segmentation_metrics", "gmmsp_enforce_connectivity", "gmmsp_connectivity",
+    "gmmsp_batch_connectivity",
 ]
 
 GMMSP_RGB8, GMMSP_LAB32 = 0, 1
@@ -539,6 +540,52 @@ def gmmsp_segmentation_metrics(labels, gt, K: int, G: int, radius: int = 2, eps:
     return {k: getattr(out, k) for k, _ in gmmsp_seg_metrics._fields_}
 
 
+class gmmsp_conn_stats(ctypes.Structure):
+    _fields_ = [("components", ctypes.c_longlong), ("small", ctypes.c_longlong), ("merged", ctypes.c_longlong)]
+
+
+def _conn_lib():
+    lib = load_library()
+    if not getattr(lib, "_conn_sigs", False):
+        P, I = ctypes.c_void_p, ctypes.c_int
+        PS = ctypes.POINTER(gmmsp_conn_stats)
+        for name, args in {"gmmsp_enforce_connectivity": [P, P, I, I, I, PS, P],
+                           "gmmsp_connectivity": [P, P, PS],
+                           "gmmsp_batch_connectivity": [P, P, PS]}.items():
+            f = getattr(lib, name)
+            f.restype = I
+            f.argtypes = args
+        lib._conn_sigs = True
+    return lib
+
+
+def _stats(st):
+    return {"components": st.components, "small": st.small, "merged": st.merged}
+
+
+def gmmsp_enforce_connectivity(labels, lab_planes, W: int, H: int, K: int, stream=None):
+    """Algorithm 1, step 8 on an (H, W) int32 CUDA label map (rewritten in place);
+    lab_planes: the CIELAB image as (3, H, W) float32 CUDA planes (or their address)."""
+    st = gmmsp_conn_stats()
+    r = _conn_lib().gmmsp_enforce_connectivity(_dptr(labels), _dptr(lab_planes), int(W), int(H), int(K),
+                                               ctypes.byref(st), _stream_handle(stream))
+    if r != 0:
+        raise GmmspError(r, "connectivity post-processing failed")
+    return _stats(st)
+
+
+def gmmsp_connectivity(ctx, labels):
+    st = gmmsp_conn_stats()
+    _check(ctx, _conn_lib().gmmsp_connectivity(ctx, _dptr(labels), ctypes.byref(st)))
+    return _stats(st)
+
+
+def gmmsp_batch_connectivity(b, labels):
+    st = gmmsp_conn_stats()
+    _bcheck(b, _conn_lib().gmmsp_batch_connectivity(b, _ptr_array(labels), ctypes.byref(st)))
+    return _stats(st)
+
+
 class SuperpixelsBatch:
     """A batch context over lists of (H, W, 3) uint8 RGB (or float32 CIELAB) CUDA tensors."""
 
@@ -575,6 +622,10 @@ class SuperpixelsBatch:
 
     def tuning(self):
         return gmmsp_batch_get_tuning(self.b)
+
+    def connectivity(self):
+        """Algorithm 1, step 8 on the labels of the last segment (in place); totals."""
+        return gmmsp_batch_connectivity(self.b, self.labels)
 
     def get_params(self, i: int, K: int):
         return gmmsp_batch_get_params(self.b, i, K)
@@ -713,6 +764,10 @@ class Superpixels:
 
     def get_lab(self):
         return gmmsp_get_lab(self.ctx, self.H, self.W)
+
+    def connectivity(self, labels):
+        """Algorithm 1, step 8 on `labels` (from this context's last labels / segment), in place."""
+        return gmmsp_connectivity(self.ctx, labels)
 
     def init_from_net(self, net) -> None:
         """Replace theta by the network's theta_0 for the current image."""

@@ -514,6 +514,16 @@ gmmsp_status gmmsp_set_params(gmmsp_ctx c, const double* mu_host, const double* 
   return GMMSP_OK;
 }
 
+gmmsp_status gmmsp_connectivity(gmmsp_ctx c, int32_t* labels_dev, gmmsp_conn_stats* stats_host) {
+  gmmsp_status st = check_ready(c);
+  if (st != GMMSP_OK) return st;
+  if (!labels_dev) return fail(c, GMMSP_E_INVALID, "null labels");
+  st = gmmsp::enforce_connectivity(labels_dev, c->lab, c->g.W, c->g.H, c->g.K, stats_host, c->stream);
+  if (st == GMMSP_E_CUDA || st == GMMSP_E_NOMEM) return fail(c, st, "connectivity post-processing failed");
+  if (st != GMMSP_OK) c->err = "connectivity post-processing: a bounded device loop ran out";
+  return st;
+}
+
 gmmsp_status gmmsp_init_from_net(gmmsp_ctx c, gmmsp_net n) {
   gmmsp_status st = check_ready(c);
   if (st != GMMSP_OK) return st;

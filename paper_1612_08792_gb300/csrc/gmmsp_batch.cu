@@ -425,6 +425,24 @@ gmmsp_status gmmsp_batch_set_init_net(gmmsp_batch b, gmmsp_net net) {
   return GMMSP_OK;
 }
 
+gmmsp_status gmmsp_batch_connectivity(gmmsp_batch b, int32_t* const* labels_dev, gmmsp_conn_stats* stats_host) {
+  if (!b || !labels_dev) return GMMSP_E_INVALID;
+  gmmsp_conn_stats total{0, 0, 0};
+  for (int i = 0; i < b->n; ++i) {
+    if (!labels_dev[i]) return bfail(b, GMMSP_E_INVALID, "null labels");
+    const BatchImage& im = b->host[i];
+    gmmsp_conn_stats st{0, 0, 0};
+    const gmmsp_status r = gmmsp::enforce_connectivity(labels_dev[i], b->lab + 3 * im.pix_off, im.g.W, im.g.H,
+                                                       im.g.K, &st, b->stream);
+    if (r != GMMSP_OK) return bfail(b, r, "connectivity post-processing failed");
+    total.components += st.components;
+    total.small += st.small;
+    total.merged += st.merged;
+  }
+  if (stats_host) *stats_host = total;
+  return GMMSP_OK;
+}
+
 gmmsp_status gmmsp_batch_lab(gmmsp_batch b, const float** lab_dev) {
   if (!b || !lab_dev) return GMMSP_E_INVALID;
   *lab_dev = b->lab;

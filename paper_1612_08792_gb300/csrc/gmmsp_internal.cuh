@@ -169,3 +169,11 @@ cudaError_t launch_ll_per_image(const BatchImage* imgs, int n, const double* cel
                                 cudaStream_t s);
 
 }  // namespace gmmsp
+
+#include "../../include/gmmsp_conn.h"
+namespace gmmsp {
+// Connectivity post-processing of one image (labels in place; lab: three
+// FP32 planes of W H values); synchronises `s`.
+gmmsp_status enforce_connectivity(int32_t* labels_dev, const float* lab, int W, int H, int K,
+                                  gmmsp_conn_stats* stats, cudaStream_t s);
+}  // namespace gmmsp
