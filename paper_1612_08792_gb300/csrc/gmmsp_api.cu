@@ -72,6 +72,7 @@ struct gmmsp_ctx_s {
   unsigned long long* counters = nullptr;
   int* bad = nullptr;
   int wpc = 1;                    // warps per cell of the E+M pass (launch shape)
+  gmmsp::ConnScratch conn;        // post-processing scratch, kept between calls
   bool timing = false;            // record events between the kernels (gmmsp_set_timing)
   std::vector<cudaEvent_t> tev;   // timing events, created on demand
   int tev_used = 0;               // events recorded by the last enqueued sequence
@@ -518,7 +519,7 @@ gmmsp_status gmmsp_connectivity(gmmsp_ctx c, int32_t* labels_dev, gmmsp_conn_sta
   gmmsp_status st = check_ready(c);
   if (st != GMMSP_OK) return st;
   if (!labels_dev) return fail(c, GMMSP_E_INVALID, "null labels");
-  st = gmmsp::enforce_connectivity(labels_dev, c->lab, c->g.W, c->g.H, c->g.K, stats_host, c->stream);
+  st = gmmsp::enforce_connectivity(labels_dev, c->lab, c->g.W, c->g.H, c->g.K, stats_host, c->stream, &c->conn);
   if (st == GMMSP_E_CUDA || st == GMMSP_E_NOMEM) return fail(c, st, "connectivity post-processing failed");
   if (st != GMMSP_OK) c->err = "connectivity post-processing: a bounded device loop ran out";
   return st;
@@ -682,6 +683,7 @@ void gmmsp_destroy(gmmsp_ctx c) {
   free_graph(c);
   free_timing(c);
   if (c->slab) cudaFree(c->slab);
+  if (c->conn.ptr) cudaFree(c->conn.ptr);
   delete c;
 }
 

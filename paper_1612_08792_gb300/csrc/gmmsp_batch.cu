@@ -55,6 +55,7 @@ struct gmmsp_batch_s {
   int g_bps = -1;
   gmmsp_net g_net = nullptr;
   long long g_gen = -1;
+  gmmsp::ConnScratch conn;         // post-processing scratch, kept between calls
   std::string err;
   gmmsp_status state = GMMSP_OK;
 };
@@ -427,19 +428,19 @@ gmmsp_status gmmsp_batch_set_init_net(gmmsp_batch b, gmmsp_net net) {
 
 gmmsp_status gmmsp_batch_connectivity(gmmsp_batch b, int32_t* const* labels_dev, gmmsp_conn_stats* stats_host) {
   if (!b || !labels_dev) return GMMSP_E_INVALID;
-  gmmsp_conn_stats total{0, 0, 0};
+  std::vector<int> W(b->n), H(b->n), K(b->n);
+  std::vector<const float*> lab(b->n);
   for (int i = 0; i < b->n; ++i) {
     if (!labels_dev[i]) return bfail(b, GMMSP_E_INVALID, "null labels");
     const BatchImage& im = b->host[i];
-    gmmsp_conn_stats st{0, 0, 0};
-    const gmmsp_status r = gmmsp::enforce_connectivity(labels_dev[i], b->lab + 3 * im.pix_off, im.g.W, im.g.H,
-                                                       im.g.K, &st, b->stream);
-    if (r != GMMSP_OK) return bfail(b, r, "connectivity post-processing failed");
-    total.components += st.components;
-    total.small += st.small;
-    total.merged += st.merged;
+    W[i] = im.g.W;
+    H[i] = im.g.H;
+    K[i] = im.g.K;
+    lab[i] = b->lab + 3 * im.pix_off;
   }
-  if (stats_host) *stats_host = total;
+  const gmmsp_status r = gmmsp::enforce_connectivity_many(b->n, W.data(), H.data(), K.data(), labels_dev, lab.data(),
+                                                          stats_host, b->stream, &b->conn);
+  if (r != GMMSP_OK) return bfail(b, r, "connectivity post-processing failed");
   return GMMSP_OK;
 }
 
@@ -463,6 +464,7 @@ void gmmsp_batch_destroy(gmmsp_batch b) {
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
   if (b->slab) cudaFree(b->slab);
+  if (b->conn.ptr) cudaFree(b->conn.ptr);
   delete b;
 }
 

@@ -17,12 +17,14 @@
 // cluster's own (size, index) order, gives exactly what the sequential pass
 // over the whole image gives there.  One thread runs each cluster.
 //
-// Kernels: union-find component labelling (k_cc_*), component sizes and
-// colour sums (k_comp_stats), small-component indices (k_small_index), one
-// edge walk (k_edges) three times -- small-small clusters, then the
-// adjacency lists of the small components -- a block scan for the offsets,
-// the cluster member lists (k_cluster_count / _fill), the per-cluster merge
-// (k_cluster_merge) and the relabelling (k_relabel).
+// Kernels (all images of a call at once: blockIdx.y is the image): union-
+// find component labelling (k_cc_*), component sizes and colour sums
+// (k_comp_stats), small-component indices (k_small_index), one edge walk
+// (k_edges) three times -- small-small clusters, then the adjacency lists of
+// the small components -- a block scan for the offsets, the cluster member
+// lists (k_cluster_count / _fill), the per-cluster merge (k_cluster_merge)
+// and the relabelling (k_relabel).  One allocation (kept by a context
+// between calls) and one synchronisation per call.
 // Every loop over a parent chain or a retry is bounded; running out sets the
 // error word (reported as GMMSP_E_TIMEOUT).
 #include <cuda_runtime.h>
@@ -30,6 +32,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "../../include/gmmsp.h"
 #include "../../include/gmmsp_conn.h"
@@ -42,6 +45,14 @@ constexpr int kMaxHops = 1 << 24;      // bound on any parent-chain walk or unio
 constexpr int kFixedShift = 20;        // colour sums in units of 2^-20
 constexpr int kMaxCluster = 1 << 16;   // bound on the members one cluster thread sorts
 
+// One image of a call: pixels [off, off + W H) of the call's arrays.
+struct Img {
+  int W, H, K;
+  long long off;
+  const float* lab;   // three FP32 planes of W H values
+  int32_t* labels;    // the caller's labels (rewritten)
+};
+
 struct Scratch {
   int* parent;                // per pixel: component union-find, then the component root
   int* size;                  // per root: component size
@@ -49,6 +60,7 @@ struct Scratch {
   int* cpar;                  // per small root: cluster union-find over roots
   int* sid;                   // per root: index of the small component, or -1
   int* sroot;                 // per small index: its root
+  int* simg;                  // per small index: its image
   int* deg;                   // per small index: adjacency count, then fill cursor
   int* aoff;                  // per small index + 1: adjacency offsets
   int* adj;                   // adjacency lists (roots of neighbouring components)
@@ -59,7 +71,9 @@ struct Scratch {
   int* gsize;                 // per root: group size
   int* next;                  // per small root: next member of its group, -1 at the end
   int* tail;                  // per small root founding a group: last member
-  unsigned long long* cnt;    // counters: 0 small, 1 merged, 2 components, 3 edges, 4 error
+  int32_t* in;                // the input labels of all images
+  unsigned long long* cnt;    // counters: 0 small, 1 merged, 2 components
+  int* nsmall;                // the small count as int (read by later kernels)
   int* err;
 };
 
@@ -73,12 +87,29 @@ __device__ __forceinline__ int find_root(const int* p, int x, int* err) {
   return x;
 }
 
+// Root of x with path halving, for the union phase: every visited node is
+// re-pointed at its grandparent, an ancestor in the same set, so no set
+// changes; a concurrent link that such a store overwrites is redone by that
+// link's own retry.
+__device__ __forceinline__ int find_halve(int* p, int x, int* err) {
+  for (int h = 0; h < kMaxHops; ++h) {
+    const int q = p[x];
+    if (q == x) return x;
+    const int r = p[q];
+    if (r == q) return q;
+    p[x] = r;
+    x = r;
+  }
+  atomicExch(err, 1);
+  return x;
+}
+
 // Lock-free union by the smaller index (atomicMin on the larger root): the
 // final root of every set is its smallest member.
 __device__ __forceinline__ void unite(int* p, int a, int b, int* err) {
   for (int h = 0; h < kMaxHops; ++h) {
-    a = find_root(p, a, err);
-    b = find_root(p, b, err);
+    a = find_halve(p, a, err);
+    b = find_halve(p, b, err);
     if (a == b) return;
     if (a < b) {
       const int old = atomicMin(p + b, a);
@@ -93,33 +124,44 @@ __device__ __forceinline__ void unite(int* p, int a, int b, int* err) {
   atomicExch(err, 1);
 }
 
-__global__ void k_cc_init(int* __restrict__ p, long long N) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    p[i] = int(i);
-}
+// Per-image pixel loops: blockIdx.y is the image, x strides over its pixels.
+#define FOR_PIXELS(im, i)                                                                    \
+  const Img im = imgs[blockIdx.y];                                                           \
+  const long long im##_N = (long long)im.W * im.H;                                           \
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < im##_N;           \
+       i += (long long)gridDim.x * blockDim.x)
 
-__global__ void k_cc_union(const int32_t* __restrict__ L, int W, int H, int* p, int* err) {
-  const long long N = (long long)W * H;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const int y = int(i / W), x = int(i - (long long)y * W);
-    if (x + 1 < W && L[i] == L[i + 1]) unite(p, int(i), int(i + 1), err);
-    if (y + 1 < H && L[i] == L[i + W]) unite(p, int(i), int(i + W), err);
+__global__ void k_cc_init(const Img* __restrict__ imgs, int* __restrict__ p, int32_t* __restrict__ in) {
+  FOR_PIXELS(im, i) {
+    p[im.off + i] = int(im.off + i);
+    in[im.off + i] = im.labels[i];
   }
 }
 
-__global__ void k_cc_flatten(int* p, long long N, int* err) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    p[i] = find_root(p, int(i), err);
+__global__ void k_cc_union(const Img* __restrict__ imgs, const int32_t* __restrict__ in, int* p, int* err) {
+  FOR_PIXELS(im, i) {
+    const int y = int(i / im.W), x = int(i - (long long)y * im.W);
+    const long long g = im.off + i;
+    if (x + 1 < im.W && in[g] == in[g + 1]) unite(p, int(g), int(g + 1), err);
+    if (y + 1 < im.H && in[g] == in[g + im.W]) unite(p, int(g), int(g + im.W), err);
+  }
 }
 
-__global__ void k_comp_stats(const int* __restrict__ p, const float* __restrict__ lab, long long N,
-                             int* __restrict__ size, long long* __restrict__ csum) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const int r = p[i];
+// After the unions: every pixel points at its root.  The walks only read, so
+// the one store per pixel (its root) cannot be overwritten by another
+// thread's walk (a halving store here could leave a non-root behind).
+__global__ void k_cc_flatten(const Img* __restrict__ imgs, int* p, int* err) {
+  FOR_PIXELS(im, i) p[im.off + i] = find_root(p, int(im.off + i), err);
+}
+
+__global__ void k_comp_stats(const Img* __restrict__ imgs, const int* __restrict__ p, int* __restrict__ size,
+                             long long* __restrict__ csum) {
+  FOR_PIXELS(im, i) {
+    const int r = p[im.off + i];
     atomicAdd(size + r, 1);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const long long f = llrint(double(lab[c * N + i]) * double(1 << kFixedShift));
+      const long long f = llrint(double(im.lab[c * im_N + i]) * double(1 << kFixedShift));
       atomicAdd(reinterpret_cast<unsigned long long*>(csum + 3LL * r + c), (unsigned long long)f);
     }
   }
@@ -128,65 +170,67 @@ __global__ void k_comp_stats(const int* __restrict__ p, const float* __restrict_
 __device__ __forceinline__ bool small_size(long long s, int K, long long N) { return 4LL * K * s < N; }
 
 // Small components get an index; every root starts its own group.
-__global__ void k_small_index(const int* __restrict__ p, const int* __restrict__ size, long long N, int K,
-                              int* __restrict__ sid, int* __restrict__ sroot, int* __restrict__ cpar,
-                              int* __restrict__ gpar, int* __restrict__ gsize, int* __restrict__ next,
-                              int* __restrict__ tail, unsigned long long* cnt) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    sid[i] = -1;
-    if (p[i] != int(i)) continue;
-    atomicAdd(cnt + 2, 1ull);
-    gpar[i] = int(i);
-    gsize[i] = size[i];
-    if (small_size(size[i], K, N)) {
-      const int s = int(atomicAdd(cnt + 0, 1ull));
-      sid[i] = s;
-      sroot[s] = int(i);
-      cpar[i] = int(i);
-      next[i] = -1;
-      tail[i] = int(i);
+__global__ void k_small_index(const Img* __restrict__ imgs, Scratch S) {
+  FOR_PIXELS(im, i) {
+    const long long g = im.off + i;
+    S.sid[g] = -1;
+    if (S.parent[g] != int(g)) continue;
+    atomicAdd(S.cnt + 2, 1ull);
+    S.gpar[g] = int(g);
+    S.gsize[g] = S.size[g];
+    if (small_size(S.size[g], im.K, im_N)) {
+      const int s = int(atomicAdd(S.cnt + 0, 1ull));
+      S.sid[g] = s;
+      S.sroot[s] = int(g);
+      S.simg[s] = int(blockIdx.y);
+      S.cpar[g] = int(g);
+      S.next[g] = -1;
+      S.tail[g] = int(g);
     }
   }
 }
+
+__global__ void k_set_nsmall(Scratch S) { *S.nsmall = int(S.cnt[0]); }
 
 // Walks the 4-neighbour edges between different components; `mode` 0 unites
 // small-small pairs into clusters, 1 counts each small side's adjacency, 2
 // fills it.
-__global__ void k_edges(const int* __restrict__ p, int W, int H, const int* __restrict__ sid, int* cpar,
-                        int* deg, const int* __restrict__ aoff, int* __restrict__ adj, int mode, int* err) {
-  const long long N = (long long)W * H;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const int y = int(i / W), x = int(i - (long long)y * W);
-    const int ri = p[i];
+__global__ void k_edges(const Img* __restrict__ imgs, Scratch S, int mode) {
+  FOR_PIXELS(im, i) {
+    const int y = int(i / im.W), x = int(i - (long long)y * im.W);
+    const long long g = im.off + i;
+    const int ri = S.parent[g];
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
       long long j;
       if (d == 0) {
-        if (x + 1 >= W) continue;
-        j = i + 1;
+        if (x + 1 >= im.W) continue;
+        j = g + 1;
       } else {
-        if (y + 1 >= H) continue;
-        j = i + W;
+        if (y + 1 >= im.H) continue;
+        j = g + im.W;
       }
-      const int rj = p[j];
+      const int rj = S.parent[j];
       if (ri == rj) continue;
-      const int si = sid[ri], sj = sid[rj];
+      const int si = S.sid[ri], sj = S.sid[rj];
       if (mode == 0) {
-        if (si >= 0 && sj >= 0) unite(cpar, ri, rj, err);
+        if (si >= 0 && sj >= 0) unite(S.cpar, ri, rj, S.err);
       } else if (mode == 1) {
-        if (si >= 0) atomicAdd(deg + si, 1);
-        if (sj >= 0) atomicAdd(deg + sj, 1);
+        if (si >= 0) atomicAdd(S.deg + si, 1);
+        if (sj >= 0) atomicAdd(S.deg + sj, 1);
       } else {
-        if (si >= 0) adj[aoff[si] + atomicAdd(deg + si, 1)] = rj;
-        if (sj >= 0) adj[aoff[sj] + atomicAdd(deg + sj, 1)] = ri;
+        if (si >= 0) S.adj[S.aoff[si] + atomicAdd(S.deg + si, 1)] = rj;
+        if (sj >= 0) S.adj[S.aoff[sj] + atomicAdd(S.deg + sj, 1)] = ri;
       }
     }
   }
 }
 
-// Exclusive prefix sum of n ints into out[0..n] (one block; n up to a few million).
-__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int n, int* __restrict__ out) {
+// Exclusive prefix sum of the first *np ints of `in` into out[0..*np] (one block).
+__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, const int* __restrict__ np,
+                                               int* __restrict__ out) {
   __shared__ int part[1024];
+  const int n = *np;
   const int t = threadIdx.x;
   const int chunk = (n + 1023) / 1024;
   const int b = t * chunk, e = min(n, b + chunk);
@@ -208,20 +252,20 @@ __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int n
   if (t == 1023) out[n] = part[1023];
 }
 
-// Cluster root of every small component (flattened), member counts per cluster root.
-__global__ void k_cluster_count(int* cpar, const int* __restrict__ sroot, const int* __restrict__ sid, int nsmall,
-                                int* __restrict__ cl_count, int* err) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsmall; s += gridDim.x * blockDim.x) {
-    const int c = find_root(cpar, sroot[s], err);
-    atomicAdd(cl_count + sid[c], 1);
+// Cluster root of every small component, member counts per cluster root.
+__global__ void k_cluster_count(Scratch S) {
+  const int n = *S.nsmall;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const int c = find_root(S.cpar, S.sroot[s], S.err);
+    atomicAdd(S.cl_count + S.sid[c], 1);
   }
 }
 
-__global__ void k_cluster_fill(const int* cpar, const int* __restrict__ sroot, const int* __restrict__ sid, int nsmall,
-                               const int* __restrict__ cl_off, int* cl_cur, int* __restrict__ cl_mem, int* err) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsmall; s += gridDim.x * blockDim.x) {
-    const int c = sid[find_root(cpar, sroot[s], err)];
-    cl_mem[cl_off[c] + atomicAdd(cl_cur + c, 1)] = s;
+__global__ void k_cluster_fill(Scratch S) {
+  const int n = *S.nsmall;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const int c = S.sid[find_root(S.cpar, S.sroot[s], S.err)];
+    S.cl_mem[S.cl_off[c] + atomicAdd(S.cl_count + c, 1)] = s;
   }
 }
 
@@ -239,188 +283,187 @@ __device__ __forceinline__ double dist2(const long long* csum, const int* size, 
 
 // One thread per cluster: the sequential rule over the cluster's members in
 // (size, root) order.
-__global__ void k_cluster_merge(const int* __restrict__ sroot, int nsmall, const int* __restrict__ cpar,
-                                const int* __restrict__ sid, const int* __restrict__ cl_off, int* cl_mem,
-                                const int* __restrict__ size, const long long* __restrict__ csum,
-                                const int* __restrict__ aoff, const int* __restrict__ adj, int* gpar, int* gsize,
-                                int* next, int* tail, int K, long long N, unsigned long long* cnt, int* err) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsmall; s += gridDim.x * blockDim.x) {
-    const int r0 = sroot[s];
-    if (cpar[r0] != r0) continue;  // not a cluster root
-    int* mem = cl_mem + cl_off[s];
-    const int n = cl_off[s + 1] - cl_off[s];
+__global__ void k_cluster_merge(const Img* __restrict__ imgs, Scratch S) {
+  const int nsm = *S.nsmall;
+  unsigned merged = 0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsm; s += gridDim.x * blockDim.x) {
+    const int r0 = S.sroot[s];
+    if (S.cpar[r0] != r0) continue;  // not a cluster root
+    const Img im = imgs[S.simg[s]];
+    const long long N = (long long)im.W * im.H;
+    int* mem = S.cl_mem + S.cl_off[s];
+    const int n = S.cl_off[s + 1] - S.cl_off[s];
     if (n > kMaxCluster) {
-      atomicExch(err, 1);
+      atomicExch(S.err, 1);
       continue;
     }
     // insertion sort of the members by (size, root)
     for (int a = 1; a < n; ++a) {
       const int v = mem[a];
-      const int rv = sroot[v];
-      const long long kv = ((long long)size[rv] << 32) | (unsigned)rv;
+      const int rv = S.sroot[v];
+      const long long kv = ((long long)S.size[rv] << 32) | (unsigned)rv;
       int b = a - 1;
       while (b >= 0) {
-        const int rb = sroot[mem[b]];
-        const long long kb = ((long long)size[rb] << 32) | (unsigned)rb;
+        const int rb = S.sroot[mem[b]];
+        const long long kb = ((long long)S.size[rb] << 32) | (unsigned)rb;
         if (kb <= kv) break;
         mem[b + 1] = mem[b];
         --b;
       }
       mem[b + 1] = v;
     }
-    unsigned merged = 0;
     for (int a = 0; a < n; ++a) {
-      const int r = sroot[mem[a]];
-      if (gpar[r] != r || !small_size(gsize[r], K, N)) continue;
+      const int r = S.sroot[mem[a]];
+      if (S.gpar[r] != r || !small_size(S.gsize[r], im.K, N)) continue;
       int best = -1;
       double bd = 0.0;
       int hops = 0;
-      for (int m = r; m >= 0 && hops < kMaxHops; m = next[m], ++hops) {
-        const int sm = sid[m];
-        for (int q = aoff[sm]; q < aoff[sm + 1]; ++q) {
-          const int g = find_root(gpar, adj[q], err);
+      for (int m = r; m >= 0 && hops < kMaxHops; m = S.next[m], ++hops) {
+        const int sm = S.sid[m];
+        for (int q = S.aoff[sm]; q < S.aoff[sm + 1]; ++q) {
+          const int g = find_root(S.gpar, S.adj[q], S.err);
           if (g == r) continue;
-          const double d = dist2(csum, size, r, g);
+          const double d = dist2(S.csum, S.size, r, g);
           if (best < 0 || d < bd || (d == bd && g < best)) {
             best = g;
             bd = d;
           }
         }
       }
-      if (hops >= kMaxHops) atomicExch(err, 1);
+      if (hops >= kMaxHops) atomicExch(S.err, 1);
       if (best < 0) continue;
-      gpar[r] = best;
-      atomicAdd(gsize + best, gsize[r]);  // a large destination may be shared with other clusters
-      gsize[r] = 0;
-      if (sid[best] >= 0) {  // a small founder keeps the member list of its group
-        next[tail[best]] = r;
-        tail[best] = tail[r];
+      S.gpar[r] = best;
+      atomicAdd(S.gsize + best, S.gsize[r]);  // a large destination may be shared with other clusters
+      S.gsize[r] = 0;
+      if (S.sid[best] >= 0) {  // a small founder keeps the member list of its group
+        S.next[S.tail[best]] = r;
+        S.tail[best] = S.tail[r];
       }
       ++merged;
     }
-    if (merged) atomicAdd(cnt + 1, (unsigned long long)merged);
   }
+  merged = __reduce_add_sync(0xffffffffu, merged);
+  if ((threadIdx.x & 31) == 0 && merged) atomicAdd(S.cnt + 1, (unsigned long long)merged);
 }
 
-__global__ void k_relabel(const int* __restrict__ p, const int* gpar, const int32_t* __restrict__ in, long long N,
-                          int32_t* __restrict__ out, int* err) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    out[i] = in[find_root(gpar, p[i], err)];
-}
-
-int grid_for(long long n, int block) {
-  return int(std::max<long long>(1, std::min<long long>((n + block - 1) / block, 152LL * 16)));
+__global__ void k_relabel(const Img* __restrict__ imgs, Scratch S) {
+  FOR_PIXELS(im, i) im.labels[i] = S.in[find_root(S.gpar, S.parent[im.off + i], S.err)];
 }
 
 }  // namespace conn
 
-// Runs the post-processing on one image: labels_dev in place, lab three FP32
-// planes of W H values.
-gmmsp_status enforce_connectivity(int32_t* labels_dev, const float* lab, int W, int H, int K,
-                                  gmmsp_conn_stats* stats, cudaStream_t s) {
+gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const int* K, int32_t* const* labels,
+                                       const float* const* lab, gmmsp_conn_stats* stats, cudaStream_t s,
+                                       ConnScratch* cache) {
   using namespace conn;
-  const long long N = (long long)W * H;
-  if (N >= (1LL << 30)) return GMMSP_E_INVALID;
+  if (n < 1 || n > 65535) return GMMSP_E_INVALID;
+  std::vector<Img> host(n);
+  long long T = 0, maxN = 0;
+  for (int i = 0; i < n; ++i) {
+    if (W[i] < 1 || H[i] < 1 || K[i] < 1 || !labels[i] || !lab[i]) return GMMSP_E_INVALID;
+    host[i] = Img{W[i], H[i], K[i], T, lab[i], labels[i]};
+    T += (long long)W[i] * H[i];
+    maxN = std::max(maxN, (long long)W[i] * H[i]);
+  }
+  if (T >= (1LL << 30)) return GMMSP_E_INVALID;
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t nI = up(size_t(N) * 4), nL = up(size_t(N) * 8);
-  // per-pixel / per-root arrays: parent, size, cpar, sid, gpar, gsize, next, tail, sroot, deg, cl_count,
-  // aoff (N + 1), cl_off (N + 1), csum (3 N long long), plus the copy of the input labels
+  const size_t nI = up(size_t(T) * 4), nI1 = up(size_t(T + 1) * 4);
+  size_t o[20];
   size_t off = 0;
-  const size_t o_parent = off; off += nI;
-  const size_t o_size = off; off += nI;
-  const size_t o_cpar = off; off += nI;
-  const size_t o_sid = off; off += nI;
-  const size_t o_gpar = off; off += nI;
-  const size_t o_gsize = off; off += nI;
-  const size_t o_next = off; off += nI;
-  const size_t o_tail = off; off += nI;
-  const size_t o_sroot = off; off += nI;
-  const size_t o_deg = off; off += nI;
-  const size_t o_clc = off; off += nI;
-  const size_t o_aoff = off; off += up(size_t(N + 1) * 4);
-  const size_t o_cloff = off; off += up(size_t(N + 1) * 4);
-  const size_t o_clmem = off; off += nI;
-  const size_t o_in = off; off += nI;
-  const size_t o_adj = off; off += up(size_t(N) * 16);  // <= 4 entries per pixel (2 edges, both sides)
-  const size_t o_csum = off; off += 3 * nL;
-  const size_t o_cnt = off; off += 256;
+  for (int j = 0; j < 14; ++j) { o[j] = off; off += nI; }          // 14 int arrays of T entries
+  o[14] = off; off += nI1;                                          // aoff
+  o[15] = off; off += nI1;                                          // cl_off
+  o[16] = off; off += up(size_t(T) * 16);                           // adj (<= 4 entries per pixel)
+  o[17] = off; off += up(size_t(T) * 24);                           // csum
+  o[18] = off; off += up(sizeof(Img) * n);                          // image table
+  o[19] = off; off += 256;                                          // counters
   void* slab = nullptr;
-  cudaError_t e = cudaMalloc(&slab, off);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return e == cudaErrorMemoryAllocation ? GMMSP_E_NOMEM : GMMSP_E_CUDA;
+  cudaError_t e = cudaSuccess;
+  if (cache && cache->bytes >= off) {
+    slab = cache->ptr;
+  } else {
+    if (cache && cache->ptr) {
+      cudaStreamSynchronize(s);
+      cudaFree(cache->ptr);
+      cache->ptr = nullptr;
+      cache->bytes = 0;
+    }
+    e = cudaMalloc(&slab, off);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? GMMSP_E_NOMEM : GMMSP_E_CUDA;
+    }
+    if (cache) {
+      cache->ptr = slab;
+      cache->bytes = off;
+    }
   }
   char* b = static_cast<char*>(slab);
+  int* ia[14];
+  for (int j = 0; j < 14; ++j) ia[j] = reinterpret_cast<int*>(b + o[j]);
   Scratch S{};
-  S.parent = reinterpret_cast<int*>(b + o_parent);
-  S.size = reinterpret_cast<int*>(b + o_size);
-  S.cpar = reinterpret_cast<int*>(b + o_cpar);
-  S.sid = reinterpret_cast<int*>(b + o_sid);
-  S.gpar = reinterpret_cast<int*>(b + o_gpar);
-  S.gsize = reinterpret_cast<int*>(b + o_gsize);
-  S.next = reinterpret_cast<int*>(b + o_next);
-  S.tail = reinterpret_cast<int*>(b + o_tail);
-  S.sroot = reinterpret_cast<int*>(b + o_sroot);
-  S.deg = reinterpret_cast<int*>(b + o_deg);
-  S.cl_count = reinterpret_cast<int*>(b + o_clc);
-  S.aoff = reinterpret_cast<int*>(b + o_aoff);
-  S.cl_off = reinterpret_cast<int*>(b + o_cloff);
-  S.cl_mem = reinterpret_cast<int*>(b + o_clmem);
-  int32_t* in = reinterpret_cast<int32_t*>(b + o_in);
-  S.adj = reinterpret_cast<int*>(b + o_adj);
-  S.csum = reinterpret_cast<long long*>(b + o_csum);
-  S.cnt = reinterpret_cast<unsigned long long*>(b + o_cnt);
-  S.err = reinterpret_cast<int*>(b + o_cnt + 64);
-  const int gb = grid_for(N, 256);
-  unsigned long long host[8] = {};
+  S.parent = ia[0]; S.size = ia[1]; S.cpar = ia[2]; S.sid = ia[3]; S.sroot = ia[4]; S.simg = ia[5];
+  S.deg = ia[6]; S.cl_count = ia[7]; S.cl_mem = ia[8]; S.gpar = ia[9]; S.gsize = ia[10]; S.next = ia[11];
+  S.tail = ia[12]; S.in = reinterpret_cast<int32_t*>(ia[13]);
+  S.aoff = reinterpret_cast<int*>(b + o[14]);
+  S.cl_off = reinterpret_cast<int*>(b + o[15]);
+  S.adj = reinterpret_cast<int*>(b + o[16]);
+  S.csum = reinterpret_cast<long long*>(b + o[17]);
+  Img* table = reinterpret_cast<Img*>(b + o[18]);
+  S.cnt = reinterpret_cast<unsigned long long*>(b + o[19]);
+  S.nsmall = reinterpret_cast<int*>(b + o[19] + 64);
+  S.err = reinterpret_cast<int*>(b + o[19] + 128);
+  // blocks per image: enough to fill the machine across the images
+  const long long per = std::max<long long>(1, std::min<long long>((maxN + 255) / 256, (152LL * 16 + n - 1) / n));
+  const dim3 gp{static_cast<unsigned>(per), static_cast<unsigned>(n)};
+  const int gs = 152 * 8;
+  unsigned long long hc[3] = {};
   int herr = 0;
-  int nsmall = 0;
   do {
+    if ((e = cudaMemcpyAsync(table, host.data(), sizeof(Img) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(S.size, 0, nI, s)) != cudaSuccess) break;
-    if ((e = cudaMemsetAsync(S.csum, 0, 3 * nL, s)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(S.csum, 0, up(size_t(T) * 24), s)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(S.deg, 0, nI, s)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(S.cl_count, 0, nI, s)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(S.cnt, 0, 256, s)) != cudaSuccess) break;
-    if ((e = cudaMemcpyAsync(in, labels_dev, size_t(N) * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) break;
-    k_cc_init<<<gb, 256, 0, s>>>(S.parent, N);
-    k_cc_union<<<gb, 256, 0, s>>>(in, W, H, S.parent, S.err);
-    k_cc_flatten<<<gb, 256, 0, s>>>(S.parent, N, S.err);
-    k_comp_stats<<<gb, 256, 0, s>>>(S.parent, lab, N, S.size, S.csum);
-    k_small_index<<<gb, 256, 0, s>>>(S.parent, S.size, N, K, S.sid, S.sroot, S.cpar, S.gpar, S.gsize, S.next,
-                                     S.tail, S.cnt);
-    k_edges<<<gb, 256, 0, s>>>(S.parent, W, H, S.sid, S.cpar, S.deg, S.aoff, S.adj, 0, S.err);
-    if ((e = cudaGetLastError()) != cudaSuccess) break;
-    if ((e = cudaMemcpyAsync(host, S.cnt, sizeof(host), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
-    nsmall = int(host[0]);
-    // adjacency of the small components
-    k_edges<<<gb, 256, 0, s>>>(S.parent, W, H, S.sid, S.cpar, S.deg, S.aoff, S.adj, 1, S.err);
-    k_scan<<<1, 1024, 0, s>>>(S.deg, nsmall, S.aoff);
+    k_cc_init<<<gp, 256, 0, s>>>(table, S.parent, S.in);
+    k_cc_union<<<gp, 256, 0, s>>>(table, S.in, S.parent, S.err);
+    k_cc_flatten<<<gp, 256, 0, s>>>(table, S.parent, S.err);
+    k_comp_stats<<<gp, 256, 0, s>>>(table, S.parent, S.size, S.csum);
+    k_small_index<<<gp, 256, 0, s>>>(table, S);
+    k_set_nsmall<<<1, 1, 0, s>>>(S);
+    k_edges<<<gp, 256, 0, s>>>(table, S, 0);
+    k_edges<<<gp, 256, 0, s>>>(table, S, 1);
+    k_scan<<<1, 1024, 0, s>>>(S.deg, S.nsmall, S.aoff);
     if ((e = cudaMemsetAsync(S.deg, 0, nI, s)) != cudaSuccess) break;
-    k_edges<<<gb, 256, 0, s>>>(S.parent, W, H, S.sid, S.cpar, S.deg, S.aoff, S.adj, 2, S.err);
-    // clusters and their member lists
-    const int gs = grid_for(std::max(nsmall, 1), 256);
-    k_cluster_count<<<gs, 256, 0, s>>>(S.cpar, S.sroot, S.sid, nsmall, S.cl_count, S.err);
-    k_scan<<<1, 1024, 0, s>>>(S.cl_count, nsmall, S.cl_off);
+    k_edges<<<gp, 256, 0, s>>>(table, S, 2);
+    k_cluster_count<<<gs, 256, 0, s>>>(S);
+    k_scan<<<1, 1024, 0, s>>>(S.cl_count, S.nsmall, S.cl_off);
     if ((e = cudaMemsetAsync(S.cl_count, 0, nI, s)) != cudaSuccess) break;
-    k_cluster_fill<<<gs, 256, 0, s>>>(S.cpar, S.sroot, S.sid, nsmall, S.cl_off, S.cl_count, S.cl_mem, S.err);
-    k_cluster_merge<<<gs, 256, 0, s>>>(S.sroot, nsmall, S.cpar, S.sid, S.cl_off, S.cl_mem, S.size, S.csum, S.aoff,
-                                       S.adj, S.gpar, S.gsize, S.next, S.tail, K, N, S.cnt, S.err);
-    k_relabel<<<gb, 256, 0, s>>>(S.parent, S.gpar, in, N, labels_dev, S.err);
+    k_cluster_fill<<<gs, 256, 0, s>>>(S);
+    k_cluster_merge<<<gs, 256, 0, s>>>(table, S);
+    k_relabel<<<gp, 256, 0, s>>>(table, S);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
-    if ((e = cudaMemcpyAsync(host, S.cnt, sizeof(host), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(hc, S.cnt, sizeof(hc), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(&herr, S.err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
     e = cudaStreamSynchronize(s);
   } while (false);
-  cudaFree(slab);
+  if (!cache) cudaFree(slab);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GMMSP_E_NOMEM : GMMSP_E_CUDA;
   if (herr) return GMMSP_E_TIMEOUT;
   if (stats) {
-    stats->components = (long long)host[2];
-    stats->small = (long long)host[0];
-    stats->merged = (long long)host[1];
+    stats->components = (long long)hc[2];
+    stats->small = (long long)hc[0];
+    stats->merged = (long long)hc[1];
   }
   return GMMSP_OK;
+}
+
+gmmsp_status enforce_connectivity(int32_t* labels_dev, const float* lab, int W, int H, int K,
+                                  gmmsp_conn_stats* stats, cudaStream_t s, ConnScratch* cache) {
+  int32_t* l[1] = {labels_dev};
+  const float* c[1] = {lab};
+  return enforce_connectivity_many(1, &W, &H, &K, l, c, stats, s, cache);
 }
 
 }  // namespace gmmsp
@@ -429,5 +472,5 @@ extern "C" gmmsp_status gmmsp_enforce_connectivity(int32_t* labels_dev, const fl
                                                    int K, gmmsp_conn_stats* stats_host, void* stream) {
   if (!labels_dev || !lab_planes_dev || W < 1 || H < 1 || K < 1) return GMMSP_E_INVALID;
   return gmmsp::enforce_connectivity(labels_dev, lab_planes_dev, W, H, K, stats_host,
-                                     static_cast<cudaStream_t>(stream));
+                                     static_cast<cudaStream_t>(stream), nullptr);
 }

@@ -172,8 +172,18 @@ cudaError_t launch_ll_per_image(const BatchImage* imgs, int n, const double* cel
 
 #include "../../include/gmmsp_conn.h"
 namespace gmmsp {
+// Device scratch a context keeps between post-processing calls (grown on demand).
+struct ConnScratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
 // Connectivity post-processing of one image (labels in place; lab: three
-// FP32 planes of W H values); synchronises `s`.
+// FP32 planes of W H values); synchronises `s`.  cache: kept scratch, or
+// nullptr to allocate and free within the call.
 gmmsp_status enforce_connectivity(int32_t* labels_dev, const float* lab, int W, int H, int K,
-                                  gmmsp_conn_stats* stats, cudaStream_t s);
+                                  gmmsp_conn_stats* stats, cudaStream_t s, ConnScratch* cache);
+// The same on n images in one set of launches (totals in stats).
+gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const int* K, int32_t* const* labels,
+                                       const float* const* lab, gmmsp_conn_stats* stats, cudaStream_t s,
+                                       ConnScratch* cache);
 }  // namespace gmmsp
