@@ -484,9 +484,9 @@ NET_FLOPS_PER_CELL = 2 * (3 * 288 * 32 + 288 * 16)
 # 96 such images (dram__bytes_read.sum + dram__bytes_write.sum), scaled per image
 # (traffic grows with the image count), per launch variant (blocks per SM):
 #   5: persistent k_em_pass_batch, 182.04 MB + 52.66 MB;
-#   7: one-cell-per-warp k_em_pass_batch_flat, 182.05 MB + 56.58 MB (spills included).
+#   7: one-cell-per-warp k_em_pass_batch_flat, 182.05 MB + 56.59 MB (spills included).
 EM_BATCH_TRAFFIC_PER_IMAGE = {5: int((182.039296e6 + 52.660480e6) / 96),
-                              7: int((182.051328e6 + 56.577536e6) / 96)}
+                              7: int((182.054400e6 + 56.586240e6) / 96)}
 
 
 def measured_peaks():
