@@ -34,6 +34,19 @@ _lib = None
 
 MAXC = 9  # |K_i| <= 9 (Sec. III-D)
 
+# Colour models (the `colour` argument below): the full 3x3 colour covariance
+# of Eq. (BlockSigma), the L | (a, b) split of Eq. (BlockSigma1), and a
+# grayscale image whose scalar colour is CIE L* (Sec. III-A, III-C).
+COLOUR_FULL, COLOUR_SPLIT, COLOUR_GRAY = 0, 1, 2
+_COLOUR_NAMES = {"full": COLOUR_FULL, "split": COLOUR_SPLIT, "gray": COLOUR_GRAY}
+
+
+def _cm(colour) -> int:
+    c = _COLOUR_NAMES.get(colour, colour) if isinstance(colour, str) else int(colour)
+    if c not in (COLOUR_FULL, COLOUR_SPLIT, COLOUR_GRAY):
+        raise ValueError(f"unknown colour model {colour!r}")
+    return c
+
 
 def build(force: bool = False) -> str:
     """Compile the C oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, OpenMP)."""
@@ -62,16 +75,17 @@ def _load():
             "orc_set_threads": (None, [I]),
             "orc_max_threads": (I, []),
             "orc_rgb2lab": (None, [P, L, P]),
+            "orc_gray2l": (None, [P, L, P]),
             "orc_grid": (I, [I, I, I, I, P]),
             "orc_candidates": (I, [I, I, I, I, I, P, P]),
             "orc_eig_clamp": (I, [I, P, D, P]),
             "orc_sym_eigvals": (None, [I, P, P]),
-            "orc_init": (None, [P, I, I, I, I, I, D, P, P, P]),
-            "orc_log_gauss": (D, [P, P, P, P]),
-            "orc_estep": (D, [P, I, I, I, P, P, P, P, P, P, P]),
-            "orc_mstep": (I, [P, I, I, I, I, I, P, P, P, D, D, P, P, P, P, P, P, P]),
+            "orc_init": (None, [P, I, I, I, I, I, D, P, P, P, I]),
+            "orc_log_gauss": (D, [P, P, P, P, I]),
+            "orc_estep": (D, [P, I, I, I, P, P, P, P, P, P, P, I]),
+            "orc_mstep": (I, [P, I, I, I, I, I, P, P, P, D, D, P, P, P, P, P, P, P, I]),
             "orc_labels": (None, [L, P, P, P, P, P]),
-            "orc_em": (I, [P, I, I, I, I, I, D, D, D, P, P, P, P, P, P, P, P, P, P, P, P, P]),
+            "orc_em": (I, [P, I, I, I, I, I, D, D, D, P, P, P, P, P, P, P, P, P, P, P, P, P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -107,6 +121,14 @@ def rgb2lab(rgb: np.ndarray) -> np.ndarray:
     assert rgb.shape[-1] == 3
     out = np.empty(rgb.shape, dtype=np.float64)
     _load().orc_rgb2lab(_ptr(rgb), int(rgb.size // 3), _ptr(out))
+    return out
+
+
+def gray2l(gray: np.ndarray) -> np.ndarray:
+    """Grey levels uint8 (...) -> CIE L* float64 (...): L* of Y = sRGB-decode(g / 255)."""
+    gray = np.ascontiguousarray(gray, dtype=np.uint8)
+    out = np.empty(gray.shape, dtype=np.float64)
+    _load().orc_gray2l(_ptr(gray), int(gray.size), _ptr(out))
     return out
 
 
@@ -147,7 +169,8 @@ class Theta:
     """theta_k = (mu_k, Sigma_k,s, Sigma_k,c) for all k, float64.
 
     mu: (K, 5) = (x, y, L, a, b); cs: (K, 3) = (xx, xy, yy);
-    cc: (K, 6) = (LL, La, Lb, aa, ab, bb).
+    cc: (K, 6) = (LL, La, Lb, aa, ab, bb).  Split model: La = Lb = 0;
+    grayscale: mu's a, b and every cc entry but LL are 0.
     """
     mu: np.ndarray
     cs: np.ndarray
@@ -157,21 +180,22 @@ class Theta:
         return Theta(self.mu.copy(), self.cs.copy(), self.cc.copy())
 
 
-def init_theta(lab: np.ndarray, g: Grid, lambda_c: float = 8.0) -> Theta:
+def init_theta(lab: np.ndarray, g: Grid, lambda_c: float = 8.0, colour="full") -> Theta:
     """Sec. III-C initialisation: centre pixels, diag(v^2, v^2), lambda^2 I."""
     lab = _f64(lab, (g.H * g.W, 3))
     th = Theta(np.zeros((g.K, 5)), np.zeros((g.K, 3)), np.zeros((g.K, 6)))
     _load().orc_init(_ptr(lab), g.W, g.H, g.v, g.nx, g.ny, float(lambda_c),
-                     _ptr(th.mu), _ptr(th.cs), _ptr(th.cc))
+                     _ptr(th.mu), _ptr(th.cs), _ptr(th.cc), _cm(colour))
     return th
 
 
-def log_gauss(z, mu, cs, cc) -> float:
+def log_gauss(z, mu, cs, cc, colour="full") -> float:
     """ln p(z; theta_k), Eq. (gaussian) with the block covariance."""
-    return float(_load().orc_log_gauss(_ptr(_f64(z)), _ptr(_f64(mu)), _ptr(_f64(cs)), _ptr(_f64(cc))))
+    return float(_load().orc_log_gauss(_ptr(_f64(z)), _ptr(_f64(mu)), _ptr(_f64(cs)), _ptr(_f64(cc)),
+                                       _cm(colour)))
 
 
-def estep(lab: np.ndarray, g: Grid, th: Theta, cand=None, ncand=None):
+def estep(lab: np.ndarray, g: Grid, th: Theta, cand=None, ncand=None, colour="full"):
     """Eq. (Rik).  Returns (R[N, 9], ll[N], L(theta), cand, ncand)."""
     if cand is None:
         cand, ncand = candidates(g)
@@ -180,11 +204,13 @@ def estep(lab: np.ndarray, g: Grid, th: Theta, cand=None, ncand=None):
     R = np.zeros((N, MAXC))
     ll = np.zeros(N)
     L = _load().orc_estep(_ptr(lab), g.W, g.H, g.K, _ptr(cand), _ptr(ncand),
-                          _ptr(_f64(th.mu)), _ptr(_f64(th.cs)), _ptr(_f64(th.cc)), _ptr(R), _ptr(ll))
+                          _ptr(_f64(th.mu)), _ptr(_f64(th.cs)), _ptr(_f64(th.cc)), _ptr(R), _ptr(ll),
+                          _cm(colour))
     return R, ll, float(L), cand, ncand
 
 
-def mstep(lab: np.ndarray, g: Grid, th: Theta, R, cand, ncand, eps_s: float = 2.0, eps_c: float = 8.0):
+def mstep(lab: np.ndarray, g: Grid, th: Theta, R, cand, ncand, eps_s: float = 2.0, eps_c: float = 8.0,
+          colour="full"):
     """Eq. (UpdateMu), (UpdateSigS), (UpdateSigC) and the floor (mlams, mlamc).
 
     Returns (theta_{t+1}, raw spatial cov, raw colour cov, wsum, dead, (raised_s, raised_c)).
@@ -198,14 +224,14 @@ def mstep(lab: np.ndarray, g: Grid, th: Theta, R, cand, ncand, eps_s: float = 2.
     dead = _load().orc_mstep(_ptr(lab), g.W, g.H, g.v, g.nx, g.ny, _ptr(cand), _ptr(ncand),
                              _ptr(_f64(R)), float(eps_s), float(eps_c),
                              _ptr(out.mu), _ptr(out.cs), _ptr(out.cc), _ptr(cs_raw), _ptr(cc_raw),
-                             _ptr(wsum), _ptr(nr))
+                             _ptr(wsum), _ptr(nr), _cm(colour))
     return out, cs_raw, cc_raw, wsum, int(dead), (int(nr[0]), int(nr[1]))
 
 
 def eig_clamp(packed: np.ndarray, eps: float) -> tuple[np.ndarray, int]:
-    """Eq. (eigdecs)-(eigdecrc): floor the eigenvalues of one packed 2x2 (3) or 3x3 (6)."""
+    """Eq. (eigdecs)-(eigdecrc): floor the eigenvalues of one packed 1x1 (1), 2x2 (3) or 3x3 (6)."""
     p = _f64(packed)
-    n = {3: 2, 6: 3}[p.size]
+    n = {1: 1, 3: 2, 6: 3}[p.size]
     out = np.zeros_like(p)
     raised = _load().orc_eig_clamp(n, _ptr(p), float(eps), _ptr(out))
     return out, int(raised)
@@ -244,8 +270,11 @@ class EMResult:
 
 def em(lab: np.ndarray, W: int, H: int, K: int = 0, spacing: int = 0, T: int = 10,
        lambda_c: float = 8.0, eps_s: float = 2.0, eps_c: float = 8.0,
-       theta0: Theta | None = None, keep_post: bool = False) -> EMResult:
-    """Algorithm 1, steps 1-7, on an (H, W, 3) CIELAB image (float, any precision)."""
+       theta0: Theta | None = None, keep_post: bool = False, colour="full") -> EMResult:
+    """Algorithm 1, steps 1-7, on an (H, W, 3) CIELAB image (float, any precision).
+
+    colour: "full" (Eq. BlockSigma), "split" (Eq. BlockSigma1) or "gray" (only
+    the L column of lab is read)."""
     g = grid(W, H, K, spacing)
     lab = _f64(lab, (H * W, 3))
     th = Theta(np.zeros((g.K, 5)), np.zeros((g.K, 3)), np.zeros((g.K, 6)))
@@ -263,7 +292,7 @@ def em(lab: np.ndarray, W: int, H: int, K: int = 0, spacing: int = 0, T: int = 1
     rc = _load().orc_em(_ptr(lab), W, H, int(K), int(spacing), int(T), float(lambda_c),
                         float(eps_s), float(eps_c), _ptr(mu_in), _ptr(cs_in), _ptr(cc_in),
                         _ptr(th.mu), _ptr(th.cs), _ptr(th.cc), _ptr(labels), _ptr(margin),
-                        _ptr(loglik), _ptr(post), _ptr(cand), _ptr(ncand), _ptr(raised))
+                        _ptr(loglik), _ptr(post), _ptr(cand), _ptr(ncand), _ptr(raised), _cm(colour))
     if rc < 0:
         raise RuntimeError(f"orc_em failed: {rc}")
     return EMResult(g, th, labels.reshape(H, W), margin.reshape(H, W), loglik, post, cand, ncand,

@@ -21,6 +21,10 @@
  *   - initialisation                                       Sec. III-C, the paragraph after Eq. (eigdecrc)
  *   - labels by maximum posterior                          Eq. (obtLi)
  *   - the loop                                             Algorithm 1, steps 1-7
+ * Three colour models (argument `cmodel`), Sec. III-A and III-C:
+ *   0  full: Sigma_c a 3x3 over (L, a, b)                  Eq. (BlockSigma)
+ *   1  split: Sigma_c = diag(sigma_l^2, Sigma_(a,b))       Eq. (BlockSigma1)
+ *   2  grayscale: c_i a scalar, Sigma_c = sigma^2          Sec. III-A, III-C (Q_k,c = 1)
  * The connectivity post-processing (Algorithm 1, step 8) is not part of the
  * EM loop and is not implemented here.
  *
@@ -31,6 +35,14 @@
  *     previous parameters (the paper does not say what happens then).
  *   - the floor epsilon is applied to eigenvalues of the covariance
  *     (variance units).
+ *   - grayscale: the scalar colour is the CIE L* of the pixel (the L
+ *     channel of a colour input; for a grey-level input g, L* of the
+ *     luminance Y = sRGB-decode(g / 255)), so that eps_c and lambda keep
+ *     their CIELAB units.
+ *   - the split model's M-step is the maximiser of Q over covariances of
+ *     the form of Eq. (BlockSigma1): the variance of L and the 2x2 weighted
+ *     covariance of (a, b), with no L-(a, b) cross terms; its floor acts on
+ *     the eigenvalues of each block (together, the eigenvalues of Sigma_c).
  *
  * Threading: the E-step is parallel over pixels and the M-step over
  * superpixels, the two independent loops the paper's Sec. III-D names.
@@ -45,7 +57,10 @@
 #include <omp.h>
 #endif
 
-#define ORC_D 5          /* dimension of z: x, y, L, a, b */
+#define ORC_D 5          /* dimension of z: x, y, L, a, b (x, y, L for grayscale) */
+#define ORC_FULL 0
+#define ORC_SPLIT 1
+#define ORC_GRAY 2
 #define ORC_MAXC 9       /* |K_i| <= 9, Sec. III-D */
 #define ORC_DEAD_W 1e-8  /* reading: below this total weight theta_k is kept */
 
@@ -114,6 +129,16 @@ void orc_rgb2lab(const uint8_t *rgb, long n, double *lab)
         lab[3 * i + 1] = 500.0 * (fx - fy);
         lab[3 * i + 2] = 200.0 * (fy - fz);
     }
+}
+
+/* Grey levels -> CIE L*: a grey pixel has R = G = B = g, whose luminance
+ * relative to the white is Y / Yn = sRGB-decode(g / 255) (the three primaries
+ * at equal drive add up to the white point). */
+void orc_gray2l(const uint8_t *gray, long n, double *L)
+{
+    long i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; ++i) L[i] = 116.0 * cielab_f(srgb_decode(gray[i] / 255.0)) - 16.0;
 }
 
 /* ------------------------------------------------------------------------
@@ -210,7 +235,9 @@ done:
  * ---------------------------------------------------------------------- */
 static void sym_unpack(int n, const double *p, double A[3][3])
 {
-    if (n == 2) {
+    if (n == 1) {
+        A[0][0] = p[0];
+    } else if (n == 2) {
         A[0][0] = p[0]; A[0][1] = A[1][0] = p[1]; A[1][1] = p[2];
     } else {
         A[0][0] = p[0]; A[0][1] = A[1][0] = p[1]; A[0][2] = A[2][0] = p[2];
@@ -220,7 +247,9 @@ static void sym_unpack(int n, const double *p, double A[3][3])
 
 static void sym_pack(int n, double A[3][3], double *p)
 {
-    if (n == 2) {
+    if (n == 1) {
+        p[0] = A[0][0];
+    } else if (n == 2) {
         p[0] = A[0][0]; p[1] = 0.5 * (A[0][1] + A[1][0]); p[2] = A[1][1];
     } else {
         p[0] = A[0][0]; p[1] = 0.5 * (A[0][1] + A[1][0]); p[2] = 0.5 * (A[0][2] + A[2][0]);
@@ -331,11 +360,12 @@ void orc_sym_eigvals(int n, const double *packed, double *lam)
 /* ------------------------------------------------------------------------
  * Initialisation, Sec. III-C: mu_k = z_j at the centre pixel
  *   j = k_x v + floor(v/2) + W (k_y v + floor(v/2)),
- * Sigma_s = diag(v^2, v^2), Sigma_c = lambda^2 I.
- * lab is N x 3 (L, a, b); mu is K x 5 (x, y, L, a, b).
+ * Sigma_s = diag(v^2, v^2), Sigma_c = lambda^2 I (of the colour dimension).
+ * lab is N x 3 (L, a, b); mu is K x 5 (x, y, L, a, b).  Grayscale: the
+ * colour is L alone; mu's a, b and every Sigma_c entry but LL are 0.
  * ---------------------------------------------------------------------- */
 void orc_init(const double *lab, int W, int H, int v, int nx, int ny, double lambda_c,
-              double *mu, double *cs, double *cc)
+              double *mu, double *cs, double *cc, int cmodel)
 {
     int k, K = nx * ny;
     (void)H;
@@ -351,31 +381,43 @@ void orc_init(const double *lab, int W, int H, int v, int nx, int ny, double lam
         cs[3 * k + 0] = (double)v * v; cs[3 * k + 1] = 0.0; cs[3 * k + 2] = (double)v * v;
         cc[6 * k + 0] = lambda_c * lambda_c; cc[6 * k + 1] = 0.0; cc[6 * k + 2] = 0.0;
         cc[6 * k + 3] = lambda_c * lambda_c; cc[6 * k + 4] = 0.0; cc[6 * k + 5] = lambda_c * lambda_c;
+        if (cmodel == ORC_GRAY) {
+            mu[5 * k + 3] = mu[5 * k + 4] = 0.0;
+            cc[6 * k + 3] = cc[6 * k + 5] = 0.0;
+        }
     }
 }
 
 /* ------------------------------------------------------------------------
- * Log of the Gaussian density, Eq. (gaussian), D = 5, with the block
- * diagonal covariance of Eq. (BlockSigma):
+ * Log of the Gaussian density, Eq. (gaussian), D = 2 + (colour dimension),
+ * with the block diagonal covariance of Eq. (BlockSigma):
  *   ln p = -(D/2) ln 2pi - (1/2) ln det Sigma - (1/2) d^T Sigma^{-1} d.
  * Sigma^{-1} d and ln det Sigma come from a Cholesky factor of each block.
+ * The colour block is the full 3x3 (model 0), diag(sigma_l^2, Sigma_(a,b))
+ * of Eq. (BlockSigma1) (model 1: the L-a and L-b entries are zero, whatever
+ * cc holds there), or the 1x1 sigma^2 of a grayscale image (model 2).
  * ---------------------------------------------------------------------- */
 typedef struct {
     double Ls[3][3], Lc[3][3];
     double logdet;
+    int nc;   /* colour dimension */
     int ok;
 } orc_chol;
 
-static void orc_factor(const double *cs, const double *cc, orc_chol *f)
+static void orc_factor(const double *cs, const double *cc, int cmodel, orc_chol *f)
 {
     double A[3][3] = {{0}}, B[3][3] = {{0}};
+    int j;
+    f->nc = (cmodel == ORC_GRAY) ? 1 : 3;
     sym_unpack(2, cs, A);
-    sym_unpack(3, cc, B);
-    f->ok = (cholesky(2, A, f->Ls) == 0) && (cholesky(3, B, f->Lc) == 0);
+    sym_unpack(f->nc, cc, B);
+    if (cmodel == ORC_SPLIT) B[0][1] = B[1][0] = B[0][2] = B[2][0] = 0.0;
+    f->ok = (cholesky(2, A, f->Ls) == 0) && (cholesky(f->nc, B, f->Lc) == 0);
     f->logdet = 0.0;
-    if (f->ok)
-        f->logdet = 2.0 * (log(f->Ls[0][0]) + log(f->Ls[1][1]) +
-                           log(f->Lc[0][0]) + log(f->Lc[1][1]) + log(f->Lc[2][2]));
+    if (f->ok) {
+        f->logdet = 2.0 * (log(f->Ls[0][0]) + log(f->Ls[1][1]));
+        for (j = 0; j < f->nc; ++j) f->logdet += 2.0 * log(f->Lc[j][j]);
+    }
 }
 
 static double quad_form(int n, const double (*L)[3], const double *d)
@@ -396,15 +438,15 @@ static double log_gauss(const double *z, const double *mu, const orc_chol *f)
 {
     double ds[2] = {z[0] - mu[0], z[1] - mu[1]};
     double dc[3] = {z[2] - mu[2], z[3] - mu[3], z[4] - mu[4]};
-    double q = quad_form(2, f->Ls, ds) + quad_form(3, f->Lc, dc);
-    return -0.5 * ORC_D * log(2.0 * ORC_PI) - 0.5 * f->logdet - 0.5 * q;
+    double q = quad_form(2, f->Ls, ds) + quad_form(f->nc, f->Lc, dc);
+    return -0.5 * (2 + f->nc) * log(2.0 * ORC_PI) - 0.5 * f->logdet - 0.5 * q;
 }
 
 /* Log density of pixel z under theta_k, exposed for tests. */
-double orc_log_gauss(const double *z, const double *mu, const double *cs, const double *cc)
+double orc_log_gauss(const double *z, const double *mu, const double *cs, const double *cc, int cmodel)
 {
     orc_chol f;
-    orc_factor(cs, cc, &f);
+    orc_factor(cs, cc, cmodel, &f);
     if (!f.ok) return NAN;
     return log_gauss(z, mu, &f);
 }
@@ -419,7 +461,7 @@ double orc_log_gauss(const double *z, const double *mu, const double *cs, const 
  * Returns L(theta), or NAN when a covariance is not positive definite.
  * ---------------------------------------------------------------------- */
 double orc_estep(const double *lab, int W, int H, int K, const int32_t *cand, const int32_t *ncand,
-                 const double *mu, const double *cs, const double *cc, double *R, double *ll)
+                 const double *mu, const double *cs, const double *cc, double *R, double *ll, int cmodel)
 {
     long N = (long)W * H, i;
     int k, bad = 0;
@@ -428,7 +470,7 @@ double orc_estep(const double *lab, int W, int H, int K, const int32_t *cand, co
     double *lli = malloc(sizeof(double) * (size_t)N);
     if (!F || !lli) { free(F); free(lli); return NAN; }
     for (k = 0; k < K; ++k) {
-        orc_factor(cs + 3 * k, cc + 6 * k, &F[k]);
+        orc_factor(cs + 3 * k, cc + 6 * k, cmodel, &F[k]);
         if (!F[k].ok) bad = 1;
     }
     if (bad) { free(F); free(lli); return NAN; }
@@ -463,6 +505,10 @@ double orc_estep(const double *lab, int W, int H, int K, const int32_t *cand, co
  * then the eigenvalue floor (Eq. mlams, mlamc) with eps_s, eps_c.
  * The covariances use the new mean (Algorithm 1, step 4 before step 5) and
  * are formed in two passes: the mean first, then centred products.
+ * Split model (Eq. BlockSigma1): sigma_l^2 and the (a, b) block are the
+ * same weighted sums with the L-a, L-b entries not formed (zero), and each
+ * block is floored on its own.  Grayscale: the colour is L alone (mu's a, b
+ * and Sigma_c's entries other than LL are zero).
  * mu, cs, cc hold theta_t on entry and theta_{t+1} on return.
  * cs_raw/cc_raw (optional) receive the covariances before the floor;
  * wsum (optional) receives sum_i R_ik; nraised (optional, [2]) counts the
@@ -472,7 +518,7 @@ double orc_estep(const double *lab, int W, int H, int K, const int32_t *cand, co
 int orc_mstep(const double *lab, int W, int H, int v, int nx, int ny,
               const int32_t *cand, const int32_t *ncand, const double *R,
               double eps_s, double eps_c, double *mu, double *cs, double *cc,
-              double *cs_raw, double *cc_raw, double *wsum, int *nraised)
+              double *cs_raw, double *cc_raw, double *wsum, int *nraised, int cmodel)
 {
     int K = nx * ny, k, dead = 0, rs = 0, rc = 0;
 #pragma omp parallel for schedule(static) reduction(+ : dead, rs, rc)
@@ -511,16 +557,30 @@ int orc_mstep(const double *lab, int W, int H, int v, int nx, int ny,
                 d[0] = x - m[0]; d[1] = y - m[1];
                 d[2] = lab[3 * i + 0] - m[2]; d[3] = lab[3 * i + 1] - m[3]; d[4] = lab[3 * i + 2] - m[4];
                 ps[0] += r * d[0] * d[0]; ps[1] += r * d[0] * d[1]; ps[2] += r * d[1] * d[1];
-                pc[0] += r * d[2] * d[2]; pc[1] += r * d[2] * d[3]; pc[2] += r * d[2] * d[4];
-                pc[3] += r * d[3] * d[3]; pc[4] += r * d[3] * d[4]; pc[5] += r * d[4] * d[4];
+                pc[0] += r * d[2] * d[2];
+                if (cmodel == ORC_FULL) { pc[1] += r * d[2] * d[3]; pc[2] += r * d[2] * d[4]; }
+                if (cmodel != ORC_GRAY) {
+                    pc[3] += r * d[3] * d[3]; pc[4] += r * d[3] * d[4]; pc[5] += r * d[4] * d[4];
+                }
             }
         for (c = 0; c < 3; ++c) ps[c] /= Wk;
         for (c = 0; c < 6; ++c) pc[c] /= Wk;
         if (cs_raw) memcpy(cs_raw + 3 * k, ps, sizeof(double) * 3);
         if (cc_raw) memcpy(cc_raw + 6 * k, pc, sizeof(double) * 6);
+        if (cmodel == ORC_GRAY) m[3] = m[4] = 0.0;
         for (c = 0; c < 5; ++c) mu[5 * k + c] = m[c];
         rs += orc_eig_clamp(2, ps, eps_s, cs + 3 * k);
-        rc += orc_eig_clamp(3, pc, eps_c, cc + 6 * k);
+        if (cmodel == ORC_FULL) {
+            rc += orc_eig_clamp(3, pc, eps_c, cc + 6 * k);
+        } else {
+            double ab[3] = {pc[3], pc[4], pc[5]}, ab_out[3] = {0.0, 0.0, 0.0};
+            memset(cc + 6 * k, 0, sizeof(double) * 6);
+            rc += orc_eig_clamp(1, pc, eps_c, cc + 6 * k);
+            if (cmodel == ORC_SPLIT) {
+                rc += orc_eig_clamp(2, ab, eps_c, ab_out);
+                cc[6 * k + 3] = ab_out[0]; cc[6 * k + 4] = ab_out[1]; cc[6 * k + 5] = ab_out[2];
+            }
+        }
     }
     if (nraised) { nraised[0] = rs; nraised[1] = rc; }
     return dead;
@@ -551,7 +611,8 @@ void orc_labels(long N, const int32_t *cand, const int32_t *ncand, const double 
 }
 
 /* ------------------------------------------------------------------------
- * Algorithm 1, steps 1-7, for T iterations, on a CIELAB image.
+ * Algorithm 1, steps 1-7, for T iterations, on a CIELAB image, for the
+ * colour model cmodel (grayscale reads only the L column of lab).
  *   step 1   initialise theta (Sec. III-C)
  *   step 2   R from theta_0
  *   loop T:  steps 4-5 (M-step with the floor), step 6 (R from theta_{t+1})
@@ -569,7 +630,7 @@ int orc_em(const double *lab, int W, int H, int K_req, int spacing, int T,
            double lambda_c, double eps_s, double eps_c,
            const double *mu_in, const double *cs_in, const double *cc_in,
            double *mu, double *cs, double *cc, int32_t *labels, double *margin,
-           double *loglik, double *post, int32_t *cand_out, int32_t *ncand_out, int *raised)
+           double *loglik, double *post, int32_t *cand_out, int32_t *ncand_out, int *raised, int cmodel)
 {
     int g[4], v, nx, ny, K, t, dead = 0;
     long N = (long)W * H;
@@ -587,19 +648,19 @@ int orc_em(const double *lab, int W, int H, int K_req, int spacing, int T,
         memcpy(cs, cs_in, sizeof(double) * 3 * K);
         memcpy(cc, cc_in, sizeof(double) * 6 * K);
     } else {
-        orc_init(lab, W, H, v, nx, ny, lambda_c, mu, cs, cc);
+        orc_init(lab, W, H, v, nx, ny, lambda_c, mu, cs, cc, cmodel);
     }
     {
-        double L0 = orc_estep(lab, W, H, K, cand, ncand, mu, cs, cc, R, NULL);
+        double L0 = orc_estep(lab, W, H, K, cand, ncand, mu, cs, cc, R, NULL, cmodel);
         if (loglik) loglik[0] = L0;
     }
     for (t = 0; t < T; ++t) {
         int nr[2];
         double Lt;
         dead += orc_mstep(lab, W, H, v, nx, ny, cand, ncand, R, eps_s, eps_c, mu, cs, cc,
-                          NULL, NULL, NULL, nr);
+                          NULL, NULL, NULL, nr, cmodel);
         if (raised) { raised[2 * t] = nr[0]; raised[2 * t + 1] = nr[1]; }
-        Lt = orc_estep(lab, W, H, K, cand, ncand, mu, cs, cc, R, NULL);
+        Lt = orc_estep(lab, W, H, K, cand, ncand, mu, cs, cc, R, NULL, cmodel);
         if (loglik) loglik[t + 1] = Lt;
     }
     orc_labels(N, cand, ncand, R, labels, margin);
