@@ -50,7 +50,19 @@ typedef enum {
 /* Image formats accepted by gmmsp_init / gmmsp_reinit. */
 enum {
     GMMSP_RGB8 = 0,   /* H rows of W x (R,G,B) uint8 sRGB, row pitch in bytes   */
-    GMMSP_LAB32 = 1   /* H rows of W x (L,a,b) float32 CIELAB, row pitch in bytes */
+    GMMSP_LAB32 = 1,  /* H rows of W x (L,a,b) float32 CIELAB, row pitch in bytes */
+    GMMSP_GRAY8 = 2   /* H rows of W uint8 grey levels (sRGB-encoded luminance),
+                         row pitch in bytes; only with GMMSP_COLOUR_GRAY       */
+};
+
+/* Colour covariance model (Sec. III-A, III-C). */
+enum {
+    GMMSP_COLOUR_FULL = 0,  /* Sigma_c a full 3x3 over (L, a, b), Eq. (BlockSigma)  */
+    GMMSP_COLOUR_SPLIT = 1, /* Sigma_c = diag(sigma_l^2, Sigma_(a,b)), Eq. (BlockSigma1):
+                               no L-(a, b) covariance, a cheaper E- and M-step     */
+    GMMSP_COLOUR_GRAY = 2   /* grayscale: the colour is the scalar CIE L* (of the L
+                               channel of a colour input, or of a grey level), so
+                               z = (x, y, L) and Sigma_c = sigma^2                  */
 };
 
 /* Arithmetic of the EM loop. */
@@ -69,12 +81,21 @@ typedef struct {
     float eps_c;        /* colour eigenvalue floor, CIELAB^2 (Sec. IV-A: 8)     */
     float lambda_c;     /* initial colour standard deviation; Sigma_c,0 =
                            lambda_c^2 I (Sec. III-C; Sec. IV-A uses 8)          */
-    int input_format;   /* GMMSP_RGB8 or GMMSP_LAB32                          */
-    int precision;      /* GMMSP_PREC_MIXED or GMMSP_PREC_FP32                 */
+    int input_format;   /* GMMSP_RGB8, GMMSP_LAB32 or GMMSP_GRAY8              */
+    int precision;      /* GMMSP_PREC_MIXED or GMMSP_PREC_FP32 (FULL model only) */
+    int colour_model;   /* GMMSP_COLOUR_FULL, _SPLIT or _GRAY.  The split and
+                           grayscale models are mixed precision only, and the
+                           learned initialiser, the training targets and the
+                           allocation-free entry point take the full model
+                           only (GMMSP_E_INVALID otherwise).  Parameters come
+                           out in the full layout: the split model's L-a, L-b
+                           covariances are 0; grayscale has mu's a, b and
+                           every Sigma_c entry but LL at 0.                    */
 } gmmsp_params;
 
 /* Fills p with the paper's settings: spacing 0, K 0 (the caller sets one of
- * them), eps_s 2, eps_c 8, lambda_c 8, RGB8, mixed precision. */
+ * them), eps_s 2, eps_c 8, lambda_c 8, RGB8, mixed precision, full colour
+ * covariance. */
 void gmmsp_default_params(gmmsp_params *p);
 
 /*
@@ -83,13 +104,15 @@ void gmmsp_default_params(gmmsp_params *p);
  * (Sec. III-C: mu_k = z at the centre pixel of cell k, Sigma_s =
  * diag(v^2, v^2), Sigma_c = lambda_c^2 I).
  *   image_dev    device pointer to the first row (see GMMSP_RGB8/LAB32);
- *   pitch_bytes  distance between rows in bytes, >= 3 W (RGB8) or 12 W (LAB32);
+ *   pitch_bytes  distance between rows in bytes, >= 3 W (RGB8), 12 W (LAB32)
+ *                or W (GRAY8);
  *   stream       cudaStream_t to queue work on (NULL = legacy default stream).
  * Allocates the context's device buffers (O(W H) bytes for the CIELAB image,
  * O(K) for theta and the per-cell partial sums).  Errors: GMMSP_E_INVALID
  * when W, H < 1, when neither spacing nor K is positive, when the grid is
- * empty (n_x or n_y = 0), when eps or lambda_c is not positive, or for an
- * unknown format; GMMSP_E_NOMEM; GMMSP_E_CUDA.  On error *out is NULL.
+ * empty (n_x or n_y = 0), when eps or lambda_c is not positive, for an
+ * unknown format or colour model, or an unsupported combination of them
+ * (see gmmsp_params); GMMSP_E_NOMEM; GMMSP_E_CUDA.  On error *out is NULL.
  */
 gmmsp_status gmmsp_init(gmmsp_ctx *out, const void *image_dev, int width, int height,
                         int pitch_bytes, const gmmsp_params *p, void *stream);
@@ -275,7 +298,8 @@ void gmmsp_batch_destroy(gmmsp_batch b);
  *   lab_dev      device rows of W x (L, a, b) float32, 4-byte aligned;
  *   pitch_bytes  row pitch, >= 12 W, a multiple of 4;
  *   p            spacing or K, eps_s, eps_c, lambda_c as for gmmsp_init
- *                (input_format is ignored; precision must be MIXED);
+ *                (input_format is ignored; precision must be MIXED and
+ *                colour_model FULL);
  *   labels_dev   device int32[W H], written (argmax posterior, Eq. obtLi);
  *   stream       cudaStream_t to queue on; the call does not synchronise;
  *   err          NULL, or err_len bytes receiving a message on failure.

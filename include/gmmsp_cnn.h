@@ -117,16 +117,17 @@ void gmmsp_net_destroy(gmmsp_net n);
  * gmmsp_init_from_net: replaces theta of a single-image context by the
  *   network's theta_0 for the context's current image (after gmmsp_init or
  *   gmmsp_reinit); the spacing must match.  Then gmmsp_em_iters /
- *   gmmsp_labels as usual.
+ *   gmmsp_labels as usual.  The context must use GMMSP_COLOUR_FULL
+ *   (GMMSP_E_INVALID otherwise, the context stays usable).
  * gmmsp_batch_set_init_net: every later gmmsp_batch_segment on b starts from
  *   the network's theta_0 instead of Sec. III-C (n = NULL restores it).  All
- *   images of b must have one size and b the network's spacing.  The network
- *   must outlive its use by b.
+ *   images of b must have one size and b the network's spacing and the full
+ *   colour model.  The network must outlive its use by b.
  * gmmsp_batch_lab: device pointer to b's CIELAB planes (valid until b is
  *   destroyed; filled by gmmsp_batch_segment).
  * gmmsp_batch_targets: training targets (B K x 10 float32, layout of the
  *   network outputs) from b's current theta, e.g. after many EM iterations.
- *   All images of b must have one size. */
+ *   All images of b must have one size; the full colour model only. */
 gmmsp_status gmmsp_init_from_net(gmmsp_ctx c, gmmsp_net n);
 gmmsp_status gmmsp_batch_set_init_net(gmmsp_batch b, gmmsp_net n);
 gmmsp_status gmmsp_batch_lab(gmmsp_batch b, const float **lab_dev);

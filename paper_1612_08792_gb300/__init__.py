@@ -34,10 +34,21 @@ __all__ = [
     "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
     "GMMSP_OK", "GMMSP_E_INVALID", "GMMSP_E_CUDA", "GMMSP_E_NOMEM", "GMMSP_E_NUMERIC", "GMMSP_E_TIMEOUT",
     "GMMSP_E_STATE", "gmmsp_segmentation_metrics", "gmmsp_enforce_connectivity", "gmmsp_connectivity",
-    "gmmsp_batch_connectivity",
+    "gmmsp_batch_connectivity", "GMMSP_GRAY8", "GMMSP_COLOUR_FULL", "GMMSP_COLOUR_SPLIT", "GMMSP_COLOUR_GRAY",
 ]
 
-GMMSP_RGB8, GMMSP_LAB32 = 0, 1
+GMMSP_RGB8, GMMSP_LAB32, GMMSP_GRAY8 = 0, 1, 2
+GMMSP_COLOUR_FULL, GMMSP_COLOUR_SPLIT, GMMSP_COLOUR_GRAY = 0, 1, 2
+_COLOUR = {"full": GMMSP_COLOUR_FULL, "split": GMMSP_COLOUR_SPLIT, "gray": GMMSP_COLOUR_GRAY}
+
+
+def colour_model(colour) -> int:
+    """GMMSP_COLOUR_* from a name ("full", "split", "gray") or the constant itself."""
+    c = _COLOUR.get(colour, None) if isinstance(colour, str) else int(colour)
+    if c not in (GMMSP_COLOUR_FULL, GMMSP_COLOUR_SPLIT, GMMSP_COLOUR_GRAY):
+        raise ValueError(f"unknown colour model {colour!r}")
+    return c
+
 GMMSP_PREC_MIXED, GMMSP_PREC_FP32 = 0, 1
 GMMSP_OK, GMMSP_E_INVALID, GMMSP_E_CUDA, GMMSP_E_NOMEM, GMMSP_E_NUMERIC, GMMSP_E_TIMEOUT, GMMSP_E_STATE = range(7)
 STATUS = {0: "GMMSP_OK", 1: "GMMSP_E_INVALID", 2: "GMMSP_E_CUDA", 3: "GMMSP_E_NOMEM",
@@ -62,7 +73,7 @@ class gmmsp_params(ctypes.Structure):
     """Mirror of the C struct ``gmmsp_params`` (include/gmmsp.h)."""
     _fields_ = [("spacing", ctypes.c_int), ("K", ctypes.c_int), ("eps_s", ctypes.c_float),
                 ("eps_c", ctypes.c_float), ("lambda_c", ctypes.c_float),
-                ("input_format", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("input_format", ctypes.c_int), ("precision", ctypes.c_int), ("colour_model", ctypes.c_int)]
 
 
 def load_library(path: str | None = None):
@@ -587,16 +598,18 @@ def gmmsp_batch_connectivity(b, labels):
 
 
 class SuperpixelsBatch:
-    """A batch context over lists of (H, W, 3) uint8 RGB (or float32 CIELAB) CUDA tensors."""
+    """A batch context over lists of (H, W, 3) uint8 RGB (or float32 CIELAB, or (H, W)
+    uint8 grey-level with gray_input) CUDA tensors.  colour: "full", "split" or "gray"."""
 
     def __init__(self, shapes, K: int = 0, spacing: int = 0, eps_s: float = 2.0, eps_c: float = 8.0,
                  lambda_c: float = 8.0, precision: int = GMMSP_PREC_MIXED, lab_input: bool = False,
-                 stream=None):
+                 stream=None, colour="full", gray_input: bool = False):
         import torch
         p = gmmsp_default_params()
         p.spacing, p.K, p.eps_s, p.eps_c, p.lambda_c = int(spacing), int(K), eps_s, eps_c, lambda_c
-        p.input_format = GMMSP_LAB32 if lab_input else GMMSP_RGB8
+        p.input_format = GMMSP_GRAY8 if gray_input else (GMMSP_LAB32 if lab_input else GMMSP_RGB8)
         p.precision = int(precision)
+        p.colour_model = colour_model(colour)
         self.shapes = [(int(h), int(w)) for (h, w) in shapes]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.b = gmmsp_batch_create([w for _, w in self.shapes], [h for h, _ in self.shapes], p, self.stream)
@@ -677,14 +690,17 @@ class Grid:
 
 
 class Superpixels:
-    """One library context over (H, W, 3) uint8 RGB or float32 CIELAB CUDA tensors."""
+    """One library context over (H, W, 3) uint8 RGB or float32 CIELAB CUDA tensors, or
+    (H, W) uint8 grey levels (grayscale colour model).  colour: "full", "split" or "gray"."""
 
     def __init__(self, image, K: int = 0, spacing: int = 0, eps_s: float = 2.0, eps_c: float = 8.0,
-                 lambda_c: float = 8.0, precision: int = GMMSP_PREC_MIXED, stream=None):
+                 lambda_c: float = 8.0, precision: int = GMMSP_PREC_MIXED, stream=None, colour="full"):
         import torch
-        if image.dim() != 3 or image.shape[2] != 3:
-            raise ValueError("image must be (H, W, 3)")
-        if image.dtype == torch.uint8:
+        if image.dim() == 2 and image.dtype == torch.uint8:
+            fmt = GMMSP_GRAY8
+        elif image.dim() != 3 or image.shape[2] != 3:
+            raise ValueError("image must be (H, W, 3), or (H, W) uint8 grey levels")
+        elif image.dtype == torch.uint8:
             fmt = GMMSP_RGB8
         elif image.dtype == torch.float32:
             fmt = GMMSP_LAB32
@@ -693,6 +709,7 @@ class Superpixels:
         p = gmmsp_default_params()
         p.spacing, p.K, p.eps_s, p.eps_c, p.lambda_c = int(spacing), int(K), eps_s, eps_c, lambda_c
         p.input_format, p.precision = fmt, int(precision)
+        p.colour_model = colour_model(colour)
         self.H, self.W = int(image.shape[0]), int(image.shape[1])
         self.format = fmt
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -701,7 +718,10 @@ class Superpixels:
 
     @staticmethod
     def _pitch(image) -> int:
-        if image.stride(2) != 1 or image.stride(1) != 3:
+        if image.dim() == 2:
+            if image.stride(1) != 1:
+                raise ValueError("grey-level rows must be packed (stride (pitch, 1))")
+        elif image.stride(2) != 1 or image.stride(1) != 3:
             raise ValueError("image rows must be packed (stride (pitch, 3, 1))")
         return int(image.stride(0) * image.element_size())
 

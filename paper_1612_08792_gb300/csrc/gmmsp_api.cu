@@ -178,6 +178,11 @@ gmmsp_status mark(gmmsp_ctx c) {
     if (s_ != GMMSP_OK) return s_;          \
   } while (0)
 
+// Smallest row pitch of a W-pixel row of the input format.
+long long row_bytes(int format, int W) {
+  return (long long)W * (format == GMMSP_RGB8 ? 3 : (format == GMMSP_GRAY8 ? 1 : 12));
+}
+
 // Enqueues step 1 of Algorithm 1: image -> CIELAB, theta_0; clears counters.
 gmmsp_status enqueue_prepare(gmmsp_ctx c, const void* image, int pitch) {
   const Geom& g = c->g;
@@ -186,6 +191,8 @@ gmmsp_status enqueue_prepare(gmmsp_ctx c, const void* image, int pitch) {
   if (c->p.input_format == GMMSP_RGB8)
     GM_CHECK(c, gmmsp::launch_rgb2lab(static_cast<const uint8_t*>(image), pitch, g, c->lab, c->counters,
                                       c->stream));
+  else if (c->p.input_format == GMMSP_GRAY8)
+    GM_CHECK(c, gmmsp::launch_gray2l(static_cast<const uint8_t*>(image), pitch, g, c->lab, c->stream));
   else
     GM_CHECK(c, gmmsp::launch_lab32(static_cast<const float*>(image), pitch, g, c->lab, c->counters,
                                     c->stream));
@@ -254,6 +261,7 @@ void gmmsp_default_params(gmmsp_params* p) {
   p->lambda_c = 8.0f;
   p->input_format = GMMSP_RGB8;
   p->precision = GMMSP_PREC_MIXED;
+  p->colour_model = GMMSP_COLOUR_FULL;
 }
 
 const char* gmmsp_status_string(gmmsp_status s) {
@@ -276,10 +284,13 @@ gmmsp_status gmmsp_init(gmmsp_ctx* out, const void* image_dev, int width, int he
   if (!out) return GMMSP_E_INVALID;
   *out = nullptr;
   if (!p || !image_dev || width < 1 || height < 1) return GMMSP_E_INVALID;
-  if (p->input_format != GMMSP_RGB8 && p->input_format != GMMSP_LAB32) return GMMSP_E_INVALID;
+  if (p->input_format != GMMSP_RGB8 && p->input_format != GMMSP_LAB32 && p->input_format != GMMSP_GRAY8)
+    return GMMSP_E_INVALID;
   if (p->precision != GMMSP_PREC_MIXED && p->precision != GMMSP_PREC_FP32) return GMMSP_E_INVALID;
-  const long long min_pitch = (long long)width * (p->input_format == GMMSP_RGB8 ? 3 : 12);
-  if (pitch_bytes < min_pitch) return GMMSP_E_INVALID;
+  if (p->colour_model < GMMSP_COLOUR_FULL || p->colour_model > GMMSP_COLOUR_GRAY) return GMMSP_E_INVALID;
+  if (p->colour_model != GMMSP_COLOUR_FULL && p->precision != GMMSP_PREC_MIXED) return GMMSP_E_INVALID;
+  if (p->input_format == GMMSP_GRAY8 && p->colour_model != GMMSP_COLOUR_GRAY) return GMMSP_E_INVALID;
+  if (pitch_bytes < row_bytes(p->input_format, width)) return GMMSP_E_INVALID;
   if (p->input_format == GMMSP_LAB32 && (pitch_bytes % 4 != 0 || (uintptr_t)image_dev % 4 != 0))
     return GMMSP_E_INVALID;
   if (!(p->eps_s > 0.f) || !(p->eps_c > 0.f) || !(p->lambda_c > 0.f) || !isfinite(p->eps_s) ||
@@ -288,6 +299,7 @@ gmmsp_status gmmsp_init(gmmsp_ctx* out, const void* image_dev, int width, int he
   if (p->spacing <= 0 && p->K <= 0) return GMMSP_E_INVALID;
   Geom g;
   if (!make_geom(width, height, p->K, p->spacing, &g)) return GMMSP_E_INVALID;
+  g.cm = p->colour_model;
 
   gmmsp_ctx c = new (std::nothrow) gmmsp_ctx_s();
   if (!c) return GMMSP_E_NOMEM;
@@ -345,8 +357,7 @@ gmmsp_status gmmsp_init(gmmsp_ctx* out, const void* image_dev, int width, int he
 gmmsp_status gmmsp_reinit(gmmsp_ctx c, const void* image_dev, int pitch_bytes) {
   if (!c) return GMMSP_E_INVALID;
   if (!image_dev) return fail(c, GMMSP_E_INVALID, "null image");
-  const long long min_pitch = (long long)c->g.W * (c->p.input_format == GMMSP_RGB8 ? 3 : 12);
-  if (pitch_bytes < min_pitch) return fail(c, GMMSP_E_INVALID, "pitch too small");
+  if (pitch_bytes < row_bytes(c->p.input_format, c->g.W)) return fail(c, GMMSP_E_INVALID, "pitch too small");
   if (c->state == GMMSP_E_CUDA || c->state == GMMSP_E_NOMEM) return GMMSP_E_STATE;
   c->state = GMMSP_OK;
   c->err.clear();
@@ -393,8 +404,7 @@ gmmsp_status gmmsp_segment(gmmsp_ctx c, const void* image_dev, int pitch_bytes, 
   if (!c) return GMMSP_E_INVALID;
   if (!image_dev || !labels_dev) return fail(c, GMMSP_E_INVALID, "null image or labels");
   if (iters < 0 || iters + 1 > kLlkCap) return fail(c, GMMSP_E_INVALID, "iters out of range");
-  const long long min_pitch = (long long)c->g.W * (c->p.input_format == GMMSP_RGB8 ? 3 : 12);
-  if (pitch_bytes < min_pitch) return fail(c, GMMSP_E_INVALID, "pitch too small");
+  if (pitch_bytes < row_bytes(c->p.input_format, c->g.W)) return fail(c, GMMSP_E_INVALID, "pitch too small");
   if (c->state == GMMSP_E_CUDA || c->state == GMMSP_E_NOMEM) return GMMSP_E_STATE;
   c->state = GMMSP_OK;
   c->err.clear();
@@ -529,6 +539,10 @@ gmmsp_status gmmsp_init_from_net(gmmsp_ctx c, gmmsp_net n) {
   gmmsp_status st = check_ready(c);
   if (st != GMMSP_OK) return st;
   if (!n) return fail(c, GMMSP_E_INVALID, "null network");
+  if (c->g.cm != gmmsp::kColourFull) {
+    c->err = "a learned start needs the full colour model";  // the context stays usable
+    return GMMSP_E_INVALID;
+  }
   std::string why;
   st = gmmsp::net_reserve(n, 1, c->g, &why);
   if (st != GMMSP_OK) {

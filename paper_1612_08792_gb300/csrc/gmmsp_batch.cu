@@ -106,6 +106,11 @@ bool geom_of(int W, int H, int K_req, int spacing, Geom* g) {
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The 16-lane finalize exists for the mixed-precision full colour model only.
+bool use_fin16(gmmsp_batch b) {
+  return b->fin16 && b->p.precision != GMMSP_PREC_FP32 && b->p.colour_model == GMMSP_COLOUR_FULL;
+}
+
 int em_blocks(gmmsp_batch b) {
   const long long need = (b->total_cells + 3) / 4;
   const long long cap = (long long)b->sm_count * b->blocks_per_sm;
@@ -131,22 +136,22 @@ gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
   const int fblocks = int(std::min<long long>((b->total_k + 31) / 32, (long long)b->sm_count * 16));
   for (int t = 0; t < iters; ++t) {
     GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, n, b->total_cells, b->lab, b->gp, b->partials,
-                                            b->p.precision, eb, b->blocks_per_sm, s));
+                                            b->p.precision, eb, b->blocks_per_sm, b->p.colour_model, s));
     GB_CHECK(b, gmmsp::launch_finalize_batch(b->table, n, b->total_k, b->partials, b->theta, b->gp,
                                              b->p.eps_s, b->p.eps_c, b->counters, b->p.precision,
-                                             b->fin16 ? 0 : fblocks, s));
+                                             use_fin16(b) ? 0 : fblocks, s));
   }
   const long long lneed = (b->total_cells + 3) / 4;
   const int lb = int(std::min<long long>(lneed, (long long)b->sm_count * b->label_blocks_per_sm));
   GB_CHECK(b, gmmsp::launch_label_pass_batch(b->table, n, b->total_cells, b->lab, b->gp,
-                                              want_ll ? b->cell_ll : nullptr, lb, s));
+                                              want_ll ? b->cell_ll : nullptr, lb, b->p.colour_model, s));
   if (want_ll) GB_CHECK(b, gmmsp::launch_ll_per_image(b->table, n, b->cell_ll, b->img_ll, s));
   return GMMSP_OK;
 }
 
 gmmsp_status upload_table(gmmsp_batch b, const void* const* images, const int* pitches,
                           int32_t* const* labels) {
-  const long long mult = b->p.input_format == GMMSP_RGB8 ? 3 : 12;
+  const long long mult = b->p.input_format == GMMSP_RGB8 ? 3 : (b->p.input_format == GMMSP_GRAY8 ? 1 : 12);
   for (int i = 0; i < b->n; ++i) {
     if (!images[i] || !labels[i]) return bfail(b, GMMSP_E_INVALID, "null image or label pointer");
     if (pitches[i] < mult * b->host[i].g.W) return bfail(b, GMMSP_E_INVALID, "pitch too small");
@@ -176,8 +181,12 @@ gmmsp_status gmmsp_batch_create(gmmsp_batch* out, int n, const int* widths, cons
   if (!out) return GMMSP_E_INVALID;
   *out = nullptr;
   if (n < 1 || !widths || !heights || !p) return GMMSP_E_INVALID;
-  if (p->input_format != GMMSP_RGB8 && p->input_format != GMMSP_LAB32) return GMMSP_E_INVALID;
+  if (p->input_format != GMMSP_RGB8 && p->input_format != GMMSP_LAB32 && p->input_format != GMMSP_GRAY8)
+    return GMMSP_E_INVALID;
   if (p->precision != GMMSP_PREC_MIXED && p->precision != GMMSP_PREC_FP32) return GMMSP_E_INVALID;
+  if (p->colour_model < GMMSP_COLOUR_FULL || p->colour_model > GMMSP_COLOUR_GRAY) return GMMSP_E_INVALID;
+  if (p->colour_model != GMMSP_COLOUR_FULL && p->precision != GMMSP_PREC_MIXED) return GMMSP_E_INVALID;
+  if (p->input_format == GMMSP_GRAY8 && p->colour_model != GMMSP_COLOUR_GRAY) return GMMSP_E_INVALID;
   if (!(p->eps_s > 0.f) || !(p->eps_c > 0.f) || !(p->lambda_c > 0.f)) return GMMSP_E_INVALID;
   if (p->spacing <= 0 && p->K <= 0) return GMMSP_E_INVALID;
   gmmsp_batch b = new (std::nothrow) gmmsp_batch_s();
@@ -195,6 +204,7 @@ gmmsp_status gmmsp_batch_create(gmmsp_batch* out, int n, const int* widths, cons
     }
     BatchImage& im = b->host[i];
     memset(&im, 0, sizeof(im));
+    g.cm = p->colour_model;
     im.g = g;
     im.pix_off = pix;
     im.row_off = int(rows);
@@ -248,6 +258,16 @@ gmmsp_status gmmsp_batch_create(gmmsp_batch* out, int n, const int* widths, cons
   b->img_ll = reinterpret_cast<double*>(base + o_ill);
   b->table = reinterpret_cast<BatchImage*>(base + o_tab);
   b->counters = reinterpret_cast<unsigned long long*>(base + o_cnt);
+  if (p->colour_model == GMMSP_COLOUR_GRAY) {
+    // the a, b planes stay zero: the conversion writes plane L only
+    e = cudaMemsetAsync(b->lab, 0, 3 * size_t(pix) * sizeof(float), b->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(b->slab);
+      delete b;
+      return GMMSP_E_CUDA;
+    }
+  }
   *out = b;
   return GMMSP_OK;
 }
@@ -255,7 +275,7 @@ gmmsp_status gmmsp_batch_create(gmmsp_batch* out, int n, const int* widths, cons
 gmmsp_status gmmsp_batch_get_tuning(gmmsp_batch b, int* blocks_per_sm, int* finalize16, double* finalize_ms) {
   if (!b) return GMMSP_E_INVALID;
   if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
-  if (finalize16) *finalize16 = (b->fin16 && b->p.precision != GMMSP_PREC_FP32) ? 1 : 0;
+  if (finalize16) *finalize16 = use_fin16(b) ? 1 : 0;
   if (finalize_ms) {
     finalize_ms[0] = b->fin_ms[0];
     finalize_ms[1] = b->fin_ms[1];
@@ -366,11 +386,13 @@ gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void* const* images_dev, 
     b->blocks_per_sm = cand[i];
     const int eb = em_blocks(b);
     GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, b->n, b->total_cells, b->lab, b->gp, b->partials,
-                                            b->p.precision, eb, b->blocks_per_sm, b->stream));  // warm-up
+                                            b->p.precision, eb, b->blocks_per_sm, b->p.colour_model,
+                                            b->stream));  // warm-up
     GB_CHECK(b, cudaEventRecord(e0, b->stream));
     for (int r = 0; r < reps; ++r)
       GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, b->n, b->total_cells, b->lab, b->gp, b->partials,
-                                              b->p.precision, eb, b->blocks_per_sm, b->stream));
+                                              b->p.precision, eb, b->blocks_per_sm, b->p.colour_model,
+                                              b->stream));
     GB_CHECK(b, cudaEventRecord(e1, b->stream));
     GB_CHECK(b, cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -380,7 +402,7 @@ gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void* const* images_dev, 
     if (per < best_ms) { best_ms = per; best_c = cand[i]; }
   }
   b->blocks_per_sm = best_c;
-  if (b->p.precision != GMMSP_PREC_FP32) {
+  if (b->p.precision != GMMSP_PREC_FP32 && b->p.colour_model == GMMSP_COLOUR_FULL) {
     // finalize: 16 lanes per superpixel against one thread per superpixel
     // (theta changes here; every segment starts again from theta_0)
     const int fblocks = int(std::min<long long>((b->total_k + 31) / 32, (long long)b->sm_count * 16));
@@ -417,6 +439,8 @@ gmmsp_status gmmsp_batch_set_init_net(gmmsp_batch b, gmmsp_net net) {
   if (!b) return GMMSP_E_INVALID;
   if (net) {
     if (!b->uniform) return bfail(b, GMMSP_E_INVALID, "a learned start needs images of one size");
+    if (b->p.colour_model != GMMSP_COLOUR_FULL)
+      return bfail(b, GMMSP_E_INVALID, "a learned start needs the full colour model");
     std::string why;
     const gmmsp_status st = gmmsp::net_reserve(net, b->n, b->host[0].g, &why);
     if (st != GMMSP_OK) return bfail(b, st == GMMSP_E_INVALID ? GMMSP_E_INVALID : st, why);
@@ -453,6 +477,7 @@ gmmsp_status gmmsp_batch_lab(gmmsp_batch b, const float** lab_dev) {
 gmmsp_status gmmsp_batch_targets(gmmsp_batch b, float* target_dev) {
   if (!b || !target_dev) return GMMSP_E_INVALID;
   if (!b->uniform) return bfail(b, GMMSP_E_INVALID, "targets need images of one size");
+  if (b->p.colour_model != GMMSP_COLOUR_FULL) return bfail(b, GMMSP_E_INVALID, "targets need the full colour model");
   GB_CHECK(b, gmmsp::launch_targets(b->theta, b->lab, b->n, b->host[0].g, b->p.lambda_c, target_dev, b->stream));
   return GMMSP_OK;
 }

@@ -26,7 +26,16 @@
 // coefficients (k_finalize_l16: 16 lanes per superpixel for small K;
 // k_finalize: one thread per superpixel for large K and the FP32 variant).
 // A superpixel with W < 1e-8 keeps its parameters.
+//
+// Colour models: the E+M and label kernels are compiled per model (template
+// CM): the split model of Eq. (BlockSigma1) drops the L-a and L-b terms of
+// the quadratic form and of the second moments (4 of 48 FP32 instructions
+// per pixel and candidate), grayscale keeps L alone (20 of 48) and reads one
+// plane instead of three.  The partial layout is the same for all models;
+// the entries a model does not form stay 0.
 #include <math.h>
+
+#include <type_traits>
 
 #include "gmmsp_internal.cuh"
 #include "gmmsp_math.cuh"
@@ -95,16 +104,27 @@ __device__ __forceinline__ void stage_params(const Geom& g, const Cell& c, const
 // log2 p(z; theta_k) for one candidate: the log normaliser plus the two
 // quadratic forms, with -1/2 log2(e) Sigma^{-1} folded into the coefficients.
 // fx, fy are the pixel's coordinates relative to the candidate's cell origin.
+template <int CM>
 __device__ __forceinline__ float log2_density(const float4* P, float fx, float fy, float4 z) {
   const float4 p0 = P[0], p1 = P[1], p2 = P[2], p3 = P[3];
   const float dx = fx - p0.x, dy = fy - p0.y;
-  const float dL = z.x - p0.z, da = z.y - p0.w, db = z.z - p1.x;
+  const float dL = z.x - p0.z;
   float q = p3.z;
   q = fmaf(fmaf(p1.z, dy, p1.y * dx), dx, q);       // (xx dx + 2xy dy) dx
   q = fmaf(p1.w * dy, dy, q);                        // yy dy^2
-  q = fmaf(fmaf(p3.x, db, fmaf(p2.w, da, p2.x * dL)), dL, q);  // (LL dL + 2La da + 2Lb db) dL
-  q = fmaf(fmaf(p3.y, db, p2.y * da), da, q);        // (aa da + 2ab db) da
-  q = fmaf(p2.z * db, db, q);                        // bb db^2
+  if constexpr (CM == kColourFull) {
+    const float da = z.y - p0.w, db = z.z - p1.x;
+    q = fmaf(fmaf(p3.x, db, fmaf(p2.w, da, p2.x * dL)), dL, q);  // (LL dL + 2La da + 2Lb db) dL
+    q = fmaf(fmaf(p3.y, db, p2.y * da), da, q);      // (aa da + 2ab db) da
+    q = fmaf(p2.z * db, db, q);                      // bb db^2
+  } else if constexpr (CM == kColourSplit) {
+    const float da = z.y - p0.w, db = z.z - p1.x;
+    q = fmaf(p2.x * dL, dL, q);                      // LL dL^2
+    q = fmaf(fmaf(p3.y, db, p2.y * da), da, q);      // (aa da + 2ab db) da
+    q = fmaf(p2.z * db, db, q);                      // bb db^2
+  } else {
+    q = fmaf(p2.x * dL, dL, q);                      // LL dL^2
+  }
   return q;
 }
 
@@ -117,7 +137,7 @@ __device__ __forceinline__ void rel_coords(int rx, int ry, int v, float (&fxs)[3
 
 // E part for one pixel: the posteriors of its candidates (Eq. Rik) into
 // R[0..8] (zero for slots off the grid) and ln-sum-exp in log2 units into ll.
-template <bool FULL>
+template <bool FULL, int CM>
 __device__ __forceinline__ void e_pixel(const float4* sp, unsigned mask, const float (&fxs)[3],
                                         const float (&fys)[3], float4 z, float (&R)[kSlots],
                                         float& ll) {
@@ -126,7 +146,7 @@ __device__ __forceinline__ void e_pixel(const float4* sp, unsigned mask, const f
   for (int s = 0; s < kSlots; ++s) {
     R[s] = 0.f;
     if (FULL || ((mask >> s) & 1u)) {
-      R[s] = log2_density(sp + 4 * s, fxs[s % 3], fys[s / 3], z);
+      R[s] = log2_density<CM>(sp + 4 * s, fxs[s % 3], fys[s / 3], z);
       m = fmaxf(m, R[s]);
     }
   }
@@ -173,7 +193,7 @@ struct EmSmem {
 template <int WPC>
 constexpr int em_smem_bytes() { return int(sizeof(EmSmem<WPC>)); }
 
-template <bool FULL, bool SHIFT, int WPC, class Src>
+template <bool FULL, bool SHIFT, int WPC, class Src, int CM>
 __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, const Cell& c,
                                              EmSmem<WPC>& sm, int slot, int warp, int lane, int wic,
                                              float (&acc)[kStats], float& ll) {
@@ -203,7 +223,7 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
   if (wic * 32 + lane < npx) {
     int rx0, ry0;
     locate(wic * 32 + lane, rx0, ry0);
-    zn = lab.load(c.x0 + rx0, c.y0 + ry0);
+    zn = load_z<CM>(lab, c.x0 + rx0, c.y0 + ry0);
   }
   for (int base = wic * 32; base < npx; base += 32 * WPC) {
     const int p = base + lane;
@@ -212,14 +232,14 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
     if (p + 32 * WPC < npx) {
       int rx1, ry1;
       locate(p + 32 * WPC, rx1, ry1);
-      zn = lab.load(c.x0 + rx1, c.y0 + ry1);
+      zn = load_z<CM>(lab, c.x0 + rx1, c.y0 + ry1);
     }
     int rx = 0, ry = 0;
     if (p < npx) {
       locate(p, rx, ry);
       float fxs[3], fys[3];
       rel_coords(rx, ry, g.v, fxs, fys);
-      e_pixel<FULL>(sp, c.mask, fxs, fys, z, R, ll);
+      e_pixel<FULL, CM>(sp, c.mask, fxs, fys, z, R, ll);
     } else {
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) R[s] = 0.f;
@@ -238,19 +258,26 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
         const float2 xy = XYw[q];
         const float4 zz = Zw[q];
         const float dx = xy.x + cx, dy = xy.y + cy;
-        const float dL = zz.x - mL, da = zz.y - ma, db = zz.z - mb;
-        const float rxd = r * dx, ryd = r * dy, rL = r * dL, ra = r * da, rb = r * db;
+        const float dL = zz.x - mL;
+        const float rxd = r * dx, ryd = r * dy, rL = r * dL;
         acc[0] += r;
-        acc[1] += rxd; acc[2] += ryd; acc[3] += rL; acc[4] += ra; acc[5] += rb;
+        acc[1] += rxd; acc[2] += ryd; acc[3] += rL;
         acc[6] = fmaf(rxd, dx, acc[6]);
         acc[7] = fmaf(rxd, dy, acc[7]);
         acc[8] = fmaf(ryd, dy, acc[8]);
         acc[9] = fmaf(rL, dL, acc[9]);
-        acc[10] = fmaf(rL, da, acc[10]);
-        acc[11] = fmaf(rL, db, acc[11]);
-        acc[12] = fmaf(ra, da, acc[12]);
-        acc[13] = fmaf(ra, db, acc[13]);
-        acc[14] = fmaf(rb, db, acc[14]);
+        if constexpr (CM != kColourGray) {
+          const float da = zz.y - ma, db = zz.z - mb;
+          const float ra = r * da, rb = r * db;
+          acc[4] += ra; acc[5] += rb;
+          if constexpr (CM == kColourFull) {
+            acc[10] = fmaf(rL, da, acc[10]);
+            acc[11] = fmaf(rL, db, acc[11]);
+          }
+          acc[12] = fmaf(ra, da, acc[12]);
+          acc[13] = fmaf(ra, db, acc[13]);
+          acc[14] = fmaf(rb, db, acc[14]);
+        }
       };
       const int np = min(32, npx - base);
       if (np == 32) {
@@ -269,7 +296,7 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
 
 // One cell of the fused pass, run by the WPC warps of cell slot `slot` of the
 // block (all threads of the block call it together when WPC > 1).
-template <typename PT, bool SHIFT, int WPC, class Src>
+template <typename PT, bool SHIFT, int WPC, class Src, int CM>
 __device__ __forceinline__ void em_cell_block(const Src& lab, const Geom& g, const float* __restrict__ gp,
                                               PT* __restrict__ partials, int cell, bool active,
                                               EmSmem<WPC>& sm, int warp, int lane, int slot, int wic,
@@ -295,9 +322,9 @@ __device__ __forceinline__ void em_cell_block(const Src& lab, const Geom& g, con
   float ll = 0.f;
   if (active) {
     if (c.mask == 0x1ffu)
-      em_cell_warp<true, SHIFT, WPC, Src>(lab, g, c, sm, slot, warp, lane, wic, acc, ll);
+      em_cell_warp<true, SHIFT, WPC, Src, CM>(lab, g, c, sm, slot, warp, lane, wic, acc, ll);
     else
-      em_cell_warp<false, SHIFT, WPC, Src>(lab, g, c, sm, slot, warp, lane, wic, acc, ll);
+      em_cell_warp<false, SHIFT, WPC, Src, CM>(lab, g, c, sm, slot, warp, lane, wic, acc, ll);
   }
   // Per-warp totals: add the three lanes of each slot, and the lanes' log-likelihoods.
 #pragma unroll
@@ -327,7 +354,7 @@ __device__ __forceinline__ void em_cell_block(const Src& lab, const Geom& g, con
   if (WPC == 1) __syncwarp(); else __syncthreads();  // the slot's buffers are reused next
 }
 
-template <typename PT, bool SHIFT, int WPC, class Src>
+template <typename PT, bool SHIFT, int WPC, class Src, int CM>
 __global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(Src lab, Geom g, const float* __restrict__ gp,
                                                            PT* __restrict__ partials) {
   constexpr int kCellsPerBlock = kEmWarps / WPC;
@@ -341,7 +368,7 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_em_pass(Src lab, Geom g, cons
   const bool active = cell < g.ncells;  // inactive threads still reach every barrier
   pdl_wait();  // gp and the image are written by the preceding kernels
   pdl_trigger();
-  em_cell_block<PT, SHIFT, WPC, Src>(lab, g, gp, partials, cell, active, sm, warp, lane, slot, wic, t);
+  em_cell_block<PT, SHIFT, WPC, Src, CM>(lab, g, gp, partials, cell, active, sm, warp, lane, slot, wic, t);
 }
 
 // ---------------------------------------------------------------- batches
@@ -365,7 +392,7 @@ __device__ __forceinline__ int find_image(const BatchImage* __restrict__ imgs, i
 
 // MINB caps the registers so that MINB blocks fit on an SM (5: at most 102
 // registers, no spills).
-template <typename PT, bool SHIFT, int MINB>
+template <typename PT, bool SHIFT, int MINB, int CM>
 __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch(const BatchImage* __restrict__ imgs, int n,
                                                                        int total_cells, const float* __restrict__ lab,
                                                                        const float* __restrict__ gp,
@@ -376,9 +403,9 @@ __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch(const Bat
   for (int cell = blockIdx.x * kEmWarps + warp; cell < total_cells; cell += gridDim.x * kEmWarps) {
     const BatchImage& im = imgs[find_image(imgs, n, cell, 0)];
     const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
-    em_cell_block<PT, SHIFT, 1, LabPlanar>(src, im.g, gp + (long long)im.k_off * kGP,
-                                           partials + (long long)im.cell_off * kPartStride,
-                                           cell - im.cell_off, true, sm, warp, lane, warp, 0, lane);
+    em_cell_block<PT, SHIFT, 1, LabPlanar, CM>(src, im.g, gp + (long long)im.k_off * kGP,
+                                               partials + (long long)im.cell_off * kPartStride,
+                                               cell - im.cell_off, true, sm, warp, lane, warp, 0, lane);
   }
 }
 
@@ -386,7 +413,7 @@ __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch(const Bat
 // registers capped so that MINB blocks fit on an SM (6: 80 registers and 8
 // bytes of spill; 7: 72 registers and some spill); the autotuner's choice of
 // 6 or 7 blocks per SM selects it.
-template <typename PT, bool SHIFT, int MINB>
+template <typename PT, bool SHIFT, int MINB, int CM>
 __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch_flat(const BatchImage* __restrict__ imgs, int n,
                                                                       int total_cells,
                                                                       const float* __restrict__ lab,
@@ -399,9 +426,9 @@ __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch_flat(cons
   if (cell >= total_cells) return;  // whole warps only; a warp works alone on its cell
   const BatchImage& im = imgs[find_image(imgs, n, cell, 0)];
   const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
-  em_cell_block<PT, SHIFT, 1, LabPlanar>(src, im.g, gp + (long long)im.k_off * kGP,
-                                         partials + (long long)im.cell_off * kPartStride, cell - im.cell_off, true,
-                                         sm, warp, lane, warp, 0, lane);
+  em_cell_block<PT, SHIFT, 1, LabPlanar, CM>(src, im.g, gp + (long long)im.k_off * kGP,
+                                             partials + (long long)im.cell_off * kPartStride, cell - im.cell_off,
+                                             true, sm, warp, lane, warp, 0, lane);
 }
 
 // Label pass: argmax posterior per pixel (ties to the smaller k, i.e. the
@@ -413,7 +440,7 @@ constexpr int kLabelPPL = 2;
 
 // LL = false: argmax only (no log-sum-exp), for callers that want no
 // log-likelihood.
-template <bool FULL, bool LL, class Src>
+template <bool FULL, bool LL, class Src, int CM>
 __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
                                                   const Cell& c, const float4* sp, int lane,
                                                   int32_t* __restrict__ labels, float& ll) {
@@ -431,7 +458,7 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
     if (p < npx) {
       int rx, ry;
       locate(p, rx, ry);
-      zn[j] = lab.load(c.x0 + rx, c.y0 + ry);
+      zn[j] = load_z<CM>(lab, c.x0 + rx, c.y0 + ry);
     }
   }
   for (int p0 = lane; p0 - lane < npx; p0 += 32 * kLabelPPL) {
@@ -445,7 +472,7 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
       if (pn < npx) {
         int x1, y1;
         locate(pn, x1, y1);
-        zn[j] = lab.load(c.x0 + x1, c.y0 + y1);
+        zn[j] = load_z<CM>(lab, c.x0 + x1, c.y0 + y1);
       }
       locate(p0 + 32 * j, rx[j], ry[j]);
       rel_coords(rx[j], ry[j], g.v, fxs[j], fys[j]);
@@ -463,7 +490,7 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
       if (FULL || ((c.mask >> s) & 1u)) {
 #pragma unroll
         for (int j = 0; j < kLabelPPL; ++j) {
-          e[j][s] = log2_density(sp + 4 * s, fxs[j][s % 3], fys[j][s / 3], z[j]);
+          e[j][s] = log2_density<CM>(sp + 4 * s, fxs[j][s % 3], fys[j][s / 3], z[j]);
           if (e[j][s] > m[j]) { m[j] = e[j][s]; best[j] = s; }
         }
       } else {
@@ -488,7 +515,7 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
 }
 
 // One cell of the label pass, run by one warp.
-template <class Src>
+template <class Src, int CM>
 __device__ __forceinline__ void label_cell_warp(const Src& lab, const Geom& g, const float* __restrict__ gp,
                                                 int32_t* __restrict__ labels, double* __restrict__ cell_ll,
                                                 int cell, float4* sp, int lane) {
@@ -497,21 +524,21 @@ __device__ __forceinline__ void label_cell_warp(const Src& lab, const Geom& g, c
   float ll = 0.f;
   if (!cell_ll) {  // labels only
     if (c.mask == 0x1ffu)
-      label_cell_pixels<true, false, Src>(lab, g, c, sp, lane, labels, ll);
+      label_cell_pixels<true, false, Src, CM>(lab, g, c, sp, lane, labels, ll);
     else
-      label_cell_pixels<false, false, Src>(lab, g, c, sp, lane, labels, ll);
+      label_cell_pixels<false, false, Src, CM>(lab, g, c, sp, lane, labels, ll);
     return;
   }
   if (c.mask == 0x1ffu)
-    label_cell_pixels<true, true, Src>(lab, g, c, sp, lane, labels, ll);
+    label_cell_pixels<true, true, Src, CM>(lab, g, c, sp, lane, labels, ll);
   else
-    label_cell_pixels<false, true, Src>(lab, g, c, sp, lane, labels, ll);
+    label_cell_pixels<false, true, Src, CM>(lab, g, c, sp, lane, labels, ll);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
   if (lane == 0) cell_ll[cell] = double(ll) * 0.69314718055994530942;
 }
 
-template <class Src>
+template <class Src, int CM>
 __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass(Src lab, Geom g, const float* __restrict__ gp,
                                                               int32_t* __restrict__ labels,
                                                               double* __restrict__ cell_ll) {
@@ -521,9 +548,10 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass(Src lab, Geom g, c
   pdl_wait();
   pdl_trigger();
   if (cell >= g.ncells) return;
-  label_cell_warp<Src>(lab, g, gp, labels, cell_ll, cell, sp_all[warp], lane);
+  label_cell_warp<Src, CM>(lab, g, gp, labels, cell_ll, cell, sp_all[warp], lane);
 }
 
+template <int CM>
 __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass_batch(const BatchImage* __restrict__ imgs, int n,
                                                                     int total_cells,
                                                                     const float* __restrict__ lab,
@@ -534,8 +562,9 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass_batch(const BatchI
   for (int cell = blockIdx.x * kEmWarps + warp; cell < total_cells; cell += gridDim.x * kEmWarps) {
     const BatchImage& im = imgs[find_image(imgs, n, cell, 0)];
     const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
-    label_cell_warp<LabPlanar>(src, im.g, gp + (long long)im.k_off * kGP, im.labels,
-                               cell_ll ? cell_ll + im.cell_off : nullptr, cell - im.cell_off, sp_all[warp], lane);
+    label_cell_warp<LabPlanar, CM>(src, im.g, gp + (long long)im.k_off * kGP, im.labels,
+                                   cell_ll ? cell_ll + im.cell_off : nullptr, cell - im.cell_off, sp_all[warp],
+                                   lane);
     __syncwarp();
   }
 }
@@ -647,7 +676,25 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
       for (int j = 2; j < 5; ++j) mu[j] = dl[j];
     }
     rs = clamp_sym2<T>(cs, T(eps_s));
-    rc = clamp_sym3<T>(cc, T(eps_c));
+    if (g.cm == kColourFull) {
+      rc = clamp_sym3<T>(cc, T(eps_c));
+    } else {
+      // Eq. (BlockSigma1) / grayscale: no L-(a, b) entries; each block floored on its own
+      cc[1] = cc[2] = T(0);
+      rc = 0;
+      if (!(cc[0] >= T(eps_c))) {
+        cc[0] = T(eps_c);
+        rc = 1;
+      }
+      if (g.cm == kColourSplit) {
+        T ab[3] = {cc[3], cc[4], cc[5]};
+        rc += clamp_sym2<T>(ab, T(eps_c));
+        cc[3] = ab[0]; cc[4] = ab[1]; cc[5] = ab[2];
+      } else {
+        cc[3] = cc[4] = cc[5] = T(0);
+        mu[3] = mu[4] = T(0);
+      }
+    }
     double* th = theta + (long long)k * kTheta;
 #pragma unroll
     for (int j = 0; j < 5; ++j) th[j] = double(mu[j]);
@@ -655,7 +702,7 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
     for (int j = 0; j < 3; ++j) th[5 + j] = double(cs[j]);
 #pragma unroll
     for (int j = 0; j < 6; ++j) th[8 + j] = double(cc[j]);
-    pack_gp<T>(mu, cs, cc, ox, oy, G);
+    pack_gp<T>(mu, cs, cc, ox, oy, G, g.cm);
   }
 }
 
@@ -985,47 +1032,64 @@ size_t finalize_workspace_doubles(const Geom& g) {
   return (b16 > size_t(ll_blocks(g)) ? b16 : size_t(ll_blocks(g))) + 1;
 }
 
-template <typename PT, bool SHIFT, int WPC, class Src>
+template <typename PT, bool SHIFT, int WPC, class Src, int CM>
 static cudaError_t em_pass_impl(Src lab, const Geom& g, const float* gp, PT* partials,
                                 cudaStream_t s) {
   constexpr int smem = em_smem_bytes<WPC>();
   static_assert(smem <= 227 * 1024, "shared memory");
   static bool attr_set = false;  // per process; the attribute is per function
   if (!attr_set && smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_em_pass<PT, SHIFT, WPC, Src>,
+    cudaError_t e = cudaFuncSetAttribute(k_em_pass<PT, SHIFT, WPC, Src, CM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   constexpr int cpb = kEmWarps / WPC;
   const int blocks = (g.ncells + cpb - 1) / cpb;
-  return launch_pdl(k_em_pass<PT, SHIFT, WPC, Src>, dim3(blocks), dim3(kEmWarps * 32), smem, s, lab, g,
+  return launch_pdl(k_em_pass<PT, SHIFT, WPC, Src, CM>, dim3(blocks), dim3(kEmWarps * 32), smem, s, lab, g,
                     gp, partials);
 }
 
-template <typename PT, bool SHIFT, class Src>
+template <typename PT, bool SHIFT, class Src, int CM>
 static cudaError_t em_pass_wpc(Src lab, const Geom& g, const float* gp, PT* partials, int wpc,
                                cudaStream_t s) {
   switch (wpc) {
-    case 2: return em_pass_impl<PT, SHIFT, 2, Src>(lab, g, gp, partials, s);
-    case 4: return em_pass_impl<PT, SHIFT, 4, Src>(lab, g, gp, partials, s);
-    default: return em_pass_impl<PT, SHIFT, 1, Src>(lab, g, gp, partials, s);
+    case 2: return em_pass_impl<PT, SHIFT, 2, Src, CM>(lab, g, gp, partials, s);
+    case 4: return em_pass_impl<PT, SHIFT, 4, Src, CM>(lab, g, gp, partials, s);
+    default: return em_pass_impl<PT, SHIFT, 1, Src, CM>(lab, g, gp, partials, s);
   }
 }
 
+// The FP32 variant and the caller-pitched source take the full colour model
+// only (the entry points check it).
 template <class Src>
 cudaError_t launch_em_pass(Src lab, const Geom& g, const float* gp, void* partials, int precision,
                            int wpc, cudaStream_t s) {
   if (precision == 1)
-    return em_pass_wpc<float, false, Src>(lab, g, gp, static_cast<float*>(partials), wpc, s);
-  return em_pass_wpc<double, true, Src>(lab, g, gp, static_cast<double*>(partials), wpc, s);
+    return em_pass_wpc<float, false, Src, kColourFull>(lab, g, gp, static_cast<float*>(partials), wpc, s);
+  double* part = static_cast<double*>(partials);
+  if constexpr (std::is_same<Src, LabPlanar>::value) {
+    if (g.cm == kColourSplit) return em_pass_wpc<double, true, Src, kColourSplit>(lab, g, gp, part, wpc, s);
+    if (g.cm == kColourGray) return em_pass_wpc<double, true, Src, kColourGray>(lab, g, gp, part, wpc, s);
+  }
+  if (g.cm != kColourFull) return cudaErrorInvalidValue;
+  return em_pass_wpc<double, true, Src, kColourFull>(lab, g, gp, part, wpc, s);
 }
 
 template <class Src>
 cudaError_t launch_label_pass(Src lab, const Geom& g, const float* gp, int32_t* labels,
                               double* cell_ll, cudaStream_t s) {
   const int blocks = (g.ncells + kEmWarps - 1) / kEmWarps;
-  return launch_pdl(k_label_pass<Src>, dim3(blocks), dim3(kEmWarps * 32), 0, s, lab, g, gp, labels,
+  if constexpr (std::is_same<Src, LabPlanar>::value) {
+    if (g.cm == kColourSplit)
+      return launch_pdl(k_label_pass<Src, kColourSplit>, dim3(blocks), dim3(kEmWarps * 32), 0, s, lab, g, gp,
+                        labels, cell_ll);
+    if (g.cm == kColourGray)
+      return launch_pdl(k_label_pass<Src, kColourGray>, dim3(blocks), dim3(kEmWarps * 32), 0, s, lab, g, gp,
+                        labels, cell_ll);
+  }
+  if (g.cm != kColourFull) return cudaErrorInvalidValue;
+  return launch_pdl(k_label_pass<Src, kColourFull>, dim3(blocks), dim3(kEmWarps * 32), 0, s, lab, g, gp, labels,
                     cell_ll);
 }
 
@@ -1042,7 +1106,7 @@ cudaError_t launch_finalize(const Geom& g, const void* partials, double* theta, 
                             double eps_s, double eps_c, double* llk_out, double* ws,
                             unsigned* ticket, unsigned long long* counters, int precision,
                             cudaStream_t s) {
-  if (precision != 1 && g.K <= kFin16MaxK) {
+  if (precision != 1 && g.K <= kFin16MaxK && g.cm == kColourFull) {
     const int blocks16 = (g.K + kFin16Threads / 16 - 1) / (kFin16Threads / 16);
     return launch_pdl(k_finalize_l16, dim3(blocks16), dim3(kFin16Threads), 0, s, g,
                       static_cast<const double*>(partials), theta, gp, eps_s, eps_c, llk_out, ws, ticket,
@@ -1068,29 +1132,47 @@ cudaError_t launch_ll_reduce(const double* cell_ll, int n, double* out, double* 
 // ---------------------------------------------------------------- batch launchers
 namespace gmmsp {
 
-cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
-                                 const float* gp, void* partials, int precision, int blocks, int minb,
-                                 cudaStream_t s) {
+template <int CM>
+static void em_pass_batch_mixed(const BatchImage* imgs, int n, int total_cells, const float* lab, const float* gp,
+                                double* partials, int blocks, int minb, cudaStream_t s) {
   constexpr int smem = em_smem_bytes<1>();
   if (minb >= 6) {  // one cell per warp over a grid sized to the work
     const int nb = (total_cells + kEmWarps - 1) / kEmWarps;
-    if (precision == 1)
-      k_em_pass_batch_flat<float, false, 6><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                          static_cast<float*>(partials));
-    else if (minb >= 7)
-      k_em_pass_batch_flat<double, true, 7><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                          static_cast<double*>(partials));
+    if (minb >= 7)
+      k_em_pass_batch_flat<double, true, 7, CM><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                              partials);
     else
-      k_em_pass_batch_flat<double, true, 6><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                          static_cast<double*>(partials));
+      k_em_pass_batch_flat<double, true, 6, CM><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                              partials);
+  } else {
+    k_em_pass_batch<double, true, 5, CM><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                           partials);
+  }
+}
+
+cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
+                                 const float* gp, void* partials, int precision, int blocks, int minb,
+                                 int cm, cudaStream_t s) {
+  constexpr int smem = em_smem_bytes<1>();
+  if (precision == 1) {  // full colour model only
+    if (cm != kColourFull) return cudaErrorInvalidValue;
+    if (minb >= 6) {
+      const int nb = (total_cells + kEmWarps - 1) / kEmWarps;
+      k_em_pass_batch_flat<float, false, 6, kColourFull><<<nb, kEmWarps * 32, smem, s>>>(
+          imgs, n, total_cells, lab, gp, static_cast<float*>(partials));
+    } else {
+      k_em_pass_batch<float, false, 5, kColourFull><<<blocks, kEmWarps * 32, smem, s>>>(
+          imgs, n, total_cells, lab, gp, static_cast<float*>(partials));
+    }
     return cudaGetLastError();
   }
-  if (precision == 1)
-    k_em_pass_batch<float, false, 5><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                       static_cast<float*>(partials));
-  else
-    k_em_pass_batch<double, true, 5><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                       static_cast<double*>(partials));
+  double* part = static_cast<double*>(partials);
+  switch (cm) {
+    case kColourFull: em_pass_batch_mixed<kColourFull>(imgs, n, total_cells, lab, gp, part, blocks, minb, s); break;
+    case kColourSplit: em_pass_batch_mixed<kColourSplit>(imgs, n, total_cells, lab, gp, part, blocks, minb, s); break;
+    case kColourGray: em_pass_batch_mixed<kColourGray>(imgs, n, total_cells, lab, gp, part, blocks, minb, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -1116,7 +1198,8 @@ cudaError_t launch_finalize_batch(const BatchImage* imgs, int n, int total_k, co
 
 int label_pass_batch_occupancy() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_label_pass_batch, kEmWarps * 32, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_label_pass_batch<kColourFull>, kEmWarps * 32, 0) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 4;
   }
@@ -1124,8 +1207,19 @@ int label_pass_batch_occupancy() {
 }
 
 cudaError_t launch_label_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
-                                    const float* gp, double* cell_ll, int blocks, cudaStream_t s) {
-  k_label_pass_batch<<<blocks, kEmWarps * 32, 0, s>>>(imgs, n, total_cells, lab, gp, cell_ll);
+                                    const float* gp, double* cell_ll, int blocks, int cm, cudaStream_t s) {
+  switch (cm) {
+    case kColourFull:
+      k_label_pass_batch<kColourFull><<<blocks, kEmWarps * 32, 0, s>>>(imgs, n, total_cells, lab, gp, cell_ll);
+      break;
+    case kColourSplit:
+      k_label_pass_batch<kColourSplit><<<blocks, kEmWarps * 32, 0, s>>>(imgs, n, total_cells, lab, gp, cell_ll);
+      break;
+    case kColourGray:
+      k_label_pass_batch<kColourGray><<<blocks, kEmWarps * 32, 0, s>>>(imgs, n, total_cells, lab, gp, cell_ll);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

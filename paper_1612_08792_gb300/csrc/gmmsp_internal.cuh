@@ -41,6 +41,15 @@ enum : int { ST_W = 0, ST_S1 = 1, ST_S2S = 6, ST_S2C = 9 };
 //
 // Master FP64 parameters (128 bytes): [0..4] mu, [5..7] Sigma_s (xx, xy, yy),
 // [8..13] Sigma_c (LL, La, Lb, aa, ab, bb), [14..15] unused.
+//
+// Colour models (Sec. III-A, III-C; gmmsp_params.colour_model): the full
+// 3x3 Sigma_c of Eq. (BlockSigma); the split diag(sigma_l^2, Sigma_(a,b)) of
+// Eq. (BlockSigma1), whose La, Lb entries and coefficients are 0; grayscale,
+// a scalar colour L with mu's a, b and every Sigma_c entry but LL at 0, the
+// a, b coefficients 0 and the normaliser of a 3-dimensional Gaussian.  The
+// layouts above are shared by all three; the E-step and M-step kernels are
+// compiled per model and skip the terms a model does not have.
+enum : int { kColourFull = 0, kColourSplit = 1, kColourGray = 2 };
 
 struct Geom {
   int W, H;      // image size
@@ -49,6 +58,7 @@ struct Geom {
   int K;
   int ncx, ncy;  // cell grid incl. remainder strips: ceil(W / v), ceil(H / v)
   int ncells;
+  int cm = kColourFull;  // colour model
 };
 
 // Where the kernels read the CIELAB colour of pixel (x, y) from.
@@ -60,6 +70,7 @@ struct LabPlanar {  // the context's image: three float32 planes L, a, b of W H 
     const long long i = (long long)y * W + x;
     return make_float4(__ldg(p + i), __ldg(p + plane + i), __ldg(p + 2 * plane + i), 0.f);
   }
+  __device__ __forceinline__ float load_l(int x, int y) const { return __ldg(p + (long long)y * W + x); }
 };
 struct LabPitched {  // a caller's image: rows of (L, a, b) float32, row pitch in bytes
   const char* p;
@@ -68,7 +79,17 @@ struct LabPitched {  // a caller's image: rows of (L, a, b) float32, row pitch i
     const float* q = reinterpret_cast<const float*>(p + (long long)y * pitch) + 3LL * x;
     return make_float4(__ldg(q), __ldg(q + 1), __ldg(q + 2), 0.f);
   }
+  __device__ __forceinline__ float load_l(int x, int y) const {
+    return __ldg(reinterpret_cast<const float*>(p + (long long)y * pitch) + 3LL * x);
+  }
 };
+
+// The colour of pixel (x, y) under colour model CM: grayscale reads L only.
+template <int CM, class Src>
+__device__ __forceinline__ float4 load_z(const Src& s, int x, int y) {
+  if constexpr (CM == kColourGray) return make_float4(s.load_l(x, y), 0.f, 0.f, 0.f);
+  else return s.load(x, y);
+}
 
 // Programmatic dependent launch (off unless GMMSP_PDL=1: measured slower on
 // this pipeline of short dependent kernels).  When on, the single-image
@@ -115,14 +136,17 @@ enum : int { CNT_DEAD = 0, CNT_RAISED_S = 1, CNT_RAISED_C = 2, CNT_NONFINITE = 3
 
 // ---- launchers (each returns the launch's cudaError_t) ----
 // lab: three planes of W H floats (L, a, b), plane stride W H.
+// Under the grayscale model only plane L is written (the a, b planes are
+// left as they are: zero, set once by the context).
 cudaError_t launch_rgb2lab(const uint8_t* img, long long pitch, const Geom& g, float* lab,
                            unsigned long long* counters, cudaStream_t s);
 cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float* lab,
                          unsigned long long* counters, cudaStream_t s);
+cudaError_t launch_gray2l(const uint8_t* img, long long pitch, const Geom& g, float* lab, cudaStream_t s);
 template <class Src>
 cudaError_t launch_init_theta(Src lab, const Geom& g, double lambda_c, double* theta, float* gp,
                               cudaStream_t s);
-// wpc: warps per cell (1, 2 or 4).
+// wpc: warps per cell (1, 2 or 4); the colour model is g.cm.
 template <class Src>
 cudaError_t launch_em_pass(Src lab, const Geom& g, const float* gp, void* partials, int precision,
                            int wpc, cudaStream_t s);
@@ -144,6 +168,7 @@ cudaError_t launch_pack_theta(const Geom& g, double* theta, float* gp, int* bad,
 
 // Batches: the same steps over all images of a BatchImage table in one launch
 // each; `blocks` is the persistent grid size.
+// Grayscale model (the images' g.cm): plane L only, as launch_rgb2lab.
 cudaError_t launch_prepare_batch(const BatchImage* imgs, int n, long long total_rows, int input_format,
                                  float* lab, unsigned long long* counters, int blocks, cudaStream_t s);
 cudaError_t launch_init_batch(const BatchImage* imgs, int n, int total_k, const float* lab,
@@ -153,15 +178,16 @@ cudaError_t launch_init_batch(const BatchImage* imgs, int n, int total_k, const 
 // kernel on `blocks` blocks.
 cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
                                  const float* gp, void* partials, int precision, int blocks, int minb,
-                                 cudaStream_t s);
-// blocks == 0 (mixed precision only): 16 lanes per superpixel, one block per
-// 4 superpixels; otherwise one thread per superpixel on `blocks` blocks.
+                                 int cm, cudaStream_t s);
+// blocks == 0 (mixed precision and the full colour model only): 16 lanes per
+// superpixel, one block per 4 superpixels; otherwise one thread per
+// superpixel on `blocks` blocks.
 cudaError_t launch_finalize_batch(const BatchImage* imgs, int n, int total_k, const void* partials,
                                   double* theta, float* gp, double eps_s, double eps_c,
                                   unsigned long long* counters, int precision, int blocks,
                                   cudaStream_t s);
 cudaError_t launch_label_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
-                                    const float* gp, double* cell_ll, int blocks, cudaStream_t s);
+                                    const float* gp, double* cell_ll, int blocks, int cm, cudaStream_t s);
 // Resident 128-thread blocks per SM of the batch label pass.
 int label_pass_batch_occupancy();
 // ll_out[i] = sum of image i's per-cell log-likelihoods (fixed order).

@@ -37,6 +37,7 @@ template <typename T> struct Num;
 template <> struct Num<double> {
   static constexpr double kLog2e = 1.4426950408889634074;
   static constexpr double kHalfD_Log2_2Pi = 6.6287403236807968;  // (5/2) log2(2 pi)
+  static constexpr double kHalf3_Log2_2Pi = 3.9772441942084784;  // (3/2) log2(2 pi)
   // 1/x: FP32 estimate (MUFU, relative error < 2^-22), two Newton steps.
   static __device__ __forceinline__ double rcp(double x) {
     float r0;
@@ -68,6 +69,7 @@ template <> struct Num<double> {
 template <> struct Num<float> {
   static constexpr float kLog2e = 1.44269504f;
   static constexpr float kHalfD_Log2_2Pi = 6.62874032f;
+  static constexpr float kHalf3_Log2_2Pi = 3.97724419f;
   static __device__ __forceinline__ float rcp(float x) { return 1.0f / x; }
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float log2_(float x) { return log2f(x); }
@@ -198,11 +200,28 @@ __device__ int clamp_sym3(T* A, T eps) {
 // superpixel's own grid cell (k_x v, k_y v), so that it keeps FP32 precision
 // on large images (absolute coordinates near 4000 would round to 2.4e-4 px).
 // Returns false when a block is not positive definite (leading minors).
+// cm: the colour model.  Split: cc's La, Lb entries are taken as 0.
+// Grayscale: only cc[0] and mu[0..2] are read, the a, b coefficients are 0
+// and the normaliser is that of a 3-dimensional Gaussian.
 template <typename T>
-__device__ bool pack_gp(const T* mu, const T* cs, const T* cc, T ox, T oy, float* gp) {
+__device__ bool pack_gp(const T* mu, const T* cs, const T* cc_in, T ox, T oy, float* gp, int cm = kColourFull) {
   using M = Num<T>;
   // spatial 2x2
   const T ds = fma(cs[0], cs[2], -cs[1] * cs[1]);
+  float4* o = reinterpret_cast<float4*>(gp);
+  if (cm == kColourGray) {
+    if (!(cs[0] > T(0) && ds > T(0) && cc_in[0] > T(0))) return false;
+    const T hs = T(-0.5) * M::kLog2e * M::rcp(ds);
+    const T hc = T(-0.5) * M::kLog2e * M::rcp(cc_in[0]);
+    o[0] = make_float4(float(mu[0] - ox), float(mu[1] - oy), float(mu[2]), 0.f);
+    o[1] = make_float4(0.f, float(hs * cs[2]), float(T(-2) * hs * cs[1]), float(hs * cs[0]));
+    o[2] = make_float4(float(hc), 0.f, 0.f, 0.f);
+    const float lnorm = -0.5f * (M::log2_(ds) + M::log2_(cc_in[0])) - float(M::kHalf3_Log2_2Pi);
+    o[3] = make_float4(0.f, 0.f, lnorm, 0.f);
+    return true;
+  }
+  const bool split = cm == kColourSplit;
+  const T cc[6] = {cc_in[0], split ? T(0) : cc_in[1], split ? T(0) : cc_in[2], cc_in[3], cc_in[4], cc_in[5]};
   // colour 3x3 cofactors
   const T c00 = fma(cc[3], cc[5], -cc[4] * cc[4]);
   const T c01 = fma(cc[2], cc[4], -cc[1] * cc[5]);
@@ -214,7 +233,6 @@ __device__ bool pack_gp(const T* mu, const T* cs, const T* cc, T ox, T oy, float
   if (!(cs[0] > T(0) && ds > T(0) && cc[0] > T(0) && c22 > T(0) && dc > T(0))) return false;
   const T hs = T(-0.5) * M::kLog2e * M::rcp(ds);   // -(1/2) log2(e) / det
   const T hc = T(-0.5) * M::kLog2e * M::rcp(dc);
-  float4* o = reinterpret_cast<float4*>(gp);
   o[0] = make_float4(float(mu[0] - ox), float(mu[1] - oy), float(mu[2]), float(mu[3]));
   o[1] = make_float4(float(mu[4]), float(hs * cs[2]), float(T(-2) * hs * cs[1]), float(hs * cs[0]));
   o[2] = make_float4(float(hc * c00), float(hc * c11), float(hc * c22), float(T(2) * hc * c01));

@@ -119,9 +119,10 @@ extern "C" gmmsp_status gmmsp_segment_lab_noalloc(const float* lab_dev, int widt
     set_err(err, err_len, "pitch must be >= 12 * width bytes and 4-byte aligned");
     return GMMSP_E_INVALID;
   }
-  if (p->precision != GMMSP_PREC_MIXED || !(p->eps_s > 0.f) || !(p->eps_c > 0.f) ||
-      !(p->lambda_c > 0.f) || iters < 0 || (p->spacing <= 0 && p->K <= 0)) {
-    set_err(err, err_len, "invalid parameters (mixed precision only; eps, lambda_c > 0; iters >= 0)");
+  if (p->precision != GMMSP_PREC_MIXED || p->colour_model != GMMSP_COLOUR_FULL || !(p->eps_s > 0.f) ||
+      !(p->eps_c > 0.f) || !(p->lambda_c > 0.f) || iters < 0 || (p->spacing <= 0 && p->K <= 0)) {
+    set_err(err, err_len,
+            "invalid parameters (mixed precision and the full colour model only; eps, lambda_c > 0; iters >= 0)");
     return GMMSP_E_INVALID;
   }
   Geom g;

@@ -9,6 +9,11 @@
 //    per block with powf) and the CIE 1976 L*a*b* formulas.
 //  * k_lab32: repacks a caller's float32 L,a,b image into planes and counts
 //    non-finite values.
+//  * k_gray2l: grey levels -> CIE L*.  A grey pixel drives the three
+//    primaries equally, so its luminance relative to the white is the decoded
+//    grey level itself: L* = 116 f(decode(g / 255)) - 16.
+//  Under the grayscale colour model every conversion writes plane L only;
+//  the context keeps the a, b planes at zero.
 //  * k_init_theta: Sec. III-C initialisation: mu_k = z of the centre pixel of
 //    cell k, Sigma_s = diag(v^2, v^2), Sigma_c = lambda_c^2 I.
 //  * k_pack_theta: re-derives the packed E-step coefficients from FP64
@@ -32,14 +37,19 @@ __device__ __forceinline__ float cielab_f(float t) {
   return t > d3 ? cbrtf(t) : fmaf(slope, t, 4.f / 29.f);
 }
 
-__global__ void __launch_bounds__(256) k_rgb2lab(const uint8_t* __restrict__ img, long long pitch,
-                                                 int W, int H, float* __restrict__ lab,
-                                                 Rgb2LabConst k) {
-  __shared__ float lin[256];
+// sRGB decoding of the 256 code values (the transfer curve of IEC 61966-2-1).
+__device__ __forceinline__ void build_srgb_table(float* lin) {
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     const float c = float(i) * (1.f / 255.f);
     lin[i] = c <= 0.04045f ? c * (1.f / 12.92f) : powf((c + 0.055f) * (1.f / 1.055f), 2.4f);
   }
+}
+
+__global__ void __launch_bounds__(256) k_rgb2lab(const uint8_t* __restrict__ img, long long pitch,
+                                                 int W, int H, float* __restrict__ lab,
+                                                 Rgb2LabConst k, bool l_only) {
+  __shared__ float lin[256];
+  build_srgb_table(lin);
   pdl_wait();  // the CIELAB buffer may still be read by the previous pipeline run
   pdl_trigger();
   __syncthreads();
@@ -55,14 +65,31 @@ __global__ void __launch_bounds__(256) k_rgb2lab(const uint8_t* __restrict__ img
     const float Z = fmaf(m[6], r, fmaf(m[7], g, m[8] * b)) * k.inv_white[2];
     const float fx = cielab_f(X), fy = cielab_f(Y), fz = cielab_f(Z);
     lab[idx] = 116.f * fy - 16.f;
-    lab[N + idx] = 500.f * (fx - fy);
-    lab[2 * N + idx] = 200.f * (fy - fz);
+    if (!l_only) {
+      lab[N + idx] = 500.f * (fx - fy);
+      lab[2 * N + idx] = 200.f * (fy - fz);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_gray2l(const uint8_t* __restrict__ img, long long pitch, int W, int H,
+                                                float* __restrict__ lab) {
+  __shared__ float lin[256];
+  build_srgb_table(lin);
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  const long long N = (long long)W * H;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int y = int(idx / W), x = int(idx - (long long)y * W);
+    lab[idx] = 116.f * cielab_f(lin[img[(long long)y * pitch + x]]) - 16.f;
   }
 }
 
 __global__ void __launch_bounds__(256) k_lab32(const float* __restrict__ img, long long pitch, int W,
                                                int H, float* __restrict__ lab,
-                                               unsigned long long* __restrict__ counters) {
+                                               unsigned long long* __restrict__ counters, bool l_only) {
   const long long N = (long long)W * H;
   unsigned bad = 0;
   pdl_wait();
@@ -72,11 +99,16 @@ __global__ void __launch_bounds__(256) k_lab32(const float* __restrict__ img, lo
     const int y = int(idx / W), x = int(idx - (long long)y * W);
     const float* p = reinterpret_cast<const float*>(reinterpret_cast<const char*>(img) +
                                                     (long long)y * pitch) + 3LL * x;
-    const float L = p[0], a = p[1], b = p[2];
-    bad += !(isfinite(L) && isfinite(a) && isfinite(b));
+    const float L = p[0];
     lab[idx] = L;
-    lab[N + idx] = a;
-    lab[2 * N + idx] = b;
+    if (l_only) {
+      bad += !isfinite(L);
+    } else {
+      const float a = p[1], b = p[2];
+      bad += !(isfinite(L) && isfinite(a) && isfinite(b));
+      lab[N + idx] = a;
+      lab[2 * N + idx] = b;
+    }
   }
   bad = __reduce_add_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&counters[CNT_NONFINITE], (unsigned long long)bad);
@@ -89,16 +121,17 @@ __device__ __forceinline__ void init_k(const Src& lab, const Geom& g, double lam
   const int kx = k % g.nx, ky = k / g.nx;
   const int x = kx * g.v + g.v / 2, y = ky * g.v + g.v / 2;
   const float4 c = lab.load(x, y);
-  const double mu[5] = {double(x), double(y), double(c.x), double(c.y), double(c.z)};
+  const bool gray = g.cm == kColourGray;
+  const double mu[5] = {double(x), double(y), double(c.x), gray ? 0.0 : double(c.y), gray ? 0.0 : double(c.z)};
   const double vv = double(g.v) * double(g.v), ll = lambda_c * lambda_c;
   const double cs[3] = {vv, 0.0, vv};
-  const double cc[6] = {ll, 0.0, 0.0, ll, 0.0, ll};
+  const double cc[6] = {ll, 0.0, 0.0, gray ? 0.0 : ll, 0.0, gray ? 0.0 : ll};
   double* th = theta + (long long)k * kTheta;
   for (int i = 0; i < 5; ++i) th[i] = mu[i];
   for (int i = 0; i < 3; ++i) th[5 + i] = cs[i];
   for (int i = 0; i < 6; ++i) th[8 + i] = cc[i];
   th[14] = th[15] = 0.0;
-  pack_gp<double>(mu, cs, cc, double(kx * g.v), double(ky * g.v), gp + (long long)k * kGP);
+  pack_gp<double>(mu, cs, cc, double(kx * g.v), double(ky * g.v), gp + (long long)k * kGP, g.cm);
 }
 
 template <class Src>
@@ -120,7 +153,7 @@ __global__ void k_pack_theta(Geom g, const double* __restrict__ theta, float* __
   for (int i = 0; i < 14; ++i) ok = ok && isfinite(th[i]);
   const int kx = k % g.nx, ky = k / g.nx;
   ok = ok && pack_gp<double>(th, th + 5, th + 8, double(kx * g.v), double(ky * g.v),
-                             gp + (long long)k * kGP);
+                             gp + (long long)k * kGP, g.cm);
   if (!ok) atomicAdd(bad, 1);
 }
 
@@ -169,13 +202,20 @@ cudaError_t launch_rgb2lab(const uint8_t* img, long long pitch, const Geom& g, f
   (void)counters;
   static const Rgb2LabConst k = make_rgb2lab_const();
   const long long N = (long long)g.W * g.H;
-  return launch_pdl(k_rgb2lab, dim3(grid_for(N, 256)), dim3(256), 0, s, img, pitch, g.W, g.H, lab, k);
+  return launch_pdl(k_rgb2lab, dim3(grid_for(N, 256)), dim3(256), 0, s, img, pitch, g.W, g.H, lab, k,
+                    g.cm == kColourGray);
+}
+
+cudaError_t launch_gray2l(const uint8_t* img, long long pitch, const Geom& g, float* lab, cudaStream_t s) {
+  const long long N = (long long)g.W * g.H;
+  return launch_pdl(k_gray2l, dim3(grid_for(N, 256)), dim3(256), 0, s, img, pitch, g.W, g.H, lab);
 }
 
 cudaError_t launch_lab32(const float* img, long long pitch, const Geom& g, float* lab,
                          unsigned long long* counters, cudaStream_t s) {
   const long long N = (long long)g.W * g.H;
-  return launch_pdl(k_lab32, dim3(grid_for(N, 256)), dim3(256), 0, s, img, pitch, g.W, g.H, lab, counters);
+  return launch_pdl(k_lab32, dim3(grid_for(N, 256)), dim3(256), 0, s, img, pitch, g.W, g.H, lab, counters,
+                    g.cm == kColourGray);
 }
 
 template <class Src>
@@ -216,10 +256,7 @@ __global__ void __launch_bounds__(256) k_prepare_batch(const BatchImage* __restr
                                                        float* __restrict__ lab, Rgb2LabConst k,
                                                        unsigned long long* __restrict__ counters) {
   __shared__ float lin[256];
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-    const float c = float(i) * (1.f / 255.f);
-    lin[i] = c <= 0.04045f ? c * (1.f / 12.92f) : powf((c + 0.055f) * (1.f / 1.055f), 2.4f);
-  }
+  build_srgb_table(lin);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * (blockDim.x >> 5);
@@ -230,9 +267,12 @@ __global__ void __launch_bounds__(256) k_prepare_batch(const BatchImage* __restr
     const long long N = (long long)W * im.g.H;
     float* P = lab + 3 * im.pix_off;
     const char* src = static_cast<const char*>(im.image) + (long long)y * im.pitch;
+    const bool l_only = im.g.cm == kColourGray;
     for (int x = lane; x < W; x += 32) {
-      float L, a, b;
-      if (input_format == 0) {
+      float L, a = 0.f, b = 0.f;
+      if (input_format == 2) {  // grey levels
+        L = 116.f * cielab_f(lin[reinterpret_cast<const uint8_t*>(src)[x]]) - 16.f;
+      } else if (input_format == 0) {
         const uint8_t* p = reinterpret_cast<const uint8_t*>(src) + 3LL * x;
         const float r = lin[p[0]], g = lin[p[1]], bl = lin[p[2]];
         const float* m = k.m;
@@ -243,11 +283,13 @@ __global__ void __launch_bounds__(256) k_prepare_batch(const BatchImage* __restr
         L = 116.f * fy - 16.f; a = 500.f * (fx - fy); b = 200.f * (fy - fz);
       } else {
         const float* p = reinterpret_cast<const float*>(src) + 3LL * x;
-        L = p[0]; a = p[1]; b = p[2];
+        L = p[0];
+        if (!l_only) { a = p[1]; b = p[2]; }
         bad += !(isfinite(L) && isfinite(a) && isfinite(b));
       }
       const long long q = (long long)y * W + x;
-      P[q] = L; P[N + q] = a; P[2 * N + q] = b;
+      P[q] = L;
+      if (!l_only) { P[N + q] = a; P[2 * N + q] = b; }
     }
   }
   bad = __reduce_add_sync(0xffffffffu, bad);

@@ -41,7 +41,32 @@ def test_default_params(lib):
     p = gm.gmmsp_default_params()
     assert (p.spacing, p.K, p.eps_s, p.eps_c, p.lambda_c) == (0, 0, 2.0, 8.0, 8.0)
     assert p.input_format == gm.GMMSP_RGB8 and p.precision == gm.GMMSP_PREC_MIXED
+    assert p.colour_model == gm.GMMSP_COLOUR_FULL
     assert gm.gmmsp_status_string(1) == "GMMSP_E_INVALID"
+
+
+@pytest.mark.parametrize("fmt,prec,cm,pitch,batch_too", [
+    (0, 0, 3, 960, True),      # unknown colour model
+    (0, 0, -1, 960, True),
+    (0, 1, 1, 960, True),      # FP32 precision with the split model
+    (1, 1, 2, 3840, True),     # FP32 precision with grayscale
+    (2, 0, 0, 320, True),      # grey-level input with the full model
+    (2, 0, 1, 320, True),      # ... or the split one
+    (2, 0, 2, 319, False),     # grey-level rows need W bytes (a batch checks pitches when it segments)
+    (3, 0, 0, 960, True),      # unknown format
+])
+def test_colour_model_combinations_rejected_on_host(lib, fmt, prec, cm, pitch, batch_too):
+    import paper_1612_08792_gb300 as gm
+    p = gm.gmmsp_default_params()
+    p.spacing, p.input_format, p.precision, p.colour_model = 12, fmt, prec, cm
+    ctx = ctypes.c_void_p(1234)
+    assert lib.gmmsp_init(ctypes.byref(ctx), 0x1000, 320, 240, pitch, ctypes.byref(p), None) == 1
+    assert not ctx.value
+    if batch_too:
+        b = ctypes.c_void_p(1234)
+        W, H = (ctypes.c_int * 1)(320), (ctypes.c_int * 1)(240)
+        assert lib.gmmsp_batch_create(ctypes.byref(b), 1, W, H, ctypes.byref(p), None) == 1
+        assert not b.value
 
 
 @pytest.mark.parametrize("W,H,K,sp,pitch,eps", [
