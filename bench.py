@@ -65,6 +65,15 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 INSTR_PER_CAND = 48
 INSTR_PER_PIXEL = 2
 FP32_PEAK_TINST = 152 * 128 * 2.070e9 / 1e12
+# The same counts for the colour models (--colour, plain-EM lines):
+#   split (Eq. BlockSigma1): no L-a, L-b terms -- E quadratic form 12 instead of 14,
+#     M second moments 7 instead of 9                      -> 21 + 23 = 44 instructions
+#     (flops: E 5 + 8 + 11 + 4, M 1 + 5 + 5 + 14            -> 53)
+#   gray: z = (x, y, L) -- E d 3, quadratic forms 5 + 2, 4; M d 3, W 1, R d 3,
+#     S1 3, second moments 4                                -> 14 + 14 = 28 instructions
+#     (flops: E 3 + 8 + 3 + 4, M 1 + 3 + 3 + 8              -> 33)
+INSTR_PER_CAND_MODEL = {"full": INSTR_PER_CAND, "split": 44, "gray": 28}
+FLOPS_PER_CAND_MODEL = {"full": FLOPS_PER_CAND, "split": 53, "gray": 33}
 
 
 def workload_config(v, nx, ny, K):
@@ -406,7 +415,7 @@ def run_other_workload(args):
                 cache[key] = torch.from_numpy(voronoi_image(Wi, Hi, batch_regions(Wi, Hi), 8.0, seed=i % 4)).cuda()
             imgs.append(cache[key])
         with torch.cuda.stream(stream):
-            bt = gm.SuperpixelsBatch([(h, w) for (w, h) in sizes], spacing=15, stream=stream)
+            bt = gm.SuperpixelsBatch([(h, w) for (w, h) in sizes], spacing=15, stream=stream, colour=args.colour)
             bps, tune = bt.autotune(imgs, reps=3)
         pix, K, cells = bt.info()
         em_ms = tune[bps]
@@ -420,8 +429,10 @@ def run_other_workload(args):
             _, ll = bt.segment(imgs, ITERS, want_loglik=True)
         config = {"workload": f"batch of 256 synthetic Voronoi sRGB images, sizes uniform over "
                               f"320x240/481x321/640x480/1280x720/1920x1080 (regions proportional to area, "
-                              f"sigma 8), spacing 15, {ITERS} plain-EM iterations, one batch context",
+                              f"sigma 8), spacing 15, {ITERS} plain-EM iterations, one batch context, "
+                              f"{args.colour} colour covariance",
                   "images": 256, "pixels": pix, "K": K, "cells": cells, "blocks_per_sm": bps,
+                  "colour_model": args.colour,
                   "l2": "flushed between timed steps (256 MiB memset)"}
         launches = 2 + 2 * ITERS + 1
         extra = {"loglik_mean_per_pixel": float(np.sum(ll)) / pix, "em_pass_autotune_ms": tune}
@@ -431,7 +442,7 @@ def run_other_workload(args):
         img = torch.from_numpy(voronoi_image(Wd, Hd, 2000, 6.0, seed=0)).cuda()
         labels = torch.empty((Hd, Wd), dtype=torch.int32, device="cuda")
         with torch.cuda.stream(stream):
-            sp = gm.Superpixels(img, K=20000, stream=stream)
+            sp = gm.Superpixels(img, K=20000, stream=stream, colour=args.colour)
             sp.em_iters(2)
             wpc, _ = sp.autotune(reps=3)
         v, nx, ny, K = sp.grid.v, sp.grid.nx, sp.grid.ny, sp.grid.K
@@ -447,15 +458,16 @@ def run_other_workload(args):
             fin_ms = sp.profile_kernel(gm.GMMSP_KERNEL_FINALIZE, reps=10)
         units = candidate_units(Wd, Hd, v, nx, ny)
         config = {"workload": f"{Wd}x{Hd} synthetic Voronoi sRGB (2000 regions, sigma 6), K=20000 requested "
-                              f"-> v={v}, K={K}; {ITERS} plain-EM iterations", "W": Wd, "H": Hd, "K": K, "v": v,
+                              f"-> v={v}, K={K}; {ITERS} plain-EM iterations, {args.colour} colour covariance",
+                  "W": Wd, "H": Hd, "K": K, "v": v, "colour_model": args.colour,
                   "warps_per_cell": wpc, "l2": "flushed between timed steps (256 MiB memset)"}
         launches = 2 + 2 * ITERS + 1
         extra = {"loglik_per_pixel": float(ll[-1]) / pix, "kernel_ms": {"em_pass": em_ms, "finalize": fin_ms}}
         sp.close()
     ms = sum(step_ms) / len(step_ms)
-    flops = units * FLOPS_PER_CAND + pix * FLOPS_PER_PIXEL
+    flops = units * FLOPS_PER_CAND_MODEL[args.colour] + pix * FLOPS_PER_PIXEL
     achieved = flops / (em_ms * 1e-3) / 1e12
-    instr = units * INSTR_PER_CAND + pix * INSTR_PER_PIXEL
+    instr = units * INSTR_PER_CAND_MODEL[args.colour] + pix * INSTR_PER_PIXEL
     achieved_i = instr / (em_ms * 1e-3) / 1e12
     line = {"metric": METRIC, "value": round(pix / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4),
@@ -756,7 +768,7 @@ def run_profile_case(args):
         return 0
     if args.workload == "3840x2160":
         img = torch.from_numpy(voronoi_image(3840, 2160, 2000, 6.0, seed=0)).cuda()
-        sp = gm.Superpixels(img, K=20000)
+        sp = gm.Superpixels(img, K=20000, colour=args.colour)
     else:
         img = torch.from_numpy(voronoi_image(W, H, REGIONS, SIGMA, seed=0)).cuda()
         sp = gm.Superpixels(img, K=K_REQ)
@@ -786,7 +798,13 @@ def main():
                     help="learned481 (the headline line); 481x321, 3840x2160 or batch256 (other lines); "
                          "with --profile-case the case to profile")
     ap.add_argument("--images", type=int, default=LEARN_IMAGES, help="learned481: images per step")
+    ap.add_argument("--colour", default="full", choices=["full", "split", "gray"],
+                    help="colour covariance model of the plain-EM lines batch256 and 3840x2160 (the others "
+                         "run the full model)")
     args = ap.parse_args()
+    if args.colour != "full" and (args.workload not in ("batch256", "3840x2160") or
+                                  (args.profile_case and args.workload != "3840x2160")):
+        ap.error("--colour applies to the batch256 and 3840x2160 lines (and the 3840x2160 profile case) only")
     if args.profile_case:
         return run_profile_case(args)
     if args.workload == "learned481":
