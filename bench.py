@@ -766,6 +766,13 @@ def run_profile_case(args):
         net.close()
         print("profile case done", args.images)
         return 0
+    if args.workload == "conn256":
+        stream = torch.cuda.Stream()
+        bt, _ = _conn_case(gm, torch, args.images, stream)
+        st = bt.connectivity()
+        bt.close()
+        print("profile case done", st)
+        return 0
     if args.workload == "3840x2160":
         img = torch.from_numpy(voronoi_image(3840, 2160, 2000, 6.0, seed=0)).cuda()
         sp = gm.Superpixels(img, K=20000, colour=args.colour)
@@ -781,6 +788,134 @@ def run_profile_case(args):
     print("profile case done", tuple(labels.shape))
     return 0
 
+# Algorithmic DRAM bytes per pixel of the connectivity post-processing: the input
+# labels (4 B) and CIELAB colour (12 B) read once, the output labels (4 B) written.
+CONN_BYTES_PER_PIXEL = 20
+CONN_LAUNCHES = 20  # kernels of one gmmsp_batch_connectivity call
+
+
+def _conn_case(gm, torch, n, stream, keep_images=False):
+    """n held-out 481x321 images (v = 15) segmented by 10 plain-EM iterations in one batch
+    context: the label maps the connectivity post-processing works on."""
+    from synth.voronoi_torch import voronoi_batch
+    buf = voronoi_batch(W, H, REGIONS, SIGMA, range(HELD_OUT0, HELD_OUT0 + n))
+    imgs = [buf[i] for i in range(n)]
+    with torch.cuda.stream(stream):
+        bt = gm.SuperpixelsBatch([(H, W)] * n, spacing=LEARN_V, stream=stream)
+        bt.segment(imgs, ITERS)
+    stream.synchronize()
+    before = [x.clone() for x in bt.labels]
+    return (bt, before, buf) if keep_images else (bt, before)
+
+
+def conn_oracle_sample(buf, labels, seconds):
+    """The connectivity oracle, as it stands, on the case's images one at a time for about
+    `seconds` (its CIELAB input from the FP64 conversion of the same sRGB image)."""
+    import oracle
+    from oracle.connectivity import enforce_connectivity
+    K = (W // LEARN_V) * (H // LEARN_V)
+    done, t0 = 0, time.perf_counter()
+    while done < len(labels) and (done == 0 or time.perf_counter() - t0 < seconds):
+        lab = oracle.rgb2lab(buf[done].cpu().numpy()).astype(np.float32)
+        enforce_connectivity(labels[done].cpu().numpy(), lab, K)
+        done += 1
+    secs = time.perf_counter() - t0
+    return done, secs
+
+
+def run_conn_workload(args):
+    """`conn256`: Algorithm 1, step 8 (connectivity post-processing) on the label maps of 256
+    held-out 481x321 images after 10 plain-EM iterations, one call for the whole batch."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    n = 256
+    bt, before, buf = _conn_case(gm, torch, n, stream, keep_images=True)
+
+    def restore():
+        with torch.cuda.stream(stream):
+            for x, y in zip(bt.labels, before):
+                x.copy_(y)
+
+    for _ in range(max(args.warmup, 3)):
+        restore()
+        bt.connectivity()
+    times = []
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            restore()
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = bt.connectivity()        # synchronises the stream at its end
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    pix = n * W * H
+    achieved = pix * CONN_BYTES_PER_PIXEL / (ms * 1e-3) / 1e9
+    peak = measured_peaks().get("hbm_gbs")
+    src = "MEASURED_PEAKS.json hbm_gbs"
+    if not peak:
+        peak, src = 6800.0, "fallback 6.8 TB/s"
+    bt.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        done, secs = conn_oracle_sample(buf, before, args.cpu_seconds)
+        cpu = {"value": round(done * W * H / secs / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} of the {n} label maps in {secs:.1f} s (numpy, one thread; CIELAB conversion "
+                         "included)"}
+    line = {"metric": "Mpixel/s connectivity post-processing (Algorithm 1, step 8)",
+            "value": round(pix / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32 (labels), int64 (fixed-point colour sums), f64",
+            "data": "synthetic",
+            "config": {"workload": f"{n} held-out synthetic 481x321 Voronoi images (150 regions, sigma 8), label maps "
+                                   f"after {ITERS} plain-EM iterations at spacing {LEARN_V}; one "
+                                   "gmmsp_batch_connectivity call per step", "images": n,
+                       "l2": "flushed before every timed step (256 MiB memset); the label maps are restored "
+                             "outside the timed interval"},
+            "components": st["components"], "small": st["small"], "merged": st["merged"],
+            "roofline": {"kernel": f"the whole post-processing call ({CONN_LAUNCHES} kernels)", "bound": "hbm",
+                         "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src,
+                         "algorithmic_bytes_per_pixel": CONN_BYTES_PER_PIXEL},
+            "gpu_launches": CONN_LAUNCHES * args.steps, "clocks": clk.summary(), "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_conn(args):
+    """`--impl reference --workload conn256`: the connectivity oracle on the same label maps,
+    one image per step (the label maps themselves come from the GPU EM)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    bt, before, buf = _conn_case(gm, torch, max(args.steps + args.warmup, 1), stream, keep_images=True)
+    bt.close()
+    conn_oracle_sample(buf[:1], before[:1], 0.0)   # untimed: the oracle's first call
+    done, secs = conn_oracle_sample(buf[args.warmup:], before[args.warmup:], 1e9)
+    v = round(done * W * H / secs / 1e6, 4)
+    print(json.dumps({"impl": "reference", "metric": "Mpixel/s connectivity post-processing (Algorithm 1, step 8)",
+                      "value": v, "unit": UNIT, "n_gpus": 1, "steps": done, "warmup": args.warmup,
+                      "ms_per_step": round(secs / max(done, 1) * 1e3, 3), "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64", "data": "synthetic",
+                      "config": {"workload": "held-out synthetic 481x321 label maps after 10 plain-EM iterations, "
+                                             "one image per step"},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                       "sample": f"{done} images"},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+    return 0
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -794,7 +929,7 @@ def main():
                     help="run a short untimed case for ncu captures and exit")
     ap.add_argument("--warps-per-cell", type=int, default=0, help="with --profile-case: launch shape")
     ap.add_argument("--workload", default="learned481",
-                    choices=["learned481", "481x321", "3840x2160", "batch256"],
+                    choices=["learned481", "481x321", "3840x2160", "batch256", "conn256"],
                     help="learned481 (the headline line); 481x321, 3840x2160 or batch256 (other lines); "
                          "with --profile-case the case to profile")
     ap.add_argument("--images", type=int, default=LEARN_IMAGES, help="learned481: images per step")
@@ -809,6 +944,8 @@ def main():
         return run_profile_case(args)
     if args.workload == "learned481":
         return run_reference_learned(args) if args.impl == "reference" else run_learned(args)
+    if args.workload == "conn256":
+        return run_reference_conn(args) if args.impl == "reference" else run_conn_workload(args)
     if args.workload != "481x321" and args.impl == "gmmsp":
         return run_other_workload(args)
     if args.impl == "reference":

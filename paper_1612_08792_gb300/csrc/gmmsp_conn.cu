@@ -21,10 +21,14 @@
 // find component labelling (k_cc_*), component sizes and colour sums
 // (k_comp_stats), small-component indices (k_small_index), one edge walk
 // (k_edges) three times -- small-small clusters, then the adjacency lists of
-// the small components -- a block scan for the offsets, the cluster member
-// lists (k_cluster_count / _fill), the per-cluster merge (k_cluster_merge)
-// and the relabelling (k_relabel).  One allocation (kept by a context
-// between calls) and one synchronisation per call.
+// the small components -- a three-kernel scan for the offsets (k_scan_*),
+// the cluster member lists as (size, root) sort keys (k_cluster_count /
+// _fill), the per-cluster merge -- one thread per cluster of at most
+// kThreadCluster members (k_cluster_merge), one warp per larger cluster
+// (k_cluster_merge_warp: the keys sorted in shared memory, the neighbours
+// of each member's group scanned by the lanes) -- and the relabelling
+// (k_relabel).  One allocation (kept by a context between calls) and one
+// synchronisation per call.
 // Every loop over a parent chain or a retry is bounded; running out sets the
 // error word (reported as GMMSP_E_TIMEOUT).
 #include <cuda_runtime.h>
@@ -43,7 +47,10 @@ namespace conn {
 
 constexpr int kMaxHops = 1 << 24;      // bound on any parent-chain walk or union retry
 constexpr int kFixedShift = 20;        // colour sums in units of 2^-20
-constexpr int kMaxCluster = 1 << 16;   // bound on the members one cluster thread sorts
+constexpr int kMaxCluster = 1 << 16;   // bound on the members a cluster sorted in global memory may have
+constexpr int kThreadCluster = 16;     // clusters up to this size: one thread; larger: one warp
+constexpr int kWarpSortMax = 1024;     // members a warp sorts in shared memory
+constexpr int kScanTile = 4096;        // elements per block of the scan (1024 threads x 4)
 
 // One image of a call: pixels [off, off + W H) of the call's arrays.
 struct Img {
@@ -66,7 +73,9 @@ struct Scratch {
   int* adj;                   // adjacency lists (roots of neighbouring components)
   int* cl_count;              // per small index: members of the cluster it roots, then fill cursor
   int* cl_off;                // per small index + 1: member offsets
-  int* cl_mem;                // members (small indices), grouped by cluster
+  unsigned long long* cl_key; // members as (size << 32 | root), grouped by cluster
+  int* big;                   // small indices of the roots of clusters above kThreadCluster
+  int* tile_sum;              // scan: per tile sums, then their exclusive prefix
   int* gpar;                  // per root: merge union-find (group founder)
   int* gsize;                 // per root: group size
   int* next;                  // per small root: next member of its group, -1 at the end
@@ -74,6 +83,7 @@ struct Scratch {
   int32_t* in;                // the input labels of all images
   unsigned long long* cnt;    // counters: 0 small, 1 merged, 2 components
   int* nsmall;                // the small count as int (read by later kernels)
+  int* nbig;                  // entries of `big`
   int* err;
 };
 
@@ -169,17 +179,29 @@ __global__ void k_comp_stats(const Img* __restrict__ imgs, const int* __restrict
 
 __device__ __forceinline__ bool small_size(long long s, int K, long long N) { return 4LL * K * s < N; }
 
-// Small components get an index; every root starts its own group.
+// Small components get an index; every root starts its own group.  The
+// counters take one atomic per warp (ballot, then a prefix count per lane).
 __global__ void k_small_index(const Img* __restrict__ imgs, Scratch S) {
+  const int lane = threadIdx.x & 31;
   FOR_PIXELS(im, i) {
     const long long g = im.off + i;
     S.sid[g] = -1;
-    if (S.parent[g] != int(g)) continue;
-    atomicAdd(S.cnt + 2, 1ull);
+    const bool root = S.parent[g] == int(g);
+    const bool small = root && small_size(S.size[g], im.K, im_N);
+    const unsigned act = __activemask();
+    const unsigned mroot = __ballot_sync(act, root), msmall = __ballot_sync(act, small);
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if (lane == leader) {
+      if (mroot) atomicAdd(S.cnt + 2, (unsigned long long)__popc(mroot));
+      if (msmall) base = int(atomicAdd(S.cnt + 0, (unsigned long long)__popc(msmall)));
+    }
+    base = __shfl_sync(act, base, leader);
+    if (!root) continue;
     S.gpar[g] = int(g);
     S.gsize[g] = S.size[g];
-    if (small_size(S.size[g], im.K, im_N)) {
-      const int s = int(atomicAdd(S.cnt + 0, 1ull));
+    if (small) {
+      const int s = base + __popc(msmall & ((1u << lane) - 1u));
       S.sid[g] = s;
       S.sroot[s] = int(g);
       S.simg[s] = int(blockIdx.y);
@@ -226,30 +248,84 @@ __global__ void k_edges(const Img* __restrict__ imgs, Scratch S, int mode) {
   }
 }
 
-// Exclusive prefix sum of the first *np ints of `in` into out[0..*np] (one block).
-__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, const int* __restrict__ np,
-                                               int* __restrict__ out) {
-  __shared__ int part[1024];
-  const int n = *np;
-  const int t = threadIdx.x;
-  const int chunk = (n + 1023) / 1024;
-  const int b = t * chunk, e = min(n, b + chunk);
-  int s = 0;
-  for (int i = b; i < e; ++i) s += in[i];
-  part[t] = s;
+// Exclusive prefix sum of the first n = *np ints of `in` into out[0..n]
+// (out[n] = the total), in three kernels: tile scans (kScanTile elements per
+// block), a scan of the tile sums (one block), the tile offsets added.  The
+// grids cover the largest possible n; blocks past n return at once.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the chunk sums
-    const int v = t >= o ? part[t - o] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
+  if (warp == 0) {
+    int w = lane < int(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_sums[lane] = w;  // inclusive prefix of the warp totals
   }
-  int run = t ? part[t - 1] : 0;
-  for (int i = b; i < e; ++i) {
-    out[i] = run;
-    run += in[i];
+  __syncthreads();
+  total = warp_sums[(blockDim.x >> 5) - 1];
+  const int before = warp ? warp_sums[warp - 1] : 0;
+  __syncthreads();  // warp_sums is reused by the next call
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int* __restrict__ in, const int* __restrict__ np,
+                                                     int* __restrict__ out, int* __restrict__ tile_sum) {
+  __shared__ int warp_sums[32];
+  const int n = *np;
+  const long long base = (long long)blockIdx.x * kScanTile;
+  if (base >= n) return;
+  const long long i0 = base + 4LL * threadIdx.x;
+  int v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = (i0 + j < n) ? in[i0 + j] : 0;
+  const int t = v[0] + v[1] + v[2] + v[3];
+  int total;
+  int run = block_exclusive_scan(t, warp_sums, total);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (i0 + j < n) out[i0 + j] = run;
+    run += v[j];
   }
-  if (t == 1023) out[n] = part[1023];
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tile_sums(int* __restrict__ tile_sum, const int* __restrict__ np,
+                                                         int* __restrict__ out) {
+  __shared__ int warp_sums[32];
+  const int n = *np;
+  const int ntiles = (n + kScanTile - 1) / kScanTile;
+  int carry = 0;
+  for (int c = 0; c < ntiles; c += 1024) {
+    const int i = c + threadIdx.x;
+    const int v = i < ntiles ? tile_sum[i] : 0;
+    int total;
+    const int ex = block_exclusive_scan(v, warp_sums, total);
+    if (i < ntiles) tile_sum[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_add(int* __restrict__ out, const int* __restrict__ tile_sum,
+                                                   const int* __restrict__ np) {
+  const int n = *np;
+  const long long base = (long long)blockIdx.x * kScanTile;
+  if (base >= n || blockIdx.x == 0) return;
+  const int add = tile_sum[blockIdx.x];
+  const long long i0 = base + 4LL * threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (i0 + j < n) out[i0 + j] += add;
 }
 
 // Cluster root of every small component, member counts per cluster root.
@@ -261,11 +337,15 @@ __global__ void k_cluster_count(Scratch S) {
   }
 }
 
+// Members of each cluster as sort keys (size << 32 | root): contiguous per
+// cluster, so that the sort reads and writes no scattered data.
 __global__ void k_cluster_fill(Scratch S) {
   const int n = *S.nsmall;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const int c = S.sid[find_root(S.cpar, S.sroot[s], S.err)];
-    S.cl_mem[S.cl_off[c] + atomicAdd(S.cl_count + c, 1)] = s;
+    const int r = S.sroot[s];
+    const int c = S.sid[find_root(S.cpar, r, S.err)];
+    S.cl_key[S.cl_off[c] + atomicAdd(S.cl_count + c, 1)] =
+        ((unsigned long long)(unsigned)S.size[r] << 32) | (unsigned)r;
   }
 }
 
@@ -281,39 +361,52 @@ __device__ __forceinline__ double dist2(const long long* csum, const int* size, 
   return d;
 }
 
-// One thread per cluster: the sequential rule over the cluster's members in
-// (size, root) order.
+// Merge of small component r (still its group's founder, still small) into
+// the nearest group next to its group, under the sequential rule; the
+// caller has found the nearest (best, or -1 for none).
+__device__ __forceinline__ void merge_into(Scratch& S, int r, int best) {
+  S.gpar[r] = best;
+  atomicAdd(S.gsize + best, S.gsize[r]);  // a large destination may be shared with other clusters
+  S.gsize[r] = 0;
+  if (S.sid[best] >= 0) {  // a small founder keeps the member list of its group
+    S.next[S.tail[best]] = r;
+    S.tail[best] = S.tail[r];
+  }
+}
+
+// Insertion sort of n keys (one thread).
+__device__ __forceinline__ void sort_keys(unsigned long long* key, int n) {
+  for (int a = 1; a < n; ++a) {
+    const unsigned long long v = key[a];
+    int b = a - 1;
+    while (b >= 0 && key[b] > v) {
+      key[b + 1] = key[b];
+      --b;
+    }
+    key[b + 1] = v;
+  }
+}
+
+// One thread per cluster of at most kThreadCluster members: the sequential
+// rule over the members in (size, root) order.  Larger clusters go to the
+// list of the warp kernel.
 __global__ void k_cluster_merge(const Img* __restrict__ imgs, Scratch S) {
   const int nsm = *S.nsmall;
   unsigned merged = 0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsm; s += gridDim.x * blockDim.x) {
     const int r0 = S.sroot[s];
     if (S.cpar[r0] != r0) continue;  // not a cluster root
-    const Img im = imgs[S.simg[s]];
-    const long long N = (long long)im.W * im.H;
-    int* mem = S.cl_mem + S.cl_off[s];
     const int n = S.cl_off[s + 1] - S.cl_off[s];
-    if (n > kMaxCluster) {
-      atomicExch(S.err, 1);
+    if (n > kThreadCluster) {
+      S.big[atomicAdd(S.nbig, 1)] = s;
       continue;
     }
-    // insertion sort of the members by (size, root)
-    for (int a = 1; a < n; ++a) {
-      const int v = mem[a];
-      const int rv = S.sroot[v];
-      const long long kv = ((long long)S.size[rv] << 32) | (unsigned)rv;
-      int b = a - 1;
-      while (b >= 0) {
-        const int rb = S.sroot[mem[b]];
-        const long long kb = ((long long)S.size[rb] << 32) | (unsigned)rb;
-        if (kb <= kv) break;
-        mem[b + 1] = mem[b];
-        --b;
-      }
-      mem[b + 1] = v;
-    }
+    const Img im = imgs[S.simg[s]];
+    const long long N = (long long)im.W * im.H;
+    unsigned long long* key = S.cl_key + S.cl_off[s];
+    sort_keys(key, n);
     for (int a = 0; a < n; ++a) {
-      const int r = S.sroot[mem[a]];
+      const int r = int(unsigned(key[a]));
       if (S.gpar[r] != r || !small_size(S.gsize[r], im.K, N)) continue;
       int best = -1;
       double bd = 0.0;
@@ -332,18 +425,105 @@ __global__ void k_cluster_merge(const Img* __restrict__ imgs, Scratch S) {
       }
       if (hops >= kMaxHops) atomicExch(S.err, 1);
       if (best < 0) continue;
-      S.gpar[r] = best;
-      atomicAdd(S.gsize + best, S.gsize[r]);  // a large destination may be shared with other clusters
-      S.gsize[r] = 0;
-      if (S.sid[best] >= 0) {  // a small founder keeps the member list of its group
-        S.next[S.tail[best]] = r;
-        S.tail[best] = S.tail[r];
-      }
+      merge_into(S, r, best);
       ++merged;
     }
   }
   merged = __reduce_add_sync(0xffffffffu, merged);
   if ((threadIdx.x & 31) == 0 && merged) atomicAdd(S.cnt + 1, (unsigned long long)merged);
+}
+
+// One warp per cluster above kThreadCluster members.  The keys are sorted in
+// shared memory (bitonic; clusters above kWarpSortMax members are sorted in
+// place by one lane), then the members are taken in order as above, with the
+// adjacency entries of each member's group spread over the lanes and the
+// nearest group found by a warp reduction on (distance, group index) -- the
+// same minimum the sequential scan finds.  __syncwarp orders lane 0's merge
+// writes before the next member's reads.
+constexpr int kMergeWarps = 4;
+
+__global__ void __launch_bounds__(kMergeWarps * 32) k_cluster_merge_warp(const Img* __restrict__ imgs, Scratch S) {
+  __shared__ unsigned long long sk[kMergeWarps][kWarpSortMax];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nbig = *S.nbig;
+  unsigned merged = 0;
+  for (int b = blockIdx.x * kMergeWarps + warp; b < nbig; b += gridDim.x * kMergeWarps) {
+    const int s = S.big[b];
+    const Img im = imgs[S.simg[s]];
+    const long long N = (long long)im.W * im.H;
+    unsigned long long* gkey = S.cl_key + S.cl_off[s];
+    const int n = S.cl_off[s + 1] - S.cl_off[s];
+    const unsigned long long* key = sk[warp];
+    if (n <= kWarpSortMax) {
+      int P = 32;
+      while (P < n) P <<= 1;
+      unsigned long long* k = sk[warp];
+      for (int i = lane; i < P; i += 32) k[i] = i < n ? gkey[i] : ~0ull;
+      __syncwarp();
+      for (int w = 2; w <= P; w <<= 1)
+        for (int j = w >> 1; j > 0; j >>= 1) {
+          for (int i = lane; i < P; i += 32) {
+            const int l = i ^ j;
+            if (l > i) {
+              const unsigned long long x = k[i], y = k[l];
+              if ((x > y) == ((i & w) == 0)) {
+                k[i] = y;
+                k[l] = x;
+              }
+            }
+          }
+          __syncwarp();
+        }
+    } else {
+      if (lane == 0) {
+        if (n > kMaxCluster) atomicExch(S.err, 1);
+        else sort_keys(gkey, n);
+      }
+      __syncwarp();
+      if (n > kMaxCluster) continue;
+      key = gkey;
+    }
+    for (int a = 0; a < n; ++a) {
+      const int r = int(unsigned(key[a]));
+      if (S.gpar[r] != r || !small_size(S.gsize[r], im.K, N)) continue;  // warp-uniform
+      int best = 0x7fffffff;
+      double bd = INFINITY;
+      int hops = 0;
+      for (int m = r; m >= 0 && hops < kMaxHops; m = S.next[m], ++hops) {
+        const int sm = S.sid[m];
+        const int q1 = S.aoff[sm + 1];
+        for (int q = S.aoff[sm] + lane; q < q1; q += 32) {
+          const int g = find_root(S.gpar, S.adj[q], S.err);
+          if (g == r) continue;
+          const double d = dist2(S.csum, S.size, r, g);
+          if (d < bd || (d == bd && g < best)) {
+            best = g;
+            bd = d;
+          }
+        }
+      }
+      if (hops >= kMaxHops && lane == 0) atomicExch(S.err, 1);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double d2 = __shfl_xor_sync(0xffffffffu, bd, o);
+        const int g2 = __shfl_xor_sync(0xffffffffu, best, o);
+        if (d2 < bd || (d2 == bd && g2 < best)) {
+          bd = d2;
+          best = g2;
+        }
+      }
+      if (best != 0x7fffffff) {
+        if (lane == 0) {
+          merge_into(S, r, best);
+          ++merged;
+        }
+      }
+      __syncwarp();
+    }
+    __syncwarp();  // sk[warp] is refilled by the next cluster
+  }
+  merged = __reduce_add_sync(0xffffffffu, merged);
+  if (lane == 0 && merged) atomicAdd(S.cnt + 1, (unsigned long long)merged);
 }
 
 __global__ void k_relabel(const Img* __restrict__ imgs, Scratch S) {
@@ -368,7 +548,8 @@ gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const 
   if (T >= (1LL << 30)) return GMMSP_E_INVALID;
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t nI = up(size_t(T) * 4), nI1 = up(size_t(T + 1) * 4);
-  size_t o[20];
+  const long long ntiles = std::max<long long>(1, (T + kScanTile - 1) / kScanTile);
+  size_t o[22];
   size_t off = 0;
   for (int j = 0; j < 14; ++j) { o[j] = off; off += nI; }          // 14 int arrays of T entries
   o[14] = off; off += nI1;                                          // aoff
@@ -377,6 +558,8 @@ gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const 
   o[17] = off; off += up(size_t(T) * 24);                           // csum
   o[18] = off; off += up(sizeof(Img) * n);                          // image table
   o[19] = off; off += 256;                                          // counters
+  o[20] = off; off += up(size_t(T) * 8);                            // cl_key
+  o[21] = off; off += up(size_t(ntiles + 1) * 4);                   // tile_sum
   void* slab = nullptr;
   cudaError_t e = cudaSuccess;
   if (cache && cache->bytes >= off) {
@@ -403,7 +586,7 @@ gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const 
   for (int j = 0; j < 14; ++j) ia[j] = reinterpret_cast<int*>(b + o[j]);
   Scratch S{};
   S.parent = ia[0]; S.size = ia[1]; S.cpar = ia[2]; S.sid = ia[3]; S.sroot = ia[4]; S.simg = ia[5];
-  S.deg = ia[6]; S.cl_count = ia[7]; S.cl_mem = ia[8]; S.gpar = ia[9]; S.gsize = ia[10]; S.next = ia[11];
+  S.deg = ia[6]; S.cl_count = ia[7]; S.big = ia[8]; S.gpar = ia[9]; S.gsize = ia[10]; S.next = ia[11];
   S.tail = ia[12]; S.in = reinterpret_cast<int32_t*>(ia[13]);
   S.aoff = reinterpret_cast<int*>(b + o[14]);
   S.cl_off = reinterpret_cast<int*>(b + o[15]);
@@ -413,6 +596,9 @@ gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const 
   S.cnt = reinterpret_cast<unsigned long long*>(b + o[19]);
   S.nsmall = reinterpret_cast<int*>(b + o[19] + 64);
   S.err = reinterpret_cast<int*>(b + o[19] + 128);
+  S.nbig = reinterpret_cast<int*>(b + o[19] + 192);
+  S.cl_key = reinterpret_cast<unsigned long long*>(b + o[20]);
+  S.tile_sum = reinterpret_cast<int*>(b + o[21]);
   // blocks per image: enough to fill the machine across the images
   const long long per = std::max<long long>(1, std::min<long long>((maxN + 255) / 256, (152LL * 16 + n - 1) / n));
   const dim3 gp{static_cast<unsigned>(per), static_cast<unsigned>(n)};
@@ -434,14 +620,19 @@ gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const 
     k_set_nsmall<<<1, 1, 0, s>>>(S);
     k_edges<<<gp, 256, 0, s>>>(table, S, 0);
     k_edges<<<gp, 256, 0, s>>>(table, S, 1);
-    k_scan<<<1, 1024, 0, s>>>(S.deg, S.nsmall, S.aoff);
+    k_scan_tiles<<<unsigned(ntiles), 1024, 0, s>>>(S.deg, S.nsmall, S.aoff, S.tile_sum);
+    k_scan_tile_sums<<<1, 1024, 0, s>>>(S.tile_sum, S.nsmall, S.aoff);
+    k_scan_add<<<unsigned(ntiles), 1024, 0, s>>>(S.aoff, S.tile_sum, S.nsmall);
     if ((e = cudaMemsetAsync(S.deg, 0, nI, s)) != cudaSuccess) break;
     k_edges<<<gp, 256, 0, s>>>(table, S, 2);
     k_cluster_count<<<gs, 256, 0, s>>>(S);
-    k_scan<<<1, 1024, 0, s>>>(S.cl_count, S.nsmall, S.cl_off);
+    k_scan_tiles<<<unsigned(ntiles), 1024, 0, s>>>(S.cl_count, S.nsmall, S.cl_off, S.tile_sum);
+    k_scan_tile_sums<<<1, 1024, 0, s>>>(S.tile_sum, S.nsmall, S.cl_off);
+    k_scan_add<<<unsigned(ntiles), 1024, 0, s>>>(S.cl_off, S.tile_sum, S.nsmall);
     if ((e = cudaMemsetAsync(S.cl_count, 0, nI, s)) != cudaSuccess) break;
     k_cluster_fill<<<gs, 256, 0, s>>>(S);
     k_cluster_merge<<<gs, 256, 0, s>>>(table, S);
+    k_cluster_merge_warp<<<152 * 4, kMergeWarps * 32, 0, s>>>(table, S);
     k_relabel<<<gp, 256, 0, s>>>(table, S);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(hc, S.cnt, sizeof(hc), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
