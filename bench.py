@@ -791,7 +791,7 @@ def run_profile_case(args):
 # Algorithmic DRAM bytes per pixel of the connectivity post-processing: the input
 # labels (4 B) and CIELAB colour (12 B) read once, the output labels (4 B) written.
 CONN_BYTES_PER_PIXEL = 20
-CONN_LAUNCHES = 20  # kernels of one gmmsp_batch_connectivity call
+CONN_LAUNCHES = 21  # kernels of one gmmsp_batch_connectivity call
 
 
 def _conn_case(gm, torch, n, stream, keep_images=False):

@@ -19,7 +19,8 @@
 //
 // Kernels (all images of a call at once: blockIdx.y is the image): union-
 // find component labelling (k_cc_*), component sizes and colour sums
-// (k_comp_stats), small-component indices (k_small_index), one edge walk
+// (k_comp_stats), small-component indices in pixel order (k_small_count /
+// _scan / _assign), one edge walk
 // (k_edges) three times -- small-small clusters, then the adjacency lists of
 // the small components -- a three-kernel scan for the offsets (k_scan_*),
 // the cluster member lists as (size, root) sort keys (k_cluster_count /
@@ -48,7 +49,7 @@ namespace conn {
 constexpr int kMaxHops = 1 << 24;      // bound on any parent-chain walk or union retry
 constexpr int kFixedShift = 20;        // colour sums in units of 2^-20
 constexpr int kMaxCluster = 1 << 16;   // bound on the members a cluster sorted in global memory may have
-constexpr int kThreadCluster = 16;     // clusters up to this size: one thread; larger: one warp
+constexpr int kThreadCluster = 8;      // clusters up to this size: one thread; larger: one warp
 constexpr int kWarpSortMax = 1024;     // members a warp sorts in shared memory
 constexpr int kScanTile = 4096;        // elements per block of the scan (1024 threads x 4)
 
@@ -112,6 +113,21 @@ __device__ __forceinline__ int find_halve(int* p, int x, int* err) {
   }
   atomicExch(err, 1);
   return x;
+}
+
+// Root of x in the merge union-find, with path compression.  Only the
+// thread or warp that owns a cluster calls it, on that cluster's members and
+// on large components (their own roots), so the compression writes touch no
+// other cluster's nodes; lanes of one warp that compress the same node write
+// the same root.
+__device__ __forceinline__ int find_group(int* p, int x, int* err) {
+  const int r = find_root(p, x, err);
+  for (int h = 0; h < kMaxHops && p[x] != r; ++h) {
+    const int q = p[x];
+    p[x] = r;
+    x = q;
+  }
+  return r;
 }
 
 // Lock-free union by the smaller index (atomicMin on the larger root): the
@@ -179,40 +195,127 @@ __global__ void k_comp_stats(const Img* __restrict__ imgs, const int* __restrict
 
 __device__ __forceinline__ bool small_size(long long s, int K, long long N) { return 4LL * K * s < N; }
 
-// Small components get an index; every root starts its own group.  The
-// counters take one atomic per warp (ballot, then a prefix count per lane).
-__global__ void k_small_index(const Img* __restrict__ imgs, Scratch S) {
-  const int lane = threadIdx.x & 31;
-  FOR_PIXELS(im, i) {
-    const long long g = im.off + i;
-    S.sid[g] = -1;
-    const bool root = S.parent[g] == int(g);
-    const bool small = root && small_size(S.size[g], im.K, im_N);
-    const unsigned act = __activemask();
-    const unsigned mroot = __ballot_sync(act, root), msmall = __ballot_sync(act, small);
-    const int leader = __ffs(act) - 1;
-    int base = 0;
-    if (lane == leader) {
-      if (mroot) atomicAdd(S.cnt + 2, (unsigned long long)__popc(mroot));
-      if (msmall) base = int(atomicAdd(S.cnt + 0, (unsigned long long)__popc(msmall)));
+// Exclusive scan of one int per thread over the block; total = the block sum.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < int(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
-    base = __shfl_sync(act, base, leader);
-    if (!root) continue;
+    warp_sums[lane] = w;  // inclusive prefix of the warp totals
+  }
+  __syncthreads();
+  total = warp_sums[(blockDim.x >> 5) - 1];
+  const int before = warp ? warp_sums[warp - 1] : 0;
+  __syncthreads();  // warp_sums is reused by the next call
+  return before + x - v;
+}
+
+// Image of pixel g of the call (binary search over the images' offsets).
+__device__ __forceinline__ int image_of(const Img* __restrict__ imgs, int n, long long g) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (imgs[mid].off <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Small components get consecutive indices in pixel order, from a count per
+// tile of kScanTile pixels (k_small_count), a scan of the counts
+// (k_small_scan) and the assignment (k_small_assign): no counter that every
+// block updates.  Every root starts its own group.
+__device__ __forceinline__ bool small_root(const Img* __restrict__ imgs, int n, const Scratch& S, long long g,
+                                           int* img) {
+  if (S.parent[g] != int(g)) return false;
+  const int i = image_of(imgs, n, g);
+  *img = i;
+  const Img im = imgs[i];
+  return small_size(S.size[g], im.K, (long long)im.W * im.H);
+}
+
+__global__ void __launch_bounds__(1024) k_small_count(const Img* __restrict__ imgs, int n, long long T, Scratch S) {
+  __shared__ int warp_sums[32];
+  const long long g0 = (long long)blockIdx.x * kScanTile + 4LL * threadIdx.x;
+  int c = 0, roots = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const long long g = g0 + j;
+    if (g >= T) break;
+    S.sid[g] = -1;
+    if (S.parent[g] != int(g)) continue;
+    ++roots;
     S.gpar[g] = int(g);
     S.gsize[g] = S.size[g];
-    if (small) {
-      const int s = base + __popc(msmall & ((1u << lane) - 1u));
-      S.sid[g] = s;
-      S.sroot[s] = int(g);
-      S.simg[s] = int(blockIdx.y);
-      S.cpar[g] = int(g);
-      S.next[g] = -1;
-      S.tail[g] = int(g);
-    }
+    int img;
+    c += small_root(imgs, n, S, g, &img);
+  }
+  int total, total_roots;
+  block_exclusive_scan(c, warp_sums, total);
+  block_exclusive_scan(roots, warp_sums, total_roots);
+  if (threadIdx.x == 0) {
+    S.tile_sum[blockIdx.x] = total;
+    if (total_roots) atomicAdd(S.cnt + 2, (unsigned long long)total_roots);
   }
 }
 
-__global__ void k_set_nsmall(Scratch S) { *S.nsmall = int(S.cnt[0]); }
+// Exclusive scan of the ntiles tile counts in place (one block); the total is
+// the small count.
+__global__ void __launch_bounds__(1024) k_small_scan(int ntiles, Scratch S) {
+  __shared__ int warp_sums[32];
+  int carry = 0;
+  for (int c = 0; c < ntiles; c += 1024) {
+    const int i = c + threadIdx.x;
+    const int v = i < ntiles ? S.tile_sum[i] : 0;
+    int total;
+    const int ex = block_exclusive_scan(v, warp_sums, total);
+    if (i < ntiles) S.tile_sum[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) {
+    *S.nsmall = carry;
+    S.cnt[0] = (unsigned long long)carry;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_small_assign(const Img* __restrict__ imgs, int n, long long T, Scratch S) {
+  __shared__ int warp_sums[32];
+  const long long g0 = (long long)blockIdx.x * kScanTile + 4LL * threadIdx.x;
+  bool f[4];
+  int img[4] = {0, 0, 0, 0};
+  int c = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    f[j] = g0 + j < T && small_root(imgs, n, S, g0 + j, &img[j]);
+    c += f[j];
+  }
+  int total;
+  int s = S.tile_sum[blockIdx.x] + block_exclusive_scan(c, warp_sums, total);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!f[j]) continue;
+    const int g = int(g0 + j);
+    S.sid[g] = s;
+    S.sroot[s] = g;
+    S.simg[s] = img[j];
+    S.cpar[g] = g;
+    S.next[g] = -1;
+    S.tail[g] = g;
+    ++s;
+  }
+}
+
 
 // Walks the 4-neighbour edges between different components; `mode` 0 unites
 // small-small pairs into clusters, 1 counts each small side's adjacency, 2
@@ -252,32 +355,6 @@ __global__ void k_edges(const Img* __restrict__ imgs, Scratch S, int mode) {
 // (out[n] = the total), in three kernels: tile scans (kScanTile elements per
 // block), a scan of the tile sums (one block), the tile offsets added.  The
 // grids cover the largest possible n; blocks past n return at once.
-__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int& total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_sums[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int w = lane < int(blockDim.x >> 5) ? warp_sums[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    warp_sums[lane] = w;  // inclusive prefix of the warp totals
-  }
-  __syncthreads();
-  total = warp_sums[(blockDim.x >> 5) - 1];
-  const int before = warp ? warp_sums[warp - 1] : 0;
-  __syncthreads();  // warp_sums is reused by the next call
-  return before + x - v;
-}
-
 __global__ void __launch_bounds__(1024) k_scan_tiles(const int* __restrict__ in, const int* __restrict__ np,
                                                      int* __restrict__ out, int* __restrict__ tile_sum) {
   __shared__ int warp_sums[32];
@@ -414,7 +491,7 @@ __global__ void k_cluster_merge(const Img* __restrict__ imgs, Scratch S) {
       for (int m = r; m >= 0 && hops < kMaxHops; m = S.next[m], ++hops) {
         const int sm = S.sid[m];
         for (int q = S.aoff[sm]; q < S.aoff[sm + 1]; ++q) {
-          const int g = find_root(S.gpar, S.adj[q], S.err);
+          const int g = find_group(S.gpar, S.adj[q], S.err);
           if (g == r) continue;
           const double d = dist2(S.csum, S.size, r, g);
           if (best < 0 || d < bd || (d == bd && g < best)) {
@@ -493,7 +570,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) k_cluster_merge_warp(const I
         const int sm = S.sid[m];
         const int q1 = S.aoff[sm + 1];
         for (int q = S.aoff[sm] + lane; q < q1; q += 32) {
-          const int g = find_root(S.gpar, S.adj[q], S.err);
+          const int g = find_group(S.gpar, S.adj[q], S.err);
           if (g == r) continue;
           const double d = dist2(S.csum, S.size, r, g);
           if (d < bd || (d == bd && g < best)) {
@@ -616,8 +693,9 @@ gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const 
     k_cc_union<<<gp, 256, 0, s>>>(table, S.in, S.parent, S.err);
     k_cc_flatten<<<gp, 256, 0, s>>>(table, S.parent, S.err);
     k_comp_stats<<<gp, 256, 0, s>>>(table, S.parent, S.size, S.csum);
-    k_small_index<<<gp, 256, 0, s>>>(table, S);
-    k_set_nsmall<<<1, 1, 0, s>>>(S);
+    k_small_count<<<unsigned(ntiles), 1024, 0, s>>>(table, n, T, S);
+    k_small_scan<<<1, 1024, 0, s>>>(int(ntiles), S);
+    k_small_assign<<<unsigned(ntiles), 1024, 0, s>>>(table, n, T, S);
     k_edges<<<gp, 256, 0, s>>>(table, S, 0);
     k_edges<<<gp, 256, 0, s>>>(table, S, 1);
     k_scan_tiles<<<unsigned(ntiles), 1024, 0, s>>>(S.deg, S.nsmall, S.aoff, S.tile_sum);
