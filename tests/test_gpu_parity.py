@@ -256,3 +256,31 @@ def test_4k_matches_oracle(gm):
     assert parity.cov_rel_err(got["cc"], ref.theta.cc) <= parity.COV_TOL
     agree, ndiff, worst = parity.label_report(got["labels"], ref.labels, ref.margin)
     assert agree >= parity.LABEL_AGREE and worst < parity.MARGIN_TOL, (agree, ndiff, worst)
+
+
+@pytest.mark.parametrize("colour", ["full", "split", "gray"])
+@pytest.mark.parametrize("W,H,R,seed,K,sp", [(37, 23, 4, 3, 0, 6), (97, 61, 8, 5, 0, 7), (481, 321, 150, 7, 0, 15),
+                                             (320, 240, 40, 8, 0, 12)])
+def test_argmax_only_labels_equal_full_scan(gm, colour, W, H, R, seed, K, sp):
+    """Without a log-likelihood the label pass skips candidates whose spatial bound
+    cannot reach the best value; its labels must equal those of the full scan."""
+    import torch
+    _, lab32 = lab_input(W, H, R, 8.0, seed)
+    ctx = gm.Superpixels(torch.from_numpy(lab32).cuda(), K=K, spacing=sp, colour=colour)
+    for t in (0, 2, 5):
+        if t:
+            ctx.em_iters(t - (0 if t == 2 else 2))
+        full, _ = ctx.labels(want_loglik=True)
+        fast = ctx.labels()
+        torch.testing.assert_close(fast, full, rtol=0, atol=0)
+    ctx.close()
+    # and in a batch of uneven sizes
+    imgs = [torch.from_numpy(lab_input(w, h, max(4, w * h // 1000), 8.0, 40 + i)[1]).cuda()
+            for i, (w, h) in enumerate([(W, H), (160, 120), (W, H)])]
+    bt = gm.SuperpixelsBatch([(x.shape[0], x.shape[1]) for x in imgs], spacing=sp or 12, lab_input=True,
+                             colour=colour)
+    a = [x.clone() for x in bt.segment(imgs, iters=3)]
+    b, _ = bt.segment(imgs, iters=3, want_loglik=True)
+    for x, y in zip(a, b):
+        torch.testing.assert_close(x, y, rtol=0, atol=0)
+    bt.close()
