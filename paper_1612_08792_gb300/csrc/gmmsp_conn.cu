@@ -15,23 +15,33 @@
 // small components split into clusters (connected sets of the small-small
 // adjacency), and the sequential rule restricted to one cluster, in the
 // cluster's own (size, index) order, gives exactly what the sequential pass
-// over the whole image gives there.  One thread runs each cluster.
+// over the whole image gives there.  One thread (or one warp) runs each
+// cluster.
 //
-// Kernels (all images of a call at once: blockIdx.y is the image): union-
-// find component labelling (k_cc_*), component sizes and colour sums
-// (k_comp_stats), small-component indices in pixel order (k_small_count /
-// _scan / _assign), one edge walk
-// (k_edges) three times -- small-small clusters, then the adjacency lists of
-// the small components -- a three-kernel scan for the offsets (k_scan_*),
-// the cluster member lists as (size, root) sort keys (k_cluster_count /
-// _fill), the per-cluster merge -- one thread per cluster of at most
-// kThreadCluster members (k_cluster_merge), one warp per larger cluster
-// (k_cluster_merge_warp: the keys sorted in shared memory, the neighbours
-// of each member's group scanned by the lanes) -- and the relabelling
-// (k_relabel).  One allocation (kept by a context between calls) and one
-// synchronisation per call.
-// Every loop over a parent chain or a retry is bounded; running out sets the
-// error word (reported as GMMSP_E_TIMEOUT).
+// Data layout.  After the pixel-level labelling every component gets a
+// compact index c in the order of its smallest pixel (so ordering by c is
+// ordering by that pixel), and every per-component array is indexed by c:
+// about 1.6 M entries for 256 images of 481x321, a few MB each, which the
+// L2 keeps while the merge reads them at random.
+//
+// Kernels (all images of a call at once; pixel loops take blockIdx.y as the
+// image, tile loops cover all pixels of the call):
+//   k_cc_init / _union / _flatten   union-find labelling, parent = root pixel
+//   k_root_count / _scan / _assign  compact index per root (tile counts, scan)
+//   k_comp_map                      parent := compact index; sizes and
+//                                   fixed-point colour sums (atomics)
+//   k_comp_flags                    small flag, mean colour, group state per component
+//   k_edges (x2)                    small-small clusters and adjacency counts;
+//                                   adjacency lists (of the small components)
+//   k_scan_tiles / _tile_sums / _add  offsets (twice)
+//   k_cluster_count / _fill         member lists as (size << 32 | c) keys
+//   k_cluster_merge                 one thread per cluster of <= kThreadCluster
+//   k_cluster_merge_warp            one warp per larger cluster (keys sorted
+//                                   in shared memory, adjacency over the lanes)
+//   k_relabel                       label of the group founder
+// One allocation (kept by a context between calls) and one synchronisation
+// per call.  Every loop over a parent chain or a retry is bounded; running
+// out sets the error word (reported as GMMSP_E_TIMEOUT).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -51,39 +61,43 @@ constexpr int kFixedShift = 20;        // colour sums in units of 2^-20
 constexpr int kMaxCluster = 1 << 16;   // bound on the members a cluster sorted in global memory may have
 constexpr int kThreadCluster = 8;      // clusters up to this size: one thread; larger: one warp
 constexpr int kWarpSortMax = 1024;     // members a warp sorts in shared memory
-constexpr int kScanTile = 4096;        // elements per block of the scan (1024 threads x 4)
+constexpr int kScanTile = 4096;        // elements per block of the tile kernels (1024 threads x 4)
+constexpr int kMergeWarps = 4;
 
 // One image of a call: pixels [off, off + W H) of the call's arrays.
 struct Img {
   int W, H, K;
   long long off;
   const float* lab;   // three FP32 planes of W H values
-  int32_t* labels;    // the caller's labels (rewritten)
+  int32_t* labels;    // the caller's labels (read, then rewritten by k_relabel)
 };
 
 struct Scratch {
-  int* parent;                // per pixel: component union-find, then the component root
-  int* size;                  // per root: component size
-  long long* csum;            // per root: 3 fixed-point colour sums
-  int* cpar;                  // per small root: cluster union-find over roots
-  int* sid;                   // per root: index of the small component, or -1
-  int* sroot;                 // per small index: its root
-  int* simg;                  // per small index: its image
-  int* deg;                   // per small index: adjacency count, then fill cursor
-  int* aoff;                  // per small index + 1: adjacency offsets
-  int* adj;                   // adjacency lists (roots of neighbouring components)
-  int* cl_count;              // per small index: members of the cluster it roots, then fill cursor
-  int* cl_off;                // per small index + 1: member offsets
-  unsigned long long* cl_key; // members as (size << 32 | root), grouped by cluster
-  int* big;                   // small indices of the roots of clusters above kThreadCluster
-  int* tile_sum;              // scan: per tile sums, then their exclusive prefix
-  int* gpar;                  // per root: merge union-find (group founder)
-  int* gsize;                 // per root: group size
-  int* next;                  // per small root: next member of its group, -1 at the end
-  int* tail;                  // per small root founding a group: last member
-  int32_t* in;                // the input labels of all images
+  // per pixel of the call
+  int* parent;                // union-find, then the root pixel, then the compact index
+  int* cidr;                  // at root pixels: the compact index
+  // per component (compact index c < ncomp)
+  int* size;                  // pixel count
+  long long* csum;            // 3 fixed-point colour sums, then (k_comp_flags) ...
+  double* mean;               // ... the 3 mean colours csum / size, in the same memory
+  int* cimg;                  // image
+  int32_t* clabel;            // its label
+  int* small;                 // 1 for a small component
+  int* cpar;                  // cluster union-find over small components
+  int* deg;                   // adjacency count, then fill cursor
+  int* aoff;                  // (ncomp + 1) adjacency offsets
+  int* adj;                   // adjacency lists (compact indices of neighbouring components)
+  int* cl_count;              // members of the cluster it roots, then fill cursor
+  int* cl_off;                // (ncomp + 1) member offsets
+  unsigned long long* cl_key; // members as (size << 32 | c), grouped by cluster
+  int* big;                   // roots of clusters above kThreadCluster members
+  int* gpar;                  // merge union-find (group founder)
+  int* gsize;                 // group size (kept for small founders)
+  int* next;                  // next member of its group, -1 at the end
+  int* tail;                  // of a group's founder: its last member
+  int* tile_sum;              // tile kernels: per tile counts, then their exclusive prefix
   unsigned long long* cnt;    // counters: 0 small, 1 merged, 2 components
-  int* nsmall;                // the small count as int (read by later kernels)
+  int* ncomp;                 // the component count as int (read by later kernels)
   int* nbig;                  // entries of `big`
   int* err;
 };
@@ -98,7 +112,7 @@ __device__ __forceinline__ int find_root(const int* p, int x, int* err) {
   return x;
 }
 
-// Root of x with path halving, for the union phase: every visited node is
+// Root of x with path halving, for the union phases: every visited node is
 // re-pointed at its grandparent, an ancestor in the same set, so no set
 // changes; a concurrent link that such a store overwrites is redone by that
 // link's own retry.
@@ -150,6 +164,8 @@ __device__ __forceinline__ void unite(int* p, int a, int b, int* err) {
   atomicExch(err, 1);
 }
 
+__device__ __forceinline__ bool small_size(long long s, int K, long long N) { return 4LL * K * s < N; }
+
 // Per-image pixel loops: blockIdx.y is the image, x strides over its pixels.
 #define FOR_PIXELS(im, i)                                                                    \
   const Img im = imgs[blockIdx.y];                                                           \
@@ -157,19 +173,22 @@ __device__ __forceinline__ void unite(int* p, int a, int b, int* err) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < im##_N;           \
        i += (long long)gridDim.x * blockDim.x)
 
-__global__ void k_cc_init(const Img* __restrict__ imgs, int* __restrict__ p, int32_t* __restrict__ in) {
-  FOR_PIXELS(im, i) {
-    p[im.off + i] = int(im.off + i);
-    in[im.off + i] = im.labels[i];
-  }
+// Per-component loops over c < *S.ncomp.
+#define FOR_COMPONENTS(c)      \
+  const int ncomp_ = *S.ncomp; \
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp_; c += gridDim.x * blockDim.x)
+
+__global__ void k_cc_init(const Img* __restrict__ imgs, int* __restrict__ p) {
+  FOR_PIXELS(im, i) p[im.off + i] = int(im.off + i);
 }
 
-__global__ void k_cc_union(const Img* __restrict__ imgs, const int32_t* __restrict__ in, int* p, int* err) {
+__global__ void k_cc_union(const Img* __restrict__ imgs, int* p, int* err) {
   FOR_PIXELS(im, i) {
     const int y = int(i / im.W), x = int(i - (long long)y * im.W);
     const long long g = im.off + i;
-    if (x + 1 < im.W && in[g] == in[g + 1]) unite(p, int(g), int(g + 1), err);
-    if (y + 1 < im.H && in[g] == in[g + im.W]) unite(p, int(g), int(g + im.W), err);
+    const int32_t l = im.labels[i];
+    if (x + 1 < im.W && l == im.labels[i + 1]) unite(p, int(g), int(g + 1), err);
+    if (y + 1 < im.H && l == im.labels[i + im.W]) unite(p, int(g), int(g + im.W), err);
   }
 }
 
@@ -179,21 +198,6 @@ __global__ void k_cc_union(const Img* __restrict__ imgs, const int32_t* __restri
 __global__ void k_cc_flatten(const Img* __restrict__ imgs, int* p, int* err) {
   FOR_PIXELS(im, i) p[im.off + i] = find_root(p, int(im.off + i), err);
 }
-
-__global__ void k_comp_stats(const Img* __restrict__ imgs, const int* __restrict__ p, int* __restrict__ size,
-                             long long* __restrict__ csum) {
-  FOR_PIXELS(im, i) {
-    const int r = p[im.off + i];
-    atomicAdd(size + r, 1);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const long long f = llrint(double(im.lab[c * im_N + i]) * double(1 << kFixedShift));
-      atomicAdd(reinterpret_cast<unsigned long long*>(csum + 3LL * r + c), (unsigned long long)f);
-    }
-  }
-}
-
-__device__ __forceinline__ bool small_size(long long s, int K, long long N) { return 4LL * K * s < N; }
 
 // Exclusive scan of one int per thread over the block; total = the block sum.
 __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int& total) {
@@ -232,47 +236,23 @@ __device__ __forceinline__ int image_of(const Img* __restrict__ imgs, int n, lon
   return lo;
 }
 
-// Small components get consecutive indices in pixel order, from a count per
-// tile of kScanTile pixels (k_small_count), a scan of the counts
-// (k_small_scan) and the assignment (k_small_assign): no counter that every
-// block updates.  Every root starts its own group.
-__device__ __forceinline__ bool small_root(const Img* __restrict__ imgs, int n, const Scratch& S, long long g,
-                                           int* img) {
-  if (S.parent[g] != int(g)) return false;
-  const int i = image_of(imgs, n, g);
-  *img = i;
-  const Img im = imgs[i];
-  return small_size(S.size[g], im.K, (long long)im.W * im.H);
-}
-
-__global__ void __launch_bounds__(1024) k_small_count(const Img* __restrict__ imgs, int n, long long T, Scratch S) {
+// Compact indices of the components in the order of their roots (smallest
+// pixels): a count per tile of kScanTile pixels, a scan of the counts, the
+// assignment.  No counter that every block updates.
+__global__ void __launch_bounds__(1024) k_root_count(long long T, Scratch S) {
   __shared__ int warp_sums[32];
   const long long g0 = (long long)blockIdx.x * kScanTile + 4LL * threadIdx.x;
-  int c = 0, roots = 0;
+  int c = 0;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const long long g = g0 + j;
-    if (g >= T) break;
-    S.sid[g] = -1;
-    if (S.parent[g] != int(g)) continue;
-    ++roots;
-    S.gpar[g] = int(g);
-    S.gsize[g] = S.size[g];
-    int img;
-    c += small_root(imgs, n, S, g, &img);
-  }
-  int total, total_roots;
+  for (int j = 0; j < 4; ++j) c += (g0 + j < T && S.parent[g0 + j] == int(g0 + j));
+  int total;
   block_exclusive_scan(c, warp_sums, total);
-  block_exclusive_scan(roots, warp_sums, total_roots);
-  if (threadIdx.x == 0) {
-    S.tile_sum[blockIdx.x] = total;
-    if (total_roots) atomicAdd(S.cnt + 2, (unsigned long long)total_roots);
-  }
+  if (threadIdx.x == 0) S.tile_sum[blockIdx.x] = total;
 }
 
-// Exclusive scan of the ntiles tile counts in place (one block); the total is
-// the small count.
-__global__ void __launch_bounds__(1024) k_small_scan(int ntiles, Scratch S) {
+// Exclusive scan of the ntiles tile counts in place (one block); the total
+// is the component count.
+__global__ void __launch_bounds__(1024) k_root_scan(int ntiles, Scratch S) {
   __shared__ int warp_sums[32];
   int carry = 0;
   for (int c = 0; c < ntiles; c += 1024) {
@@ -284,47 +264,113 @@ __global__ void __launch_bounds__(1024) k_small_scan(int ntiles, Scratch S) {
     carry += total;
   }
   if (threadIdx.x == 0) {
-    *S.nsmall = carry;
-    S.cnt[0] = (unsigned long long)carry;
+    *S.ncomp = carry;
+    S.cnt[2] = (unsigned long long)carry;
   }
 }
 
-__global__ void __launch_bounds__(1024) k_small_assign(const Img* __restrict__ imgs, int n, long long T, Scratch S) {
+__global__ void __launch_bounds__(1024) k_root_assign(const Img* __restrict__ imgs, int n, long long T, Scratch S) {
   __shared__ int warp_sums[32];
   const long long g0 = (long long)blockIdx.x * kScanTile + 4LL * threadIdx.x;
   bool f[4];
-  int img[4] = {0, 0, 0, 0};
-  int c = 0;
+  int cnt = 0;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    f[j] = g0 + j < T && small_root(imgs, n, S, g0 + j, &img[j]);
-    c += f[j];
+    f[j] = g0 + j < T && S.parent[g0 + j] == int(g0 + j);
+    cnt += f[j];
   }
   int total;
-  int s = S.tile_sum[blockIdx.x] + block_exclusive_scan(c, warp_sums, total);
+  int c = S.tile_sum[blockIdx.x] + block_exclusive_scan(cnt, warp_sums, total);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (!f[j]) continue;
-    const int g = int(g0 + j);
-    S.sid[g] = s;
-    S.sroot[s] = g;
-    S.simg[s] = img[j];
-    S.cpar[g] = g;
-    S.next[g] = -1;
-    S.tail[g] = g;
-    ++s;
+    const long long g = g0 + j;
+    const int i = image_of(imgs, n, g);
+    S.cidr[g] = c;
+    S.cimg[c] = i;
+    S.clabel[c] = imgs[i].labels[g - imgs[i].off];
+    ++c;
   }
 }
 
+// parent := compact index of the pixel's component; component sizes and
+// fixed-point colour sums.  A warp takes 32 consecutive pixels; the lanes of
+// a run of equal components (a row segment of one component) add their
+// values to the run's first lane (a segmented reduction by shuffles), which
+// alone updates the sums: one set of atomics per run instead of per pixel.
+__global__ void k_comp_map(const Img* __restrict__ imgs, Scratch S) {
+  const Img im = imgs[blockIdx.y];
+  const long long N = (long long)im.W * im.H;
+  const int lane = threadIdx.x & 31;
+  const long long step = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i - lane < N; i += step) {
+    const bool valid = i < N;  // warp-uniform loop: every lane takes part in the shuffles
+    int c = -1 - lane;         // distinct for invalid lanes: they form runs of their own
+    long long v[4] = {0, 0, 0, 0};
+    if (valid) {
+      const long long g = im.off + i;
+      c = S.cidr[S.parent[g]];
+      S.parent[g] = c;
+      v[0] = 1;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)  // z 2^20 is exact in FP32 (a power-of-two scaling): round(2^20 z)
+        v[1 + k] = __float2ll_rn(im.lab[k * N + i] * float(1 << kFixedShift));
+    }
+    const int cprev = __shfl_up_sync(0xffffffffu, c, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || cprev != c);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of my run
+    const int run_end = (heads & (0xfffffffeu << lane)) ? __ffs(heads & (0xfffffffeu << lane)) - 1 : 32;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const long long w = __shfl_down_sync(0xffffffffu, v[k], o);
+        if (lane + o < run_end) v[k] += w;
+      }
+    }
+    if (valid && lane == start) {
+      atomicAdd(S.size + c, int(v[0]));
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        atomicAdd(reinterpret_cast<unsigned long long*>(S.csum + 3LL * c + k), (unsigned long long)v[1 + k]);
+    }
+  }
+}
+
+// Small flag, mean colour (the FP64 quotient csum / size, written over the
+// sums) and the initial group state of every component (each is its own
+// group); the small count takes one atomic per block.
+__global__ void __launch_bounds__(256) k_comp_flags(const Img* __restrict__ imgs, Scratch S) {
+  const int ncomp = *S.ncomp;
+  for (int base = blockIdx.x * blockDim.x; base < ncomp; base += gridDim.x * blockDim.x) {
+    const int c = base + threadIdx.x;
+    bool sm = false;
+    if (c < ncomp) {
+      const Img im = imgs[S.cimg[c]];
+      const int sz = S.size[c];
+      sm = small_size(sz, im.K, (long long)im.W * im.H);
+      S.small[c] = sm ? 1 : 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) S.mean[3LL * c + k] = double(S.csum[3LL * c + k]) / double(sz);
+      S.gpar[c] = c;
+      S.gsize[c] = sz;
+      S.cpar[c] = c;
+      S.next[c] = -1;
+      S.tail[c] = c;
+    }
+    const int nsm = __syncthreads_count(sm);
+    if (threadIdx.x == 0 && nsm) atomicAdd(S.cnt + 0, (unsigned long long)nsm);
+  }
+}
 
 // Walks the 4-neighbour edges between different components; `mode` 0 unites
-// small-small pairs into clusters, 1 counts each small side's adjacency, 2
-// fills it.
+// small-small pairs into clusters and counts each small side's adjacency, 1
+// fills the adjacency lists.
 __global__ void k_edges(const Img* __restrict__ imgs, Scratch S, int mode) {
   FOR_PIXELS(im, i) {
     const int y = int(i / im.W), x = int(i - (long long)y * im.W);
     const long long g = im.off + i;
-    const int ri = S.parent[g];
+    const int ci = S.parent[g];
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
       long long j;
@@ -335,17 +381,16 @@ __global__ void k_edges(const Img* __restrict__ imgs, Scratch S, int mode) {
         if (y + 1 >= im.H) continue;
         j = g + im.W;
       }
-      const int rj = S.parent[j];
-      if (ri == rj) continue;
-      const int si = S.sid[ri], sj = S.sid[rj];
+      const int cj = S.parent[j];
+      if (ci == cj) continue;
+      const int si = S.small[ci], sj = S.small[cj];
       if (mode == 0) {
-        if (si >= 0 && sj >= 0) unite(S.cpar, ri, rj, S.err);
-      } else if (mode == 1) {
-        if (si >= 0) atomicAdd(S.deg + si, 1);
-        if (sj >= 0) atomicAdd(S.deg + sj, 1);
+        if (si && sj) unite(S.cpar, ci, cj, S.err);
+        if (si) atomicAdd(S.deg + ci, 1);
+        if (sj) atomicAdd(S.deg + cj, 1);
       } else {
-        if (si >= 0) S.adj[S.aoff[si] + atomicAdd(S.deg + si, 1)] = rj;
-        if (sj >= 0) S.adj[S.aoff[sj] + atomicAdd(S.deg + sj, 1)] = ri;
+        if (si) S.adj[S.aoff[ci] + atomicAdd(S.deg + ci, 1)] = cj;
+        if (sj) S.adj[S.aoff[cj] + atomicAdd(S.deg + cj, 1)] = ci;
       }
     }
   }
@@ -407,48 +452,47 @@ __global__ void __launch_bounds__(1024) k_scan_add(int* __restrict__ out, const 
 
 // Cluster root of every small component, member counts per cluster root.
 __global__ void k_cluster_count(Scratch S) {
-  const int n = *S.nsmall;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const int c = find_root(S.cpar, S.sroot[s], S.err);
-    atomicAdd(S.cl_count + S.sid[c], 1);
+  FOR_COMPONENTS(c) {
+    if (!S.small[c]) continue;
+    atomicAdd(S.cl_count + find_root(S.cpar, c, S.err), 1);
   }
 }
 
-// Members of each cluster as sort keys (size << 32 | root): contiguous per
+// Members of each cluster as sort keys (size << 32 | c): contiguous per
 // cluster, so that the sort reads and writes no scattered data.
 __global__ void k_cluster_fill(Scratch S) {
-  const int n = *S.nsmall;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const int r = S.sroot[s];
-    const int c = S.sid[find_root(S.cpar, r, S.err)];
-    S.cl_key[S.cl_off[c] + atomicAdd(S.cl_count + c, 1)] =
-        ((unsigned long long)(unsigned)S.size[r] << 32) | (unsigned)r;
+  FOR_COMPONENTS(c) {
+    if (!S.small[c]) continue;
+    const int r = find_root(S.cpar, c, S.err);
+    S.cl_key[S.cl_off[r] + atomicAdd(S.cl_count + r, 1)] =
+        ((unsigned long long)(unsigned)S.size[c] << 32) | unsigned(c);
   }
 }
 
-__device__ __forceinline__ double dist2(const long long* csum, const int* size, int a, int b) {
+// Squared distance of the mean colours of components a and b, in a fixed
+// order without contractions.
+__device__ __forceinline__ double dist2(const double* mean, int a, int b) {
   double d = 0.0;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const double ma = double(csum[3LL * a + c]) / double(size[a]);
-    const double mb = double(csum[3LL * b + c]) / double(size[b]);
-    const double t = __dsub_rn(ma, mb);
+  for (int k = 0; k < 3; ++k) {
+    const double t = __dsub_rn(mean[3LL * a + k], mean[3LL * b + k]);
     d = __dadd_rn(d, __dmul_rn(t, t));
   }
   return d;
 }
 
 // Merge of small component r (still its group's founder, still small) into
-// the nearest group next to its group, under the sequential rule; the
-// caller has found the nearest (best, or -1 for none).
+// the nearest group `best` next to its group.  A small destination belongs
+// to the same cluster and gets r's size and members; a large destination is
+// never a source, and no decision reads its size.
 __device__ __forceinline__ void merge_into(Scratch& S, int r, int best) {
   S.gpar[r] = best;
-  atomicAdd(S.gsize + best, S.gsize[r]);  // a large destination may be shared with other clusters
-  S.gsize[r] = 0;
-  if (S.sid[best] >= 0) {  // a small founder keeps the member list of its group
+  if (S.small[best]) {
+    S.gsize[best] += S.gsize[r];
     S.next[S.tail[best]] = r;
     S.tail[best] = S.tail[r];
   }
+  S.gsize[r] = 0;
 }
 
 // Insertion sort of n keys (one thread).
@@ -465,22 +509,20 @@ __device__ __forceinline__ void sort_keys(unsigned long long* key, int n) {
 }
 
 // One thread per cluster of at most kThreadCluster members: the sequential
-// rule over the members in (size, root) order.  Larger clusters go to the
+// rule over the members in (size, index) order.  Larger clusters go to the
 // list of the warp kernel.
 __global__ void k_cluster_merge(const Img* __restrict__ imgs, Scratch S) {
-  const int nsm = *S.nsmall;
   unsigned merged = 0;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsm; s += gridDim.x * blockDim.x) {
-    const int r0 = S.sroot[s];
-    if (S.cpar[r0] != r0) continue;  // not a cluster root
-    const int n = S.cl_off[s + 1] - S.cl_off[s];
+  FOR_COMPONENTS(c) {
+    if (!S.small[c] || S.cpar[c] != c) continue;  // not a cluster root
+    const int n = S.cl_off[c + 1] - S.cl_off[c];
     if (n > kThreadCluster) {
-      S.big[atomicAdd(S.nbig, 1)] = s;
+      S.big[atomicAdd(S.nbig, 1)] = c;
       continue;
     }
-    const Img im = imgs[S.simg[s]];
+    const Img im = imgs[S.cimg[c]];
     const long long N = (long long)im.W * im.H;
-    unsigned long long* key = S.cl_key + S.cl_off[s];
+    unsigned long long* key = S.cl_key + S.cl_off[c];
     sort_keys(key, n);
     for (int a = 0; a < n; ++a) {
       const int r = int(unsigned(key[a]));
@@ -489,11 +531,10 @@ __global__ void k_cluster_merge(const Img* __restrict__ imgs, Scratch S) {
       double bd = 0.0;
       int hops = 0;
       for (int m = r; m >= 0 && hops < kMaxHops; m = S.next[m], ++hops) {
-        const int sm = S.sid[m];
-        for (int q = S.aoff[sm]; q < S.aoff[sm + 1]; ++q) {
+        for (int q = S.aoff[m]; q < S.aoff[m + 1]; ++q) {
           const int g = find_group(S.gpar, S.adj[q], S.err);
           if (g == r) continue;
-          const double d = dist2(S.csum, S.size, r, g);
+          const double d = dist2(S.mean, r, g);
           if (best < 0 || d < bd || (d == bd && g < best)) {
             best = g;
             bd = d;
@@ -517,19 +558,17 @@ __global__ void k_cluster_merge(const Img* __restrict__ imgs, Scratch S) {
 // nearest group found by a warp reduction on (distance, group index) -- the
 // same minimum the sequential scan finds.  __syncwarp orders lane 0's merge
 // writes before the next member's reads.
-constexpr int kMergeWarps = 4;
-
 __global__ void __launch_bounds__(kMergeWarps * 32) k_cluster_merge_warp(const Img* __restrict__ imgs, Scratch S) {
   __shared__ unsigned long long sk[kMergeWarps][kWarpSortMax];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nbig = *S.nbig;
   unsigned merged = 0;
   for (int b = blockIdx.x * kMergeWarps + warp; b < nbig; b += gridDim.x * kMergeWarps) {
-    const int s = S.big[b];
-    const Img im = imgs[S.simg[s]];
+    const int c = S.big[b];
+    const Img im = imgs[S.cimg[c]];
     const long long N = (long long)im.W * im.H;
-    unsigned long long* gkey = S.cl_key + S.cl_off[s];
-    const int n = S.cl_off[s + 1] - S.cl_off[s];
+    unsigned long long* gkey = S.cl_key + S.cl_off[c];
+    const int n = S.cl_off[c + 1] - S.cl_off[c];
     const unsigned long long* key = sk[warp];
     if (n <= kWarpSortMax) {
       int P = 32;
@@ -567,12 +606,11 @@ __global__ void __launch_bounds__(kMergeWarps * 32) k_cluster_merge_warp(const I
       double bd = INFINITY;
       int hops = 0;
       for (int m = r; m >= 0 && hops < kMaxHops; m = S.next[m], ++hops) {
-        const int sm = S.sid[m];
-        const int q1 = S.aoff[sm + 1];
-        for (int q = S.aoff[sm] + lane; q < q1; q += 32) {
+        const int q1 = S.aoff[m + 1];
+        for (int q = S.aoff[m] + lane; q < q1; q += 32) {
           const int g = find_group(S.gpar, S.adj[q], S.err);
           if (g == r) continue;
-          const double d = dist2(S.csum, S.size, r, g);
+          const double d = dist2(S.mean, r, g);
           if (d < bd || (d == bd && g < best)) {
             best = g;
             bd = d;
@@ -589,11 +627,9 @@ __global__ void __launch_bounds__(kMergeWarps * 32) k_cluster_merge_warp(const I
           best = g2;
         }
       }
-      if (best != 0x7fffffff) {
-        if (lane == 0) {
-          merge_into(S, r, best);
-          ++merged;
-        }
+      if (best != 0x7fffffff && lane == 0) {
+        merge_into(S, r, best);
+        ++merged;
       }
       __syncwarp();
     }
@@ -604,7 +640,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) k_cluster_merge_warp(const I
 }
 
 __global__ void k_relabel(const Img* __restrict__ imgs, Scratch S) {
-  FOR_PIXELS(im, i) im.labels[i] = S.in[find_root(S.gpar, S.parent[im.off + i], S.err)];
+  FOR_PIXELS(im, i) im.labels[i] = S.clabel[find_root(S.gpar, S.parent[im.off + i], S.err)];
 }
 
 }  // namespace conn
@@ -624,19 +660,23 @@ gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const 
   }
   if (T >= (1LL << 30)) return GMMSP_E_INVALID;
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  // every per-component array has room for T components (one per pixel at most)
   const size_t nI = up(size_t(T) * 4), nI1 = up(size_t(T + 1) * 4);
   const long long ntiles = std::max<long long>(1, (T + kScanTile - 1) / kScanTile);
-  size_t o[22];
+  enum { A_PARENT, A_CIDR, A_SIZE, A_CIMG, A_CLABEL, A_SMALL, A_CPAR, A_DEG, A_CLCOUNT, A_BIG, A_GPAR, A_GSIZE,
+         A_NEXT, A_TAIL, kIntArrays };
+  enum { O_AOFF = kIntArrays, O_CLOFF, O_ADJ, O_CSUM, O_TABLE, O_CNT, O_KEY, O_TILE, kRegions };
+  size_t o[kRegions];
   size_t off = 0;
-  for (int j = 0; j < 14; ++j) { o[j] = off; off += nI; }          // 14 int arrays of T entries
-  o[14] = off; off += nI1;                                          // aoff
-  o[15] = off; off += nI1;                                          // cl_off
-  o[16] = off; off += up(size_t(T) * 16);                           // adj (<= 4 entries per pixel)
-  o[17] = off; off += up(size_t(T) * 24);                           // csum
-  o[18] = off; off += up(sizeof(Img) * n);                          // image table
-  o[19] = off; off += 256;                                          // counters
-  o[20] = off; off += up(size_t(T) * 8);                            // cl_key
-  o[21] = off; off += up(size_t(ntiles + 1) * 4);                   // tile_sum
+  for (int j = 0; j < kIntArrays; ++j) { o[j] = off; off += nI; }
+  o[O_AOFF] = off; off += nI1;
+  o[O_CLOFF] = off; off += nI1;
+  o[O_ADJ] = off; off += up(size_t(T) * 16);   // <= 2 edges per pixel, 2 entries per edge
+  o[O_CSUM] = off; off += up(size_t(T) * 24);
+  o[O_TABLE] = off; off += up(sizeof(Img) * n);
+  o[O_CNT] = off; off += 256;
+  o[O_KEY] = off; off += up(size_t(T) * 8);
+  o[O_TILE] = off; off += up(size_t(ntiles + 1) * 4);
   void* slab = nullptr;
   cudaError_t e = cudaSuccess;
   if (cache && cache->bytes >= off) {
@@ -659,27 +699,29 @@ gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const 
     }
   }
   char* b = static_cast<char*>(slab);
-  int* ia[14];
-  for (int j = 0; j < 14; ++j) ia[j] = reinterpret_cast<int*>(b + o[j]);
+  auto ia = [&](int j) { return reinterpret_cast<int*>(b + o[j]); };
   Scratch S{};
-  S.parent = ia[0]; S.size = ia[1]; S.cpar = ia[2]; S.sid = ia[3]; S.sroot = ia[4]; S.simg = ia[5];
-  S.deg = ia[6]; S.cl_count = ia[7]; S.big = ia[8]; S.gpar = ia[9]; S.gsize = ia[10]; S.next = ia[11];
-  S.tail = ia[12]; S.in = reinterpret_cast<int32_t*>(ia[13]);
-  S.aoff = reinterpret_cast<int*>(b + o[14]);
-  S.cl_off = reinterpret_cast<int*>(b + o[15]);
-  S.adj = reinterpret_cast<int*>(b + o[16]);
-  S.csum = reinterpret_cast<long long*>(b + o[17]);
-  Img* table = reinterpret_cast<Img*>(b + o[18]);
-  S.cnt = reinterpret_cast<unsigned long long*>(b + o[19]);
-  S.nsmall = reinterpret_cast<int*>(b + o[19] + 64);
-  S.err = reinterpret_cast<int*>(b + o[19] + 128);
-  S.nbig = reinterpret_cast<int*>(b + o[19] + 192);
-  S.cl_key = reinterpret_cast<unsigned long long*>(b + o[20]);
-  S.tile_sum = reinterpret_cast<int*>(b + o[21]);
+  S.parent = ia(A_PARENT); S.cidr = ia(A_CIDR); S.size = ia(A_SIZE); S.cimg = ia(A_CIMG);
+  S.clabel = reinterpret_cast<int32_t*>(ia(A_CLABEL)); S.small = ia(A_SMALL); S.cpar = ia(A_CPAR);
+  S.deg = ia(A_DEG); S.cl_count = ia(A_CLCOUNT); S.big = ia(A_BIG); S.gpar = ia(A_GPAR); S.gsize = ia(A_GSIZE);
+  S.next = ia(A_NEXT); S.tail = ia(A_TAIL);
+  S.aoff = ia(O_AOFF);
+  S.cl_off = ia(O_CLOFF);
+  S.adj = ia(O_ADJ);
+  S.csum = reinterpret_cast<long long*>(b + o[O_CSUM]);
+  S.mean = reinterpret_cast<double*>(b + o[O_CSUM]);
+  Img* table = reinterpret_cast<Img*>(b + o[O_TABLE]);
+  S.cnt = reinterpret_cast<unsigned long long*>(b + o[O_CNT]);
+  S.ncomp = reinterpret_cast<int*>(b + o[O_CNT] + 64);
+  S.err = reinterpret_cast<int*>(b + o[O_CNT] + 128);
+  S.nbig = reinterpret_cast<int*>(b + o[O_CNT] + 192);
+  S.cl_key = reinterpret_cast<unsigned long long*>(b + o[O_KEY]);
+  S.tile_sum = ia(O_TILE);
   // blocks per image: enough to fill the machine across the images
   const long long per = std::max<long long>(1, std::min<long long>((maxN + 255) / 256, (152LL * 16 + n - 1) / n));
   const dim3 gp{static_cast<unsigned>(per), static_cast<unsigned>(n)};
   const int gs = 152 * 8;
+  const unsigned nt = unsigned(ntiles);
   unsigned long long hc[3] = {};
   int herr = 0;
   do {
@@ -689,24 +731,24 @@ gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const 
     if ((e = cudaMemsetAsync(S.deg, 0, nI, s)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(S.cl_count, 0, nI, s)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(S.cnt, 0, 256, s)) != cudaSuccess) break;
-    k_cc_init<<<gp, 256, 0, s>>>(table, S.parent, S.in);
-    k_cc_union<<<gp, 256, 0, s>>>(table, S.in, S.parent, S.err);
+    k_cc_init<<<gp, 256, 0, s>>>(table, S.parent);
+    k_cc_union<<<gp, 256, 0, s>>>(table, S.parent, S.err);
     k_cc_flatten<<<gp, 256, 0, s>>>(table, S.parent, S.err);
-    k_comp_stats<<<gp, 256, 0, s>>>(table, S.parent, S.size, S.csum);
-    k_small_count<<<unsigned(ntiles), 1024, 0, s>>>(table, n, T, S);
-    k_small_scan<<<1, 1024, 0, s>>>(int(ntiles), S);
-    k_small_assign<<<unsigned(ntiles), 1024, 0, s>>>(table, n, T, S);
+    k_root_count<<<nt, 1024, 0, s>>>(T, S);
+    k_root_scan<<<1, 1024, 0, s>>>(int(ntiles), S);
+    k_root_assign<<<nt, 1024, 0, s>>>(table, n, T, S);
+    k_comp_map<<<gp, 256, 0, s>>>(table, S);
+    k_comp_flags<<<gs, 256, 0, s>>>(table, S);
     k_edges<<<gp, 256, 0, s>>>(table, S, 0);
-    k_edges<<<gp, 256, 0, s>>>(table, S, 1);
-    k_scan_tiles<<<unsigned(ntiles), 1024, 0, s>>>(S.deg, S.nsmall, S.aoff, S.tile_sum);
-    k_scan_tile_sums<<<1, 1024, 0, s>>>(S.tile_sum, S.nsmall, S.aoff);
-    k_scan_add<<<unsigned(ntiles), 1024, 0, s>>>(S.aoff, S.tile_sum, S.nsmall);
+    k_scan_tiles<<<nt, 1024, 0, s>>>(S.deg, S.ncomp, S.aoff, S.tile_sum);
+    k_scan_tile_sums<<<1, 1024, 0, s>>>(S.tile_sum, S.ncomp, S.aoff);
+    k_scan_add<<<nt, 1024, 0, s>>>(S.aoff, S.tile_sum, S.ncomp);
     if ((e = cudaMemsetAsync(S.deg, 0, nI, s)) != cudaSuccess) break;
-    k_edges<<<gp, 256, 0, s>>>(table, S, 2);
+    k_edges<<<gp, 256, 0, s>>>(table, S, 1);
     k_cluster_count<<<gs, 256, 0, s>>>(S);
-    k_scan_tiles<<<unsigned(ntiles), 1024, 0, s>>>(S.cl_count, S.nsmall, S.cl_off, S.tile_sum);
-    k_scan_tile_sums<<<1, 1024, 0, s>>>(S.tile_sum, S.nsmall, S.cl_off);
-    k_scan_add<<<unsigned(ntiles), 1024, 0, s>>>(S.cl_off, S.tile_sum, S.nsmall);
+    k_scan_tiles<<<nt, 1024, 0, s>>>(S.cl_count, S.ncomp, S.cl_off, S.tile_sum);
+    k_scan_tile_sums<<<1, 1024, 0, s>>>(S.tile_sum, S.ncomp, S.cl_off);
+    k_scan_add<<<nt, 1024, 0, s>>>(S.cl_off, S.tile_sum, S.ncomp);
     if ((e = cudaMemsetAsync(S.cl_count, 0, nI, s)) != cudaSuccess) break;
     k_cluster_fill<<<gs, 256, 0, s>>>(S);
     k_cluster_merge<<<gs, 256, 0, s>>>(table, S);
