@@ -59,7 +59,8 @@ namespace conn {
 constexpr int kMaxHops = 1 << 24;      // bound on any parent-chain walk or union retry
 constexpr int kFixedShift = 20;        // colour sums in units of 2^-20
 constexpr int kMaxCluster = 1 << 16;   // bound on the members a cluster sorted in global memory may have
-constexpr int kThreadCluster = 8;      // clusters up to this size: one thread; larger: one warp
+constexpr int kThreadCluster = 2;      // clusters up to this size: one thread; larger: one warp
+constexpr int kHugeCluster = 32;       // warp clusters above this size are started first
 constexpr int kWarpSortMax = 1024;     // members a warp sorts in shared memory
 constexpr int kScanTile = 4096;        // elements per block of the tile kernels (1024 threads x 4)
 constexpr int kMergeWarps = 4;
@@ -90,7 +91,8 @@ struct Scratch {
   int* cl_count;              // members of the cluster it roots, then fill cursor
   int* cl_off;                // (ncomp + 1) member offsets
   unsigned long long* cl_key; // members as (size << 32 | c), grouped by cluster
-  int* big;                   // roots of clusters above kThreadCluster members
+  int* big;                   // roots of clusters above kThreadCluster members: those above
+                              // kHugeCluster from the front, the others from the back
   int* gpar;                  // merge union-find (group founder)
   int* gsize;                 // group size (kept for small founders)
   int* next;                  // next member of its group, -1 at the end
@@ -98,7 +100,7 @@ struct Scratch {
   int* tile_sum;              // tile kernels: per tile counts, then their exclusive prefix
   unsigned long long* cnt;    // counters: 0 small, 1 merged, 2 components
   int* ncomp;                 // the component count as int (read by later kernels)
-  int* nbig;                  // entries of `big`
+  int* nbig;                  // [0] entries at the front of `big`, [1] at the back
   int* err;
 };
 
@@ -178,17 +180,43 @@ __device__ __forceinline__ bool small_size(long long s, int K, long long N) { re
   const int ncomp_ = *S.ncomp; \
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp_; c += gridDim.x * blockDim.x)
 
+// Warp-uniform pixel loop (32 consecutive pixels per warp and step, every
+// lane taking part in the shuffles; `valid` marks the pixels of the image).
+#define FOR_PIXEL_WARPS(im, i, valid)                                                          \
+  const Img im = imgs[blockIdx.y];                                                             \
+  const long long im##_N = (long long)im.W * im.H;                                             \
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i - (threadIdx.x & 31) < im##_N; \
+       i += (long long)gridDim.x * blockDim.x)                                                 \
+    if (const bool valid = i < im##_N; true)
+
+// Every pixel starts under the first pixel of its run: the pixels of one
+// label that follow each other in a row within the warp's 32 (a ballot).  No
+// union runs yet, so these plain stores race with nothing.
 __global__ void k_cc_init(const Img* __restrict__ imgs, int* __restrict__ p) {
-  FOR_PIXELS(im, i) p[im.off + i] = int(im.off + i);
+  const int lane = threadIdx.x & 31;
+  FOR_PIXEL_WARPS(im, i, valid) {
+    const int x = valid ? int(i % im.W) : 0;
+    const int32_t l = valid ? im.labels[i] : 0;
+    const int32_t lprev = __shfl_up_sync(0xffffffffu, l, 1);
+    const bool head = !valid || lane == 0 || x == 0 || lprev != l;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    if (valid) p[im.off + i] = int(im.off + i - (lane - start));
+  }
 }
 
+// The unions the runs leave: a run that begins at a warp's first lane with the
+// same label to its left, and one vertical union per pair of vertically
+// adjacent runs (at the leftmost pixel of their overlap).
 __global__ void k_cc_union(const Img* __restrict__ imgs, int* p, int* err) {
   FOR_PIXELS(im, i) {
     const int y = int(i / im.W), x = int(i - (long long)y * im.W);
     const long long g = im.off + i;
     const int32_t l = im.labels[i];
-    if (x + 1 < im.W && l == im.labels[i + 1]) unite(p, int(g), int(g + 1), err);
-    if (y + 1 < im.H && l == im.labels[i + im.W]) unite(p, int(g), int(g + im.W), err);
+    const bool left_same = x > 0 && im.labels[i - 1] == l;
+    if (left_same && (threadIdx.x & 31) == 0) unite(p, int(g), int(g - 1), err);
+    if (y + 1 < im.H && l == im.labels[i + im.W] && !(left_same && im.labels[i - 1 + im.W] == l))
+      unite(p, int(g), int(g + im.W), err);
   }
 }
 
@@ -365,7 +393,10 @@ __global__ void __launch_bounds__(256) k_comp_flags(const Img* __restrict__ imgs
 
 // Walks the 4-neighbour edges between different components; `mode` 0 unites
 // small-small pairs into clusters and counts each small side's adjacency, 1
-// fills the adjacency lists.
+// fills the adjacency lists.  An edge whose pair of components the previous
+// edge along the same line already gave (the pixel to the left for a vertical
+// edge, the pixel above for a horizontal one) is skipped: the lists are
+// neighbour sets, and most repeats go.
 __global__ void k_edges(const Img* __restrict__ imgs, Scratch S, int mode) {
   FOR_PIXELS(im, i) {
     const int y = int(i / im.W), x = int(i - (long long)y * im.W);
@@ -373,16 +404,19 @@ __global__ void k_edges(const Img* __restrict__ imgs, Scratch S, int mode) {
     const int ci = S.parent[g];
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-      long long j;
+      long long j, back;  // back: the same edge one pixel earlier along the line, or -1
       if (d == 0) {
         if (x + 1 >= im.W) continue;
         j = g + 1;
+        back = y > 0 ? g - im.W : -1;
       } else {
         if (y + 1 >= im.H) continue;
         j = g + im.W;
+        back = x > 0 ? g - 1 : -1;
       }
       const int cj = S.parent[j];
       if (ci == cj) continue;
+      if (back >= 0 && S.parent[back] == ci && S.parent[back + (j - g)] == cj) continue;
       const int si = S.small[ci], sj = S.small[cj];
       if (mode == 0) {
         if (si && sj) unite(S.cpar, ci, cj, S.err);
@@ -517,7 +551,8 @@ __global__ void k_cluster_merge(const Img* __restrict__ imgs, Scratch S) {
     if (!S.small[c] || S.cpar[c] != c) continue;  // not a cluster root
     const int n = S.cl_off[c + 1] - S.cl_off[c];
     if (n > kThreadCluster) {
-      S.big[atomicAdd(S.nbig, 1)] = c;
+      if (n > kHugeCluster) S.big[atomicAdd(S.nbig, 1)] = c;
+      else S.big[*S.ncomp - 1 - atomicAdd(S.nbig + 1, 1)] = c;
       continue;
     }
     const Img im = imgs[S.cimg[c]];
@@ -551,7 +586,9 @@ __global__ void k_cluster_merge(const Img* __restrict__ imgs, Scratch S) {
   if ((threadIdx.x & 31) == 0 && merged) atomicAdd(S.cnt + 1, (unsigned long long)merged);
 }
 
-// One warp per cluster above kThreadCluster members.  The keys are sorted in
+// One warp per cluster above kThreadCluster members, the clusters above
+// kHugeCluster members first (the longest serial chains start earliest).
+// The keys are sorted in
 // shared memory (bitonic; clusters above kWarpSortMax members are sorted in
 // place by one lane), then the members are taken in order as above, with the
 // adjacency entries of each member's group spread over the lanes and the
@@ -561,10 +598,10 @@ __global__ void k_cluster_merge(const Img* __restrict__ imgs, Scratch S) {
 __global__ void __launch_bounds__(kMergeWarps * 32) k_cluster_merge_warp(const Img* __restrict__ imgs, Scratch S) {
   __shared__ unsigned long long sk[kMergeWarps][kWarpSortMax];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nbig = *S.nbig;
+  const int nhuge = S.nbig[0], nbig = S.nbig[0] + S.nbig[1], ncomp = *S.ncomp;
   unsigned merged = 0;
   for (int b = blockIdx.x * kMergeWarps + warp; b < nbig; b += gridDim.x * kMergeWarps) {
-    const int c = S.big[b];
+    const int c = b < nhuge ? S.big[b] : S.big[ncomp - 1 - (b - nhuge)];
     const Img im = imgs[S.cimg[c]];
     const long long N = (long long)im.W * im.H;
     unsigned long long* gkey = S.cl_key + S.cl_off[c];
@@ -752,7 +789,7 @@ gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const 
     if ((e = cudaMemsetAsync(S.cl_count, 0, nI, s)) != cudaSuccess) break;
     k_cluster_fill<<<gs, 256, 0, s>>>(S);
     k_cluster_merge<<<gs, 256, 0, s>>>(table, S);
-    k_cluster_merge_warp<<<152 * 4, kMergeWarps * 32, 0, s>>>(table, S);
+    k_cluster_merge_warp<<<152 * 16, kMergeWarps * 32, 0, s>>>(table, S);
     k_relabel<<<gp, 256, 0, s>>>(table, S);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(hc, S.cnt, sizeof(hc), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
