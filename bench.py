@@ -81,7 +81,7 @@ def workload_config(v, nx, ny, K):
         "workload": f"{W}x{H} synthetic Voronoi sRGB ({REGIONS} regions, noise sigma {SIGMA:g}), "
                     f"K={K_REQ} requested -> v={v}, K={K}; {ITERS} plain-EM iterations (Sec. III-C init)",
         "W": W, "H": H, "K": K, "v": v, "nx": nx, "ny": ny, "iters": ITERS,
-        "precision": "FP32 E-step, FP64 sufficient statistics / floor / inversion",
+        "precision": "FP32 E-step and per-cell sums, FP64-accurate superpixel sums (FP32 TwoSum pairs), FP64 update / floor / inversion",
         "l2": "flushed between timed steps (256 MiB memset, outside the timed interval)",
         "init": "plain",
     }
@@ -515,7 +515,7 @@ def learned_config(n, bps):
                     f"learned theta_0 + {LEARN_T} EM iterations vs the Sec. III-C start + {ITERS} iterations",
         "images": n, "W": W, "H": H, "v": LEARN_V, "K": 672, "iters_learned": LEARN_T, "iters_plain": ITERS,
         "network": "6-layer conv initialiser, BF16 weights/activations, FP32 accumulation (tcgen05)",
-        "precision": "FP32 E-step, FP64 sufficient statistics / floor / inversion",
+        "precision": "FP32 E-step and per-cell sums, FP64-accurate superpixel sums (FP32 TwoSum pairs), FP64 update / floor / inversion",
         "l2": "flushed between timed steps (256 MiB memset, outside the timed interval); inputs > L2",
         "blocks_per_sm": bps,
     }

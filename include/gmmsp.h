@@ -67,8 +67,9 @@ enum {
 
 /* Arithmetic of the EM loop. */
 enum {
-    GMMSP_PREC_MIXED = 0, /* FP32 E-step; FP64 sufficient statistics from the
-                             per-cell partial on, FP64 floor and inversion  */
+    GMMSP_PREC_MIXED = 0, /* FP32 E-step and per-cell partial sums; the
+                             superpixel sums formed FP64-accurate (FP32 pairs,
+                             error-free TwoSum), FP64 update, floor, inversion */
     GMMSP_PREC_FP32 = 1   /* everything in FP32, raw (unshifted) moments    */
 };
 

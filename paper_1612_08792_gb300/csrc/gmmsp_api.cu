@@ -5,7 +5,7 @@
 //   lab       3 W H float         CIELAB image as planes L, a, b
 //   theta     K x 16 double       master parameters (mu, Sigma_s, Sigma_c)
 //   gp        K x 16 float        packed E-step coefficients
-//   partials  ncells x 136        per-cell FP64 (FP32 variant: float) partial sums
+//   partials  ncells x 136        per-cell FP32 partial sums
 //   cell_ll   ncells double       per-cell log-likelihood of the label pass
 //   llk       kLlkCap double      L(theta_t) per E-step
 //   ws        finalize workspace; ticket; counters; bad flag
@@ -149,7 +149,8 @@ bool inject_alloc_failure() {
 }
 
 size_t partial_bytes(const Geom& g, int precision) {
-  return size_t(g.ncells) * gmmsp::kPartStride * (precision == GMMSP_PREC_FP32 ? 4 : 8);
+  (void)precision;
+  return size_t(g.ncells) * gmmsp::kPartStride * sizeof(float);
 }
 
 gmmsp_status check_ready(gmmsp_ctx c) {

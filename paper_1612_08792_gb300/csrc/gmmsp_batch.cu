@@ -232,7 +232,7 @@ gmmsp_status gmmsp_batch_create(gmmsp_batch* out, int n, const int* widths, cons
   }
   b->sm_count = prop.multiProcessorCount;
   b->label_blocks_per_sm = std::max(1, gmmsp::label_pass_batch_occupancy());
-  const size_t pbytes = size_t(cells) * gmmsp::kPartStride * (p->precision == GMMSP_PREC_FP32 ? 4 : 8);
+  const size_t pbytes = size_t(cells) * gmmsp::kPartStride * sizeof(float);
   size_t off = 0;
   const size_t o_lab = off;   off += up256(3 * size_t(pix) * sizeof(float));
   const size_t o_theta = off; off += up256(size_t(ks) * gmmsp::kTheta * sizeof(double));

@@ -15,11 +15,15 @@
 //       d = z - mu_k(old) (the data shifted by the previous mean so that the
 //       FP32 second moments do not cancel).
 // The per-lane sums are added per slot and per cell in shared memory and
-// written once per cell as FP64: a block-level partial, with no global
-// atomics (k_em_pass).
+// written once per cell: a block-level partial, with no global atomics
+// (k_em_pass).  The partials are FP32 sums over one cell's <= v^2 pixels and
+// are stored as such.
 //
 // The finalize adds the <= 9 partials of the cells whose candidate set holds
-// k in a fixed order, giving the sums over the pixel set I_k of Eq. (Ik), and
+// k in a fixed order, giving the sums over the pixel set I_k of Eq. (Ik) --
+// mixed precision: as an unevaluated FP32 pair (hi, lo) built with the
+// error-free TwoSum (Knuth; Moller) and rounded to FP64 once, within about
+// 2^-47 of the exact sum, which keeps the FP64 pipe for the update -- and
 // turns them into Eq. (UpdateMu), (UpdateSigS) and (UpdateSigC) in FP64:
 //   mu = mu_old + S1 / W,   Sigma = S2 / W - (S1 / W)(S1 / W)^T,
 // then applies the floor of Eq. (mlams)/(mlamc) and re-packs the E-step
@@ -164,9 +168,11 @@ __device__ __forceinline__ void e_pixel(const float4* sp, unsigned mask, const f
   for (int s = 0; s < kSlots; ++s) R[s] *= inv;
 }
 
-// Fused E-step + M-step partial sums.  PT = double (mixed precision, shifted
-// moments) or float (all-FP32 variant, raw moments).  WPC warps share one
-// cell; a 128-thread block holds 4 / WPC cells.
+// Fused E-step + M-step partial sums, stored as PT = float.  SHIFT: mixed
+// precision (moments about the previous mean, the per-cell log-likelihood
+// stored in log2 units and converted by the FP64 reduction); otherwise the
+// all-FP32 variant (raw moments, the log-likelihood in nats).  WPC warps
+// share one cell; a 128-thread block holds 4 / WPC cells.
 //
 // Each warp walks its share of the cell 32 pixels at a time.  Every lane
 // takes one pixel through the E part (its <= 9 posteriors and its
@@ -348,7 +354,7 @@ __device__ __forceinline__ void em_cell_block(const Src& lab, const Geom& g, con
       float v = sm.part[w0][o];
 #pragma unroll
       for (int w = 1; w < WPC; ++w) v += sm.part[w0 + w][o];
-      out[o] = (o < kSlots * kStats) ? PT(v) : PT(v) * PT(0.69314718055994530942);
+      out[o] = (o < kSlots * kStats || SHIFT) ? PT(v) : PT(v) * PT(0.69314718055994530942);
     }
   }
   if (WPC == 1) __syncwarp(); else __syncthreads();  // the slot's buffers are reused next
@@ -574,15 +580,16 @@ constexpr int kFinThreads = 32;  // one warp per block: spreads small K over mor
 
 // Deterministic sum of the per-cell log-likelihoods: each block adds a fixed
 // strided subset and a tree, the last block to finish adds the block sums in
-// block order (one atomic ticket; no thread waits on another).
-template <typename PT, int NT>
+// block order (one atomic ticket; no thread waits on another).  LOG2: the
+// values are in log2 units and are turned into nats (in FP64) as they are read.
+template <typename PT, int NT, bool LOG2>
 __device__ void block_ll_sum(const PT* vals, long long stride, int n, double* blk, unsigned* ticket,
                              double* out) {
   __shared__ double red[NT];
   __shared__ bool last;
   double s = 0.0;
   for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT)
-    s += double(vals[(long long)i * stride]);
+    s += LOG2 ? double(vals[(long long)i * stride]) * 0.69314718055994530942 : double(vals[(long long)i * stride]);
   red[threadIdx.x] = s;
   __syncthreads();
   for (int w = NT / 2; w > 0; w >>= 1) {
@@ -614,19 +621,36 @@ __device__ void block_ll_sum(const PT* vals, long long stride, int n, double* bl
   }
 }
 
+// s + b as the unevaluated pair (hi, lo): TwoSum's exact error of the FP32
+// addition goes into lo (no contraction or reassociation: _rn intrinsics).
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
+  const float s = __fadd_rn(hi, b);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
 // Update of superpixel k from the partial sums of its <= 9 cells (see the
-// header comment); the counters are incremented by the caller.
-template <typename PT>
+// header comment); the counters are incremented by the caller.  SHIFT: the
+// mixed-precision path (pair sums rounded to FP64, FP64 arithmetic, moments
+// about the previous mean); otherwise the FP32 variant.
+template <typename PT, bool SHIFT>
 __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__ partials,
                                            double* __restrict__ theta, float* __restrict__ gp,
                                            double eps_s, double eps_c, int k, unsigned& dead,
                                            unsigned& rs, unsigned& rc) {
-  using T = PT;  // arithmetic type of the update: double, or float for the FP32 variant
-  constexpr bool kShifted = sizeof(PT) == 8;
+  using T = typename std::conditional<SHIFT, double, float>::type;  // arithmetic type of the update
+  constexpr bool kShifted = SHIFT;
   const int kx = k % g.nx, ky = k / g.nx;
   T S[kStats];
+  float hi[kStats], lo[kStats];
 #pragma unroll
-  for (int j = 0; j < kStats; ++j) S[j] = T(0);
+  for (int j = 0; j < kStats; ++j) {
+    S[j] = T(0);
+    hi[j] = 0.f;
+    lo[j] = 0.f;
+  }
   // The cells (kx+dx, ky+dy) hold k in slot (1-dy)*3 + (1-dx); fixed order.
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
@@ -638,8 +662,15 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
       if (cx < 0 || cx >= g.ncx) continue;
       const PT* P = partials + (long long)(cy * g.ncx + cx) * kPartStride + ((1 - dy) * 3 + (1 - dx)) * kStats;
 #pragma unroll
-      for (int j = 0; j < kStats; ++j) S[j] += P[j];
+      for (int j = 0; j < kStats; ++j) {
+        if (SHIFT) two_sum_acc(hi[j], lo[j], P[j]);
+        else S[j] += T(P[j]);
+      }
     }
+  }
+  if (SHIFT) {
+#pragma unroll
+    for (int j = 0; j < kStats; ++j) S[j] = T(double(hi[j]) + double(lo[j]));
   }
   const T Wk = S[ST_W];
   if (!(Wk >= T(1e-8))) {
@@ -706,7 +737,7 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
   }
 }
 
-template <typename PT>
+template <typename PT, bool SHIFT>
 __global__ void __launch_bounds__(kFinThreads) k_finalize(Geom g, const PT* __restrict__ partials,
                                                           double* __restrict__ theta,
                                                           float* __restrict__ gp, double eps_s,
@@ -716,11 +747,11 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Geom g, const PT* __re
   pdl_wait();
   pdl_trigger();
   if (llk_out)
-    block_ll_sum<PT, kFinThreads>(partials + kSlots * kStats, kPartStride, g.ncells, blk, ticket, llk_out);
+    block_ll_sum<PT, kFinThreads, SHIFT>(partials + kSlots * kStats, kPartStride, g.ncells, blk, ticket, llk_out);
 
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned dead = 0, rs = 0, rc = 0;
-  if (k < g.K) finalize_k<PT>(g, partials, theta, gp, eps_s, eps_c, k, dead, rs, rc);
+  if (k < g.K) finalize_k<PT, SHIFT>(g, partials, theta, gp, eps_s, eps_c, k, dead, rs, rc);
   dead = __reduce_add_sync(0xffffffffu, dead);
   rs = __reduce_add_sync(0xffffffffu, rs);
   rc = __reduce_add_sync(0xffffffffu, rc);
@@ -731,7 +762,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Geom g, const PT* __re
   }
 }
 
-template <typename PT>
+template <typename PT, bool SHIFT>
 __global__ void __launch_bounds__(kFinThreads) k_finalize_batch(const BatchImage* __restrict__ imgs, int n,
                                                                 int total_k, const PT* __restrict__ partials,
                                                                 double* __restrict__ theta,
@@ -744,7 +775,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_batch(const BatchImage
     const int k = base + threadIdx.x;
     if (k < total_k) {
       const BatchImage& im = imgs[find_image(imgs, n, k, 1)];
-      finalize_k<PT>(im.g, partials + (long long)im.cell_off * kPartStride, theta + (long long)im.k_off * kTheta,
+      finalize_k<PT, SHIFT>(im.g, partials + (long long)im.cell_off * kPartStride, theta + (long long)im.k_off * kTheta,
                      gp + (long long)im.k_off * kGP, eps_s, eps_c, k - im.k_off, dead, rs, rc);
     }
   }
@@ -797,7 +828,7 @@ __device__ __forceinline__ bool dpos(double x) { return __double_as_longlong(x) 
 // the image with geometry g, partials, theta and gp; all 32 lanes of the warp
 // call it together (valid = false for a half-warp without a superpixel).
 // X (48 doubles) and F (8 floats) are the half-warp's shared scratch.
-__device__ __forceinline__ void finalize_l16_body(const Geom& g, const double* __restrict__ partials,
+__device__ __forceinline__ void finalize_l16_body(const Geom& g, const float* __restrict__ partials,
                                                   double* __restrict__ theta, float* __restrict__ gp,
                                                   double eps_s, double eps_c, int k, bool valid, double* X,
                                                   float* F, unsigned long long* counters) {
@@ -810,7 +841,7 @@ __device__ __forceinline__ void finalize_l16_body(const Geom& g, const double* _
   // 1. Sums over the pixel set I_k: lane l < 15 adds statistic l of the <= 9
   //    cells holding k (cell (kx+dx, ky+dy) holds k in slot (1-dy)*3+(1-dx)).
   {
-    double v[9];
+    float v[9];
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
@@ -820,12 +851,12 @@ __device__ __forceinline__ void finalize_l16_body(const Geom& g, const double* _
         v[(dy + 1) * 3 + (dx + 1)] =
             in ? __ldg(partials + (long long)(cy * g.ncx + cx) * kPartStride +
                        ((1 - dy) * 3 + (1 - dx)) * kStats + l)
-               : 0.0;
+               : 0.f;
       }
-    double s = 0.0;
+    float hi = 0.f, lo = 0.f;
 #pragma unroll
-    for (int j = 0; j < 9; ++j) s += v[j];
-    if (l < kStats) X[l] = s;
+    for (int j = 0; j < 9; ++j) two_sum_acc(hi, lo, v[j]);
+    if (l < kStats) X[l] = double(hi) + double(lo);
   }
   __syncwarp();
   const double Wk = X[ST_W];
@@ -978,7 +1009,7 @@ __device__ __forceinline__ void finalize_l16_body(const Geom& g, const double* _
   }
 }
 
-__global__ void __launch_bounds__(kFin16Threads) k_finalize_l16(Geom g, const double* __restrict__ partials,
+__global__ void __launch_bounds__(kFin16Threads) k_finalize_l16(Geom g, const float* __restrict__ partials,
                                                               double* __restrict__ theta,
                                                               float* __restrict__ gp, double eps_s,
                                                               double eps_c, double* llk_out, double* blk,
@@ -989,7 +1020,7 @@ __global__ void __launch_bounds__(kFin16Threads) k_finalize_l16(Geom g, const do
   pdl_wait();
   pdl_trigger();
   if (llk_out)
-    block_ll_sum<double, kFin16Threads>(partials + kSlots * kStats, kPartStride, g.ncells, blk, ticket,
+    block_ll_sum<float, kFin16Threads, true>(partials + kSlots * kStats, kPartStride, g.ncells, blk, ticket,
                                         llk_out);
   const int q = threadIdx.x >> 4;
   const int k = blockIdx.x * (kFin16Threads / 16) + q;
@@ -999,7 +1030,7 @@ __global__ void __launch_bounds__(kFin16Threads) k_finalize_l16(Geom g, const do
 // The same over a batch: half-warp q of block b takes superpixel 4 b + q of
 // the batch, found in its image by a binary search over the offsets.
 __global__ void __launch_bounds__(kFin16Threads) k_finalize_l16_batch(const BatchImage* __restrict__ imgs, int n,
-                                                                    int total_k, const double* __restrict__ partials,
+                                                                    int total_k, const float* __restrict__ partials,
                                                                     double* __restrict__ theta,
                                                                     float* __restrict__ gp, double eps_s,
                                                                     double eps_c, unsigned long long* counters) {
@@ -1018,7 +1049,7 @@ __global__ void __launch_bounds__(kFinThreads) k_ll_reduce(const double* __restr
                                                            double* blk, unsigned* ticket, double* out) {
   pdl_wait();
   pdl_trigger();
-  block_ll_sum<double, kFinThreads>(cell_ll, 1, n, blk, ticket, out);
+  block_ll_sum<double, kFinThreads, false>(cell_ll, 1, n, blk, ticket, out);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1065,15 +1096,14 @@ static cudaError_t em_pass_wpc(Src lab, const Geom& g, const float* gp, PT* part
 template <class Src>
 cudaError_t launch_em_pass(Src lab, const Geom& g, const float* gp, void* partials, int precision,
                            int wpc, cudaStream_t s) {
-  if (precision == 1)
-    return em_pass_wpc<float, false, Src, kColourFull>(lab, g, gp, static_cast<float*>(partials), wpc, s);
-  double* part = static_cast<double*>(partials);
+  float* part = static_cast<float*>(partials);
+  if (precision == 1) return em_pass_wpc<float, false, Src, kColourFull>(lab, g, gp, part, wpc, s);
   if constexpr (std::is_same<Src, LabPlanar>::value) {
-    if (g.cm == kColourSplit) return em_pass_wpc<double, true, Src, kColourSplit>(lab, g, gp, part, wpc, s);
-    if (g.cm == kColourGray) return em_pass_wpc<double, true, Src, kColourGray>(lab, g, gp, part, wpc, s);
+    if (g.cm == kColourSplit) return em_pass_wpc<float, true, Src, kColourSplit>(lab, g, gp, part, wpc, s);
+    if (g.cm == kColourGray) return em_pass_wpc<float, true, Src, kColourGray>(lab, g, gp, part, wpc, s);
   }
   if (g.cm != kColourFull) return cudaErrorInvalidValue;
-  return em_pass_wpc<double, true, Src, kColourFull>(lab, g, gp, part, wpc, s);
+  return em_pass_wpc<float, true, Src, kColourFull>(lab, g, gp, part, wpc, s);
 }
 
 template <class Src>
@@ -1109,16 +1139,16 @@ cudaError_t launch_finalize(const Geom& g, const void* partials, double* theta, 
   if (precision != 1 && g.K <= kFin16MaxK && g.cm == kColourFull) {
     const int blocks16 = (g.K + kFin16Threads / 16 - 1) / (kFin16Threads / 16);
     return launch_pdl(k_finalize_l16, dim3(blocks16), dim3(kFin16Threads), 0, s, g,
-                      static_cast<const double*>(partials), theta, gp, eps_s, eps_c, llk_out, ws, ticket,
+                      static_cast<const float*>(partials), theta, gp, eps_s, eps_c, llk_out, ws, ticket,
                       counters);
   }
   const int blocks = ll_blocks(g);
   if (precision == 1)
-    return launch_pdl(k_finalize<float>, dim3(blocks), dim3(kFinThreads), 0, s, g,
+    return launch_pdl(k_finalize<float, false>, dim3(blocks), dim3(kFinThreads), 0, s, g,
                       static_cast<const float*>(partials), theta, gp, eps_s, eps_c, llk_out, ws, ticket,
                       counters);
-  return launch_pdl(k_finalize<double>, dim3(blocks), dim3(kFinThreads), 0, s, g,
-                    static_cast<const double*>(partials), theta, gp, eps_s, eps_c, llk_out, ws, ticket,
+  return launch_pdl(k_finalize<float, true>, dim3(blocks), dim3(kFinThreads), 0, s, g,
+                    static_cast<const float*>(partials), theta, gp, eps_s, eps_c, llk_out, ws, ticket,
                     counters);
 }
 
@@ -1134,19 +1164,19 @@ namespace gmmsp {
 
 template <int CM>
 static void em_pass_batch_mixed(const BatchImage* imgs, int n, int total_cells, const float* lab, const float* gp,
-                                double* partials, int blocks, int minb, cudaStream_t s) {
+                                float* partials, int blocks, int minb, cudaStream_t s) {
   constexpr int smem = em_smem_bytes<1>();
   if (minb >= 6) {  // one cell per warp over a grid sized to the work
     const int nb = (total_cells + kEmWarps - 1) / kEmWarps;
     if (minb >= 7)
-      k_em_pass_batch_flat<double, true, 7, CM><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                              partials);
+      k_em_pass_batch_flat<float, true, 7, CM><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                             partials);
     else
-      k_em_pass_batch_flat<double, true, 6, CM><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                              partials);
+      k_em_pass_batch_flat<float, true, 6, CM><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                             partials);
   } else {
-    k_em_pass_batch<double, true, 5, CM><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                           partials);
+    k_em_pass_batch<float, true, 5, CM><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
+                                                                          partials);
   }
 }
 
@@ -1166,7 +1196,7 @@ cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells,
     }
     return cudaGetLastError();
   }
-  double* part = static_cast<double*>(partials);
+  float* part = static_cast<float*>(partials);
   switch (cm) {
     case kColourFull: em_pass_batch_mixed<kColourFull>(imgs, n, total_cells, lab, gp, part, blocks, minb, s); break;
     case kColourSplit: em_pass_batch_mixed<kColourSplit>(imgs, n, total_cells, lab, gp, part, blocks, minb, s); break;
@@ -1182,17 +1212,18 @@ cudaError_t launch_finalize_batch(const BatchImage* imgs, int n, int total_k, co
                                   cudaStream_t s) {
   if (precision != 1 && blocks == 0) {  // 16 lanes per superpixel
     const int nb = (total_k + kFin16Threads / 16 - 1) / (kFin16Threads / 16);
-    k_finalize_l16_batch<<<nb, kFin16Threads, 0, s>>>(imgs, n, total_k, static_cast<const double*>(partials), theta,
+    k_finalize_l16_batch<<<nb, kFin16Threads, 0, s>>>(imgs, n, total_k, static_cast<const float*>(partials), theta,
                                                      gp, eps_s, eps_c, counters);
     return cudaGetLastError();
   }
   if (precision == 1)
-    k_finalize_batch<float><<<blocks, kFinThreads, 0, s>>>(imgs, n, total_k, static_cast<const float*>(partials),
-                                                           theta, gp, eps_s, eps_c, counters);
+    k_finalize_batch<float, false><<<blocks, kFinThreads, 0, s>>>(imgs, n, total_k,
+                                                                  static_cast<const float*>(partials), theta, gp,
+                                                                  eps_s, eps_c, counters);
   else
-    k_finalize_batch<double><<<blocks, kFinThreads, 0, s>>>(imgs, n, total_k,
-                                                            static_cast<const double*>(partials), theta, gp,
-                                                            eps_s, eps_c, counters);
+    k_finalize_batch<float, true><<<blocks, kFinThreads, 0, s>>>(imgs, n, total_k,
+                                                                 static_cast<const float*>(partials), theta, gp,
+                                                                 eps_s, eps_c, counters);
   return cudaGetLastError();
 }
 

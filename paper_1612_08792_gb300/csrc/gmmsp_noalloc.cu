@@ -36,7 +36,7 @@ constexpr size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr size_t kOffTheta = 0;
 constexpr size_t kOffGp = kOffTheta + up(size_t(GMMSP_NOALLOC_MAX_CELLS) * gmmsp::kTheta * sizeof(double));
 constexpr size_t kOffPart = kOffGp + up(size_t(GMMSP_NOALLOC_MAX_CELLS) * gmmsp::kGP * sizeof(float));
-constexpr size_t kOffCellLl = kOffPart + up(size_t(GMMSP_NOALLOC_MAX_CELLS) * gmmsp::kPartStride * sizeof(double));
+constexpr size_t kOffCellLl = kOffPart + up(size_t(GMMSP_NOALLOC_MAX_CELLS) * gmmsp::kPartStride * sizeof(float));
 constexpr size_t kOffLlk = kOffCellLl + up(size_t(GMMSP_NOALLOC_MAX_CELLS) * sizeof(double));
 constexpr size_t kOffWs = kOffLlk + up(sizeof(double));
 constexpr size_t kOffTicket = kOffWs + up((GMMSP_NOALLOC_MAX_CELLS / 4 + 2) * sizeof(double));
@@ -146,7 +146,7 @@ extern "C" gmmsp_status gmmsp_segment_lab_noalloc(const float* lab_dev, int widt
   char* b = static_cast<char*>(base);
   double* theta = reinterpret_cast<double*>(b + kOffTheta);
   float* gp = reinterpret_cast<float*>(b + kOffGp);
-  double* partials = reinterpret_cast<double*>(b + kOffPart);
+  float* partials = reinterpret_cast<float*>(b + kOffPart);
   double* ws = reinterpret_cast<double*>(b + kOffWs);
   unsigned* ticket = reinterpret_cast<unsigned*>(b + kOffTicket);
   unsigned long long* counters = reinterpret_cast<unsigned long long*>(b + kOffCounters);

@@ -1,7 +1,8 @@
 """Precision study on the 481x321 workload (K = 1000 requested -> v = 12, K = 1040,
-10 iterations): every output of the mixed-precision path (FP32 E-step, FP64
-statistics from the per-cell partial on, FP64 floor and inversion) and of the
-all-FP32 variant against the FP64 oracle on the same FP32 CIELAB input.
+10 iterations): every output of the mixed-precision path (FP32 E-step and per-cell
+sums, FP64-accurate superpixel sums from TwoSum pairs of the FP32 partials, FP64
+update, floor and inversion) and of the all-FP32 variant against the FP64 oracle on
+the same FP32 CIELAB input.
 
 The mixed path must meet the parity bar; the FP32 variant's errors are recorded
 (bounded loosely here).  With GMMSP_PRECISION_OUT set, the per-output errors are
