@@ -492,12 +492,11 @@ LEARN_IMAGES, LEARN_V, LEARN_T, HELD_OUT0 = 256, 15, 2, 1_000_000
 # 32 -> 32) and four 3 x 3 layers per cell (288 -> 32 three times, 288 -> 16).
 NET_FLOPS_PER_PATCH = 2 * (27 * 32 + 32 * 32)
 NET_FLOPS_PER_CELL = 2 * (3 * 288 * 32 + 288 * 16)
-# DRAM bytes per 481 x 321 image of one batched E + M pass, from the ncu capture on
+# DRAM bytes per 481 x 321 image of one batched E + M pass, from an ncu capture on
 # 96 such images (dram__bytes_read.sum + dram__bytes_write.sum), scaled per image
-# (traffic grows with the image count), per launch variant (blocks per SM):
-#   7: one-cell-per-warp k_em_pass_batch_flat, 182.05 MB + 56.59 MB (spills included).
-# Other variants were not captured with the current kernel and report null.
-EM_BATCH_TRAFFIC_PER_IMAGE = {7: int((182.054400e6 + 56.586240e6) / 96)}
+# (traffic grows with the image count), per launch variant (blocks per SM).  Empty
+# until the current kernel (FP32 partials) is captured: roofline.traffic is null.
+EM_BATCH_TRAFFIC_PER_IMAGE = {}
 
 
 def measured_peaks():
