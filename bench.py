@@ -494,9 +494,10 @@ NET_FLOPS_PER_PATCH = 2 * (27 * 32 + 32 * 32)
 NET_FLOPS_PER_CELL = 2 * (3 * 288 * 32 + 288 * 16)
 # DRAM bytes per 481 x 321 image of one batched E + M pass, from an ncu capture on
 # 96 such images (dram__bytes_read.sum + dram__bytes_write.sum), scaled per image
-# (traffic grows with the image count), per launch variant (blocks per SM).  Empty
-# until the current kernel (FP32 partials) is captured: roofline.traffic is null.
-EM_BATCH_TRAFFIC_PER_IMAGE = {}
+# (traffic grows with the image count), per launch variant (blocks per SM); a variant
+# not captured with the current kernel reports null.
+#   6: one-cell-per-warp k_em_pass_batch_flat, 80 registers: 182.26 MB + 27.94 MB.
+EM_BATCH_TRAFFIC_PER_IMAGE = {6: int((182.262272e6 + 27.944192e6) / 96)}
 
 
 def measured_peaks():
@@ -756,6 +757,8 @@ def run_profile_case(args):
         net = load_pretrained(LEARN_V)
         bt = gm.SuperpixelsBatch([(H, W)] * args.images, spacing=LEARN_V)
         bt.autotune(imgs, reps=2)  # the launch choices of the timed step
+        if args.blocks_per_sm:
+            bt.set_launch(args.blocks_per_sm)
         bt.set_init_net(net)
         for _ in range(2):
             bt.segment(imgs, LEARN_T)
@@ -927,6 +930,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run a short untimed case for ncu captures and exit")
     ap.add_argument("--warps-per-cell", type=int, default=0, help="with --profile-case: launch shape")
+    ap.add_argument("--blocks-per-sm", type=int, default=0,
+                    help="with --profile-case --workload learned481: E+M pass variant (after the autotuner)")
     ap.add_argument("--workload", default="learned481",
                     choices=["learned481", "481x321", "3840x2160", "batch256", "conn256"],
                     help="learned481 (the headline line); 481x321, 3840x2160 or batch256 (other lines); "
