@@ -496,8 +496,10 @@ NET_FLOPS_PER_CELL = 2 * (3 * 288 * 32 + 288 * 16)
 # 96 such images (dram__bytes_read.sum + dram__bytes_write.sum), scaled per image
 # (traffic grows with the image count), per launch variant (blocks per SM); a variant
 # not captured with the current kernel reports null.
-#   6: one-cell-per-warp k_em_pass_batch_flat, 80 registers: 182.26 MB + 27.94 MB.
-EM_BATCH_TRAFFIC_PER_IMAGE = {6: int((182.262272e6 + 27.944192e6) / 96)}
+#   6: one-cell-per-warp k_em_pass_batch_flat, 80 registers: 182.26 MB + 27.94 MB;
+#   7: the same capped at 72 registers (some spill):          182.06 MB + 29.14 MB.
+EM_BATCH_TRAFFIC_PER_IMAGE = {6: int((182.262272e6 + 27.944192e6) / 96),
+                              7: int((182.058240e6 + 29.139712e6) / 96)}
 
 
 def measured_peaks():
@@ -796,11 +798,12 @@ CONN_BYTES_PER_PIXEL = 20
 CONN_LAUNCHES = 21  # kernels of one gmmsp_batch_connectivity call
 
 
-def _conn_case(gm, torch, n, stream, keep_images=False):
+def _conn_case(gm, torch, n, stream, keep_images=False, regions=None):
     """n held-out 481x321 images (v = 15) segmented by 10 plain-EM iterations in one batch
-    context: the label maps the connectivity post-processing works on."""
+    context: the label maps the connectivity post-processing (and the accuracy metrics) work
+    on.  regions: an (n, H, W) int32 tensor that receives the generator's region maps."""
     from synth.voronoi_torch import voronoi_batch
-    buf = voronoi_batch(W, H, REGIONS, SIGMA, range(HELD_OUT0, HELD_OUT0 + n))
+    buf = voronoi_batch(W, H, REGIONS, SIGMA, range(HELD_OUT0, HELD_OUT0 + n), regions_out=regions)
     imgs = [buf[i] for i in range(n)]
     with torch.cuda.stream(stream):
         bt = gm.SuperpixelsBatch([(H, W)] * n, spacing=LEARN_V, stream=stream)
@@ -892,6 +895,119 @@ def run_conn_workload(args):
     return 0
 
 
+# Algorithmic DRAM bytes per pixel of the accuracy metrics: the labels and the ground
+# truth read once (4 + 4 B).
+METRICS_BYTES_PER_PIXEL = 8
+METRICS_LAUNCHES = 4  # kernels of one gmmsp_segmentation_metrics_many call
+
+
+def run_metrics_workload(args):
+    """`metrics256`: BR, UE (Eq. ue) and ASA of the label maps of 256 held-out 481x321
+    images after 10 plain-EM iterations against the generator's regions, one
+    gmmsp_segmentation_metrics_many call per step."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    n = 256
+    regs = torch.empty((n, H, W), dtype=torch.int32, device="cuda")
+    bt, labels, buf = _conn_case(gm, torch, n, stream, keep_images=True, regions=regs)
+    K = (W // LEARN_V) * (H // LEARN_V)
+    gts = [regs[i] for i in range(n)]
+
+    def step():
+        return gm.gmmsp_segmentation_metrics_many(labels, gts, K, REGIONS, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    times = []
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = step()                  # synchronises the stream at its end
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    bt.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        done, secs = metrics_oracle_sample(labels, gts, K, args.cpu_seconds)
+        cpu = {"value": round(done * W * H / secs / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} of the {n} label maps in {secs:.1f} s (numpy, one thread)"}
+    ms = sum(times) / len(times)
+    pix = n * W * H
+    achieved = pix * METRICS_BYTES_PER_PIXEL / (ms * 1e-3) / 1e9
+    peak = measured_peaks().get("hbm_gbs")
+    src = "MEASURED_PEAKS.json hbm_gbs"
+    if not peak:
+        peak, src = 6800.0, "fallback 6.8 TB/s"
+    line = {"metric": "Mpixel/s accuracy metrics (BR, Eq. ue, Eq. asa) against a ground truth",
+            "value": round(pix / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32 counts (exact)", "data": "synthetic",
+            "config": {"workload": f"{n} held-out synthetic 481x321 Voronoi images ({REGIONS} regions, sigma 8): "
+                                   f"label maps after {ITERS} plain-EM iterations at spacing {LEARN_V} against the "
+                                   "generator's region maps, BR radius 2, UE eps 0.05; one batched call per step",
+                       "images": n, "K": K, "G": REGIONS,
+                       "l2": "flushed before every timed step (256 MiB memset)"},
+            "mean": {k: float(np.mean([r[k] for r in res])) for k in ("br", "ue", "asa")},
+            "roofline": {"kernel": f"the whole metrics call ({METRICS_LAUNCHES} kernels)", "bound": "hbm",
+                         "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src,
+                         "algorithmic_bytes_per_pixel": METRICS_BYTES_PER_PIXEL},
+            "gpu_launches": METRICS_LAUNCHES * args.steps, "clocks": clk.summary(), "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def metrics_oracle_sample(labels, gts, K, seconds):
+    """The metrics oracle, as it stands, on the label maps one at a time for about `seconds`."""
+    from oracle import metrics as om
+    done, t0 = 0, time.perf_counter()
+    while done < len(labels) and (done == 0 or time.perf_counter() - t0 < seconds):
+        om.all_metrics(labels[done].cpu().numpy(), gts[done].cpu().numpy(), 2, 0.05)
+        done += 1
+    return done, time.perf_counter() - t0
+
+
+def run_reference_metrics(args):
+    """`--impl reference --workload metrics256`: the metrics oracle on the same label maps and
+    region maps, one image per step."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    n = max(args.steps + 1, 1)
+    regs = torch.empty((n, H, W), dtype=torch.int32, device="cuda")
+    bt, labels, _ = _conn_case(gm, torch, n, stream, keep_images=True, regions=regs)
+    bt.close()
+    K = (W // LEARN_V) * (H // LEARN_V)
+    gts = [regs[i] for i in range(n)]
+    metrics_oracle_sample(labels[:1], gts[:1], K, 0.0)   # untimed: the oracle's first call
+    done, secs = metrics_oracle_sample(labels[1:], gts[1:], K, 1e9)
+    v = round(done * W * H / secs / 1e6, 4)
+    print(json.dumps({"impl": "reference", "metric": "Mpixel/s accuracy metrics (BR, Eq. ue, Eq. asa) against a "
+                                                     "ground truth",
+                      "value": v, "unit": UNIT, "n_gpus": 1, "steps": done, "warmup": 1,
+                      "ms_per_step": round(secs / max(done, 1) * 1e3, 3), "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                      "config": {"workload": "held-out synthetic 481x321 label maps after 10 plain-EM iterations "
+                                             "against the generator's regions, one image per step"},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                       "sample": f"{done} images"},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+    return 0
+
+
 def run_reference_conn(args):
     """`--impl reference --workload conn256`: the connectivity oracle on the same label maps,
     one image per step (the label maps themselves come from the GPU EM)."""
@@ -933,7 +1049,7 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="with --profile-case --workload learned481: E+M pass variant (after the autotuner)")
     ap.add_argument("--workload", default="learned481",
-                    choices=["learned481", "481x321", "3840x2160", "batch256", "conn256"],
+                    choices=["learned481", "481x321", "3840x2160", "batch256", "conn256", "metrics256"],
                     help="learned481 (the headline line); 481x321, 3840x2160 or batch256 (other lines); "
                          "with --profile-case the case to profile")
     ap.add_argument("--images", type=int, default=LEARN_IMAGES, help="learned481: images per step")
@@ -950,6 +1066,8 @@ def main():
         return run_reference_learned(args) if args.impl == "reference" else run_learned(args)
     if args.workload == "conn256":
         return run_reference_conn(args) if args.impl == "reference" else run_conn_workload(args)
+    if args.workload == "metrics256":
+        return run_reference_metrics(args) if args.impl == "reference" else run_metrics_workload(args)
     if args.workload != "481x321" and args.impl == "gmmsp":
         return run_other_workload(args)
     if args.impl == "reference":

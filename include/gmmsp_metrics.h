@@ -41,6 +41,16 @@ gmmsp_status gmmsp_segmentation_metrics(const int32_t *labels_dev, const int32_t
                                         int G, int radius, double eps, gmmsp_seg_metrics *out_host,
                                         void *stream);
 
+/* The same for n images in one call (four kernel launches for all of them,
+ * one allocation, one synchronisation): image i is labels_dev[i], gt_dev[i]
+ * of W[i] x H[i] pixels with K[i] superpixels and G[i] segments, and its
+ * metrics go to out_host[i] (n entries).  Returns GMMSP_E_INVALID for bad
+ * arguments, or when a label or id of any image is out of range (out_host is
+ * filled for all images then). */
+gmmsp_status gmmsp_segmentation_metrics_many(int n, const int32_t *const *labels_dev, const int32_t *const *gt_dev,
+                                             const int *W, const int *H, const int *K, const int *G, int radius,
+                                             double eps, gmmsp_seg_metrics *out_host, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,7 @@ __all__ = [
     "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
     "GMMSP_OK", "GMMSP_E_INVALID", "GMMSP_E_CUDA", "GMMSP_E_NOMEM", "GMMSP_E_NUMERIC", "GMMSP_E_TIMEOUT",
     "GMMSP_E_STATE", "gmmsp_segmentation_metrics", "gmmsp_enforce_connectivity", "gmmsp_connectivity",
-    "gmmsp_batch_connectivity", "GMMSP_GRAY8", "GMMSP_COLOUR_FULL", "GMMSP_COLOUR_SPLIT", "GMMSP_COLOUR_GRAY",
+    "gmmsp_batch_connectivity", "gmmsp_segmentation_metrics_many", "GMMSP_GRAY8", "GMMSP_COLOUR_FULL", "GMMSP_COLOUR_SPLIT", "GMMSP_COLOUR_GRAY",
 ]
 
 GMMSP_RGB8, GMMSP_LAB32, GMMSP_GRAY8 = 0, 1, 2
@@ -549,6 +549,37 @@ def gmmsp_segmentation_metrics(labels, gt, K: int, G: int, radius: int = 2, eps:
     if st != 0:
         raise GmmspError(st, "segmentation metrics failed (bad arguments or ids out of range)")
     return {k: getattr(out, k) for k, _ in gmmsp_seg_metrics._fields_}
+
+
+def gmmsp_segmentation_metrics_many(labels, gts, Ks, Gs, radius: int = 2, eps: float = 0.05, stream=None):
+    """The metrics of several (labels, gt) pairs in one call (lists of (H, W) int32 CUDA maps;
+    Ks, Gs: per-image superpixel and segment counts, or one int for all); synchronises."""
+    lib = load_library()
+    f = lib.gmmsp_segmentation_metrics_many
+    n = len(labels)
+    if not getattr(f, "_sig", False):
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                      ctypes.POINTER(gmmsp_seg_metrics), ctypes.c_void_p]
+        f._sig = True
+    if len(gts) != n or n < 1:
+        raise ValueError("one ground truth per label map")
+    Ks = [int(Ks)] * n if isinstance(Ks, int) else [int(k) for k in Ks]
+    Gs = [int(Gs)] * n if isinstance(Gs, int) else [int(g) for g in Gs]
+    for l, g in zip(labels, gts):
+        if tuple(g.shape) != tuple(l.shape) or not l.is_contiguous() or not g.is_contiguous():
+            raise ValueError("labels and gt must be contiguous (H, W) maps of one size")
+    Ws = np.array([int(l.shape[1]) for l in labels], dtype=np.int32)
+    Hs = np.array([int(l.shape[0]) for l in labels], dtype=np.int32)
+    Ka, Ga = np.array(Ks, dtype=np.int32), np.array(Gs, dtype=np.int32)
+    out = (gmmsp_seg_metrics * n)()
+    st = f(n, _ptr_array(labels), _ptr_array(gts), Ws.ctypes.data_as(ctypes.c_void_p),
+           Hs.ctypes.data_as(ctypes.c_void_p), Ka.ctypes.data_as(ctypes.c_void_p), Ga.ctypes.data_as(ctypes.c_void_p),
+           int(radius), float(eps), out, _stream_handle(stream))
+    if st != 0:
+        raise GmmspError(st, "segmentation metrics failed (bad arguments or ids out of range)")
+    return [{k: getattr(o, k) for k, _ in gmmsp_seg_metrics._fields_} for o in out]
 
 
 class gmmsp_conn_stats(ctypes.Structure):

@@ -9,10 +9,13 @@
 //                 boundary pixel within the Chebyshev radius
 //   k_table       per superpixel |s_k|, max_g |s_k & s_g| and the Eq. (ue)
 //                 terms, summed per block and added with 64-bit atomics
+// Every kernel takes a table of images and blockIdx.y as the image, so a
+// batch of images is four launches, one allocation and one synchronisation.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "../../include/gmmsp.h"
 #include "../../include/gmmsp_metrics.h"
@@ -22,16 +25,32 @@ namespace metrics {
 
 enum : int { C_BAD = 0, C_BR_REC = 1, C_BR_TOT = 2, C_UE = 3, C_ASA = 4, C_N = 5 };
 
-__global__ void k_overlap(const int32_t* __restrict__ labels, const int32_t* __restrict__ gt, long long N, int K,
-                          int G, unsigned* __restrict__ table, unsigned long long* __restrict__ cnt) {
+// One image of a call and its scratch.
+struct MImg {
+  const int32_t* labels;     // W H superpixel labels in [0, K)
+  const int32_t* gt;         // W H ground-truth ids in [0, G)
+  int W, H, K, G;
+  unsigned* table;           // K x G overlap counts
+  uint8_t* sb;               // W H superpixel boundary flags
+  unsigned long long* cnt;   // C_N counters
+};
+
+#define FOR_IMAGE_PIXELS(im, i)                                                                    \
+  const MImg im = imgs[blockIdx.y];                                                                \
+  const long long im##_N = (long long)im.W * im.H;                                                 \
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < im##_N;                 \
+       i += (long long)gridDim.x * blockDim.x)
+
+__global__ void k_overlap(const MImg* __restrict__ imgs) {
   unsigned bad = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const int k = labels[i], g = gt[i];
-    if (k >= 0 && k < K && g >= 0 && g < G) atomicAdd(table + (long long)k * G + g, 1u);
+  const MImg* me = imgs + blockIdx.y;
+  FOR_IMAGE_PIXELS(im, i) {
+    const int k = im.labels[i], g = im.gt[i];
+    if (k >= 0 && k < im.K && g >= 0 && g < im.G) atomicAdd(im.table + (long long)k * im.G + g, 1u);
     else ++bad;
   }
   bad = __reduce_add_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(cnt + C_BAD, (unsigned long long)bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(me->cnt + C_BAD, (unsigned long long)bad);
 }
 
 __device__ __forceinline__ bool is_boundary(const int32_t* __restrict__ m, int W, int H, int x, int y) {
@@ -40,26 +59,24 @@ __device__ __forceinline__ bool is_boundary(const int32_t* __restrict__ m, int W
          (y > 0 && m[(long long)(y - 1) * W + x] != v) || (y + 1 < H && m[(long long)(y + 1) * W + x] != v);
 }
 
-__global__ void k_sp_boundary(const int32_t* __restrict__ labels, int W, int H, uint8_t* __restrict__ sb) {
-  const long long N = (long long)W * H;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const int y = int(i / W), x = int(i - (long long)y * W);
-    sb[i] = is_boundary(labels, W, H, x, y) ? 1 : 0;
+__global__ void k_sp_boundary(const MImg* __restrict__ imgs) {
+  FOR_IMAGE_PIXELS(im, i) {
+    const int y = int(i / im.W), x = int(i - (long long)y * im.W);
+    im.sb[i] = is_boundary(im.labels, im.W, im.H, x, y) ? 1 : 0;
   }
 }
 
-__global__ void __launch_bounds__(256) k_recall(const int32_t* __restrict__ gt, const uint8_t* __restrict__ sb,
-                                                int W, int H, int radius, unsigned long long* __restrict__ cnt) {
-  const long long N = (long long)W * H;
+__global__ void __launch_bounds__(256) k_recall(const MImg* __restrict__ imgs, int radius) {
   unsigned rec = 0, tot = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const int y = int(i / W), x = int(i - (long long)y * W);
-    if (!is_boundary(gt, W, H, x, y)) continue;
+  const MImg* me = imgs + blockIdx.y;
+  FOR_IMAGE_PIXELS(im, i) {
+    const int y = int(i / im.W), x = int(i - (long long)y * im.W);
+    if (!is_boundary(im.gt, im.W, im.H, x, y)) continue;
     ++tot;
     bool hit = false;
-    for (int yy = max(0, y - radius); yy <= min(H - 1, y + radius) && !hit; ++yy)
-      for (int xx = max(0, x - radius); xx <= min(W - 1, x + radius); ++xx)
-        if (sb[(long long)yy * W + xx]) {
+    for (int yy = max(0, y - radius); yy <= min(im.H - 1, y + radius) && !hit; ++yy)
+      for (int xx = max(0, x - radius); xx <= min(im.W - 1, x + radius); ++xx)
+        if (im.sb[(long long)yy * im.W + xx]) {
           hit = true;
           break;
         }
@@ -68,25 +85,25 @@ __global__ void __launch_bounds__(256) k_recall(const int32_t* __restrict__ gt, 
   rec = __reduce_add_sync(0xffffffffu, rec);
   tot = __reduce_add_sync(0xffffffffu, tot);
   if ((threadIdx.x & 31) == 0) {
-    if (rec) atomicAdd(cnt + C_BR_REC, (unsigned long long)rec);
-    if (tot) atomicAdd(cnt + C_BR_TOT, (unsigned long long)tot);
+    if (rec) atomicAdd(me->cnt + C_BR_REC, (unsigned long long)rec);
+    if (tot) atomicAdd(me->cnt + C_BR_TOT, (unsigned long long)tot);
   }
 }
 
-__global__ void __launch_bounds__(256) k_table(const unsigned* __restrict__ table, int K, int G, double eps,
-                                               unsigned long long* __restrict__ cnt) {
+__global__ void __launch_bounds__(256) k_table(const MImg* __restrict__ imgs, double eps) {
+  const MImg im = imgs[blockIdx.y];
   unsigned long long ue = 0, asa = 0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
-    const unsigned* row = table + (long long)k * G;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < im.K; k += gridDim.x * blockDim.x) {
+    const unsigned* row = im.table + (long long)k * im.G;
     unsigned long long size = 0;
     unsigned best = 0;
-    for (int g = 0; g < G; ++g) {
+    for (int g = 0; g < im.G; ++g) {
       size += row[g];
       best = max(best, row[g]);
     }
     asa += best;
     const double lim = eps * double(size);
-    for (int g = 0; g < G; ++g)
+    for (int g = 0; g < im.G; ++g)
       if (double(row[g]) > lim) ue += size;
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -94,14 +111,9 @@ __global__ void __launch_bounds__(256) k_table(const unsigned* __restrict__ tabl
     asa += __shfl_xor_sync(0xffffffffu, asa, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    if (ue) atomicAdd(cnt + C_UE, ue);
-    if (asa) atomicAdd(cnt + C_ASA, asa);
+    if (ue) atomicAdd(im.cnt + C_UE, ue);
+    if (asa) atomicAdd(im.cnt + C_ASA, asa);
   }
-}
-
-int grid_for(long long n, int block) {
-  long long b = (n + block - 1) / block;
-  return int(std::max<long long>(1, std::min<long long>(b, 152LL * 16)));
 }
 
 }  // namespace metrics
@@ -109,51 +121,83 @@ int grid_for(long long n, int block) {
 
 using namespace gmmsp::metrics;
 
-extern "C" gmmsp_status gmmsp_segmentation_metrics(const int32_t* labels_dev, const int32_t* gt_dev, int W, int H,
-                                                   int K, int G, int radius, double eps,
-                                                   gmmsp_seg_metrics* out, void* stream) {
-  if (!labels_dev || !gt_dev || !out || W < 1 || H < 1 || K < 1 || G < 1 || radius < 0 || radius > 64 ||
+extern "C" gmmsp_status gmmsp_segmentation_metrics_many(int n, const int32_t* const* labels_dev,
+                                                        const int32_t* const* gt_dev, const int* W, const int* H,
+                                                        const int* K, const int* G, int radius, double eps,
+                                                        gmmsp_seg_metrics* out, void* stream) {
+  if (n < 1 || n > 65535 || !labels_dev || !gt_dev || !W || !H || !K || !G || !out || radius < 0 || radius > 64 ||
       !(eps >= 0.0 && eps < 1.0))
     return GMMSP_E_INVALID;
-  const long long N = (long long)W * H;
-  const long long cells = (long long)K * G;
-  if (cells > (1LL << 31)) return GMMSP_E_INVALID;
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  std::vector<MImg> host(n);
+  std::vector<size_t> o_table(n), o_sb(n);
+  size_t off = up(sizeof(MImg) * n);                      // image table first
+  const size_t o_cnt = off;
+  off += up(sizeof(unsigned long long) * C_N * n);
+  long long maxN = 0, maxK = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!labels_dev[i] || !gt_dev[i] || W[i] < 1 || H[i] < 1 || K[i] < 1 || G[i] < 1) return GMMSP_E_INVALID;
+    const long long N = (long long)W[i] * H[i], cells = (long long)K[i] * G[i];
+    if (cells > (1LL << 31)) return GMMSP_E_INVALID;
+    o_table[i] = off;
+    off += up(size_t(cells) * 4);
+    o_sb[i] = off;
+    off += up(size_t(N));
+    maxN = std::max(maxN, N);
+    maxK = std::max<long long>(maxK, K[i]);
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t o_table = 0;
-  const size_t o_sb = (size_t(cells) * 4 + 255) & ~size_t(255);
-  const size_t o_cnt = (o_sb + size_t(N) + 255) & ~size_t(255);
-  const size_t bytes = o_cnt + sizeof(unsigned long long) * C_N;
   void* slab = nullptr;
-  cudaError_t e = cudaMalloc(&slab, bytes);
+  cudaError_t e = cudaMalloc(&slab, off);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? GMMSP_E_NOMEM : GMMSP_E_CUDA;
   }
   char* b = static_cast<char*>(slab);
-  unsigned* table = reinterpret_cast<unsigned*>(b + o_table);
-  uint8_t* sb = reinterpret_cast<uint8_t*>(b + o_sb);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(b + o_cnt);
-  unsigned long long host[C_N] = {};
-  e = cudaMemsetAsync(table, 0, size_t(cells) * 4, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(host), s);
-  if (e == cudaSuccess) {
-    k_overlap<<<grid_for(N, 256), 256, 0, s>>>(labels_dev, gt_dev, N, K, G, table, cnt);
-    k_sp_boundary<<<grid_for(N, 256), 256, 0, s>>>(labels_dev, W, H, sb);
-    k_recall<<<grid_for(N, 256), 256, 0, s>>>(gt_dev, sb, W, H, radius, cnt);
-    k_table<<<grid_for(K, 256), 256, 0, s>>>(table, K, G, eps, cnt);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host, cnt, sizeof(host), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (int i = 0; i < n; ++i)
+    host[i] = MImg{labels_dev[i], gt_dev[i], W[i], H[i], K[i], G[i], reinterpret_cast<unsigned*>(b + o_table[i]),
+                   reinterpret_cast<uint8_t*>(b + o_sb[i]), cnt + size_t(C_N) * i};
+  MImg* table = reinterpret_cast<MImg*>(b);
+  std::vector<unsigned long long> hc(size_t(C_N) * n, 0ull);
+  // pixel kernels: enough blocks per image to fill the machine across the images
+  const unsigned per = unsigned(std::max<long long>(1, std::min<long long>((maxN + 255) / 256, (152LL * 16 + n - 1) / n)));
+  const unsigned perk = unsigned(std::max<long long>(1, std::min<long long>((maxK + 255) / 256, (152LL * 16 + n - 1) / n)));
+  do {
+    if ((e = cudaMemcpyAsync(table, host.data(), sizeof(MImg) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(b + o_cnt, 0, off - o_cnt, s)) != cudaSuccess) break;  // counters and tables
+    k_overlap<<<dim3(per, n), 256, 0, s>>>(table);
+    k_sp_boundary<<<dim3(per, n), 256, 0, s>>>(table);
+    k_recall<<<dim3(per, n), 256, 0, s>>>(table, radius);
+    k_table<<<dim3(perk, n), 256, 0, s>>>(table, eps);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * C_N * n, cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+      break;
+    e = cudaStreamSynchronize(s);
+  } while (false);
   cudaFree(slab);
   if (e != cudaSuccess) return GMMSP_E_CUDA;
-  if (host[C_BAD]) return GMMSP_E_INVALID;
-  out->br_recovered = (long long)host[C_BR_REC];
-  out->br_total = (long long)host[C_BR_TOT];
-  out->ue_sum = (long long)host[C_UE];
-  out->asa_sum = (long long)host[C_ASA];
-  out->br = out->br_total ? double(out->br_recovered) / double(out->br_total) : 1.0;
-  out->ue = double(out->ue_sum) / double(N) - 1.0;
-  out->asa = double(out->asa_sum) / double(N);
-  return GMMSP_OK;
+  gmmsp_status st = GMMSP_OK;
+  for (int i = 0; i < n; ++i) {
+    const unsigned long long* h = hc.data() + size_t(C_N) * i;
+    const double N = double((long long)W[i] * H[i]);
+    gmmsp_seg_metrics& o = out[i];
+    if (h[C_BAD]) st = GMMSP_E_INVALID;
+    o.br_recovered = (long long)h[C_BR_REC];
+    o.br_total = (long long)h[C_BR_TOT];
+    o.ue_sum = (long long)h[C_UE];
+    o.asa_sum = (long long)h[C_ASA];
+    o.br = o.br_total ? double(o.br_recovered) / double(o.br_total) : 1.0;
+    o.ue = double(o.ue_sum) / N - 1.0;
+    o.asa = double(o.asa_sum) / N;
+  }
+  return st;
+}
+
+extern "C" gmmsp_status gmmsp_segmentation_metrics(const int32_t* labels_dev, const int32_t* gt_dev, int W, int H,
+                                                   int K, int G, int radius, double eps,
+                                                   gmmsp_seg_metrics* out, void* stream) {
+  if (!labels_dev || !gt_dev || !out) return GMMSP_E_INVALID;
+  return gmmsp_segmentation_metrics_many(1, &labels_dev, &gt_dev, &W, &H, &K, &G, radius, eps, out, stream);
 }

@@ -8,7 +8,7 @@ studies on BSDS500, which is not available here; these run on the seeded
 synthetic Voronoi images of the training and evaluation workload (481x321,
 150 regions, noise sigma 8, held-out seeds), whose region map is the ground
 truth.  Every segmentation and every score runs in the library's kernels
-(batch contexts, gmmsp_segmentation_metrics); this module only sequences
+(batch contexts, gmmsp_segmentation_metrics_many); this module only sequences
 the calls.
 
 Command line:
@@ -23,7 +23,7 @@ import json
 
 import numpy as np
 
-from . import SuperpixelsBatch, gmmsp_segmentation_metrics
+from . import SuperpixelsBatch, gmmsp_segmentation_metrics_many
 from .learned_init import HELD_OUT_SEED0, TRAIN
 
 SPACINGS = (10, 15, 20, 30)   # 1,536 / 672 / 384 / 160 superpixels at 481x321
@@ -37,8 +37,8 @@ def _images(seeds, buf, regs):
 
 def _scores(labels, regs, K, take):
     acc = {"br": [], "ue": [], "asa": []}
-    for i in range(take):
-        m = gmmsp_segmentation_metrics(labels[i], regs[i], K, TRAIN["regions"])
+    for m in gmmsp_segmentation_metrics_many(list(labels[:take]), [regs[i] for i in range(take)], K,
+                                             TRAIN["regions"]):
         for key in acc:
             acc[key].append(m[key])
     return acc

@@ -63,3 +63,26 @@ def test_out_of_range_is_rejected(gm):
     labels[3, 3] = 9
     with pytest.raises(gm.GmmspError):
         gpu_metrics(gm, labels, np.zeros((8, 8), dtype=np.int32), 5, 1)
+
+
+def test_many_equals_oracle_per_image(gm):
+    """The batched call over images of different sizes, label counts and segment counts."""
+    import torch
+    rng = np.random.default_rng(5)
+    cases = [(12, 9, 7, 4), (37, 23, 50, 6), (64, 80, 300, 12), (5, 5, 3, 2), (40, 33, 20, 20)]
+    labels, gts, refs = [], [], []
+    for H, W, K, G in cases:
+        lab = rng.integers(0, K, (H, W))
+        gt = rng.integers(0, G, (H, W))
+        labels.append(torch.from_numpy(lab.astype(np.int32)).cuda())
+        gts.append(torch.from_numpy(gt.astype(np.int32)).cuda())
+        refs.append(om.all_metrics(lab, gt, 2, 0.05))
+    out = gm.gmmsp_segmentation_metrics_many(labels, gts, [c[2] for c in cases], [c[3] for c in cases])
+    for m, ref in zip(out, refs):
+        check_equal(m, ref)
+    # one image out of range fails the call
+    bad = labels[1].clone()
+    bad[0, 0] = 10_000
+    with pytest.raises(gm.GmmspError):
+        gm.gmmsp_segmentation_metrics_many([labels[0], bad], gts[:2], [cases[0][2], cases[1][2]],
+                                           [cases[0][3], cases[1][3]])
