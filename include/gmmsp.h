@@ -279,6 +279,10 @@ gmmsp_status gmmsp_batch_set_launch(gmmsp_batch b, int blocks_per_sm);
  * two finalize times the autotuner measured (ms; 0 before gmmsp_batch_autotune).
  * Any pointer may be NULL. */
 gmmsp_status gmmsp_batch_get_tuning(gmmsp_batch b, int *blocks_per_sm, int *finalize16, double *finalize_ms);
+/* Sets both launch choices, e.g. from a tuning cache (blocks_per_sm 1..16,
+ * finalize16 0 or 1; finalize16 has an effect only where the 16-lane
+ * finalize applies: mixed precision, full colour model). */
+gmmsp_status gmmsp_batch_set_tuning(gmmsp_batch b, int blocks_per_sm, int finalize16);
 gmmsp_status gmmsp_batch_info(gmmsp_batch b, long long *total_pixels, int *total_k, int *total_cells);
 const char *gmmsp_batch_last_error(gmmsp_batch b);
 void gmmsp_batch_destroy(gmmsp_batch b);

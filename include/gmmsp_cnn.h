@@ -70,6 +70,15 @@ gmmsp_status gmmsp_net_create(gmmsp_net *out, int spacing, void *stream);
 gmmsp_status gmmsp_net_set_weights(gmmsp_net n, const float *host, long long count);
 gmmsp_status gmmsp_net_get_weights(gmmsp_net n, float *host, long long count);
 
+/* Optimiser state in / out (host): the Adam first and second moments
+ * (count = gmmsp_net_param_count() floats each) and the step count, so that
+ * a checkpoint resumes training where it stopped (set after set_weights,
+ * which clears the state).  v must be >= 0 and everything finite
+ * (GMMSP_E_INVALID otherwise).  Both synchronise. */
+gmmsp_status gmmsp_net_get_adam(gmmsp_net n, float *m_host, float *v_host, long long count, long long *step);
+gmmsp_status gmmsp_net_set_adam(gmmsp_net n, const float *m_host, const float *v_host, long long count,
+                                long long step);
+
 /* Forward pass over B images: out_dev receives B n_y n_x x GMMSP_NET_CHANNELS
  * float32 (superpixel-major, k = k_y n_x + k_x within an image).  The first
  * call for a larger batch allocates workspace. */

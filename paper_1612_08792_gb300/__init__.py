@@ -27,11 +27,11 @@ __all__ = [
     "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_set_timing", "gmmsp_get_timing", "gmmsp_set_launch", "gmmsp_get_launch",
     "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "SuperpixelsBatch",
     "gmmsp_batch_create", "gmmsp_batch_segment", "gmmsp_batch_get_params", "gmmsp_batch_autotune",
-    "gmmsp_batch_set_launch", "gmmsp_batch_info", "gmmsp_batch_destroy", "gmmsp_status_string", "gmmsp_destroy",
+    "gmmsp_batch_set_launch", "gmmsp_batch_set_tuning", "gmmsp_batch_info", "gmmsp_batch_destroy", "gmmsp_status_string", "gmmsp_destroy",
     "gmmsp_batch_get_tuning", "gmmsp_batch_set_init_net", "gmmsp_batch_lab", "gmmsp_batch_targets",
     "gmmsp_net_param_count", "gmmsp_net_create", "gmmsp_net_set_weights", "gmmsp_net_get_weights",
     "gmmsp_net_forward", "gmmsp_net_grad", "gmmsp_net_adam", "gmmsp_net_train_step", "gmmsp_net_get_activation",
-    "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
+    "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_net_get_adam", "gmmsp_net_set_adam", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
     "GMMSP_OK", "GMMSP_E_INVALID", "GMMSP_E_CUDA", "GMMSP_E_NOMEM", "GMMSP_E_NUMERIC", "GMMSP_E_TIMEOUT",
     "GMMSP_E_STATE", "gmmsp_segmentation_metrics", "gmmsp_enforce_connectivity", "gmmsp_connectivity",
     "gmmsp_batch_connectivity", "gmmsp_segmentation_metrics_many", "GMMSP_GRAY8", "GMMSP_COLOUR_FULL", "GMMSP_COLOUR_SPLIT", "GMMSP_COLOUR_GRAY",
@@ -316,6 +316,7 @@ def _batch_lib():
             "gmmsp_batch_get_params": (I, [P, I, P, P, P]),
             "gmmsp_batch_autotune": (I, [P, P, P, P, I, pint, P]),
             "gmmsp_batch_set_launch": (I, [P, I]),
+            "gmmsp_batch_set_tuning": (I, [P, I, I]),
             "gmmsp_batch_info": (I, [P, ctypes.POINTER(ctypes.c_longlong), pint, pint]),
             "gmmsp_batch_get_tuning": (I, [P, pint, pint, P]),
             "gmmsp_batch_last_error": (ctypes.c_char_p, [P]),
@@ -382,6 +383,10 @@ def gmmsp_batch_set_launch(b, blocks_per_sm: int) -> None:
     _bcheck(b, _batch_lib().gmmsp_batch_set_launch(b, int(blocks_per_sm)))
 
 
+def gmmsp_batch_set_tuning(b, blocks_per_sm: int, finalize16: bool) -> None:
+    _bcheck(b, _batch_lib().gmmsp_batch_set_tuning(b, int(blocks_per_sm), 1 if finalize16 else 0))
+
+
 def gmmsp_batch_info(b):
     pix, K, cells = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
     _bcheck(b, _batch_lib().gmmsp_batch_info(b, ctypes.byref(pix), ctypes.byref(K), ctypes.byref(cells)))
@@ -413,6 +418,8 @@ def _net_lib():
             "gmmsp_net_create": (I, [PP, I, P]),
             "gmmsp_net_set_weights": (I, [P, P, LL]),
             "gmmsp_net_get_weights": (I, [P, P, LL]),
+            "gmmsp_net_get_adam": (I, [P, P, P, LL, ctypes.POINTER(LL)]),
+            "gmmsp_net_set_adam": (I, [P, P, P, LL, LL]),
             "gmmsp_net_forward": (I, [P, P, I, I, I, P]),
             "gmmsp_net_grad": (I, [P, P, I, I, I, P, P, PD]),
             "gmmsp_net_adam": (I, [P, F, F, F, F]),
@@ -460,6 +467,25 @@ def gmmsp_net_get_weights(n):
     w = np.zeros(gmmsp_net_param_count(), dtype=np.float32)
     _ncheck(n, _net_lib().gmmsp_net_get_weights(n, w.ctypes.data_as(ctypes.c_void_p), w.size))
     return w
+
+
+def gmmsp_net_get_adam(n):
+    """(m, v, step): the Adam moments (float32 host arrays) and the step count."""
+    m = np.zeros(gmmsp_net_param_count(), dtype=np.float32)
+    v = np.zeros_like(m)
+    step = ctypes.c_longlong()
+    _ncheck(n, _net_lib().gmmsp_net_get_adam(n, m.ctypes.data_as(ctypes.c_void_p), v.ctypes.data_as(ctypes.c_void_p),
+                                             m.size, ctypes.byref(step)))
+    return m, v, int(step.value)
+
+
+def gmmsp_net_set_adam(n, m, v, step: int) -> None:
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    if m.shape != v.shape:
+        raise ValueError("m and v must have one shape")
+    _ncheck(n, _net_lib().gmmsp_net_set_adam(n, m.ctypes.data_as(ctypes.c_void_p), v.ctypes.data_as(ctypes.c_void_p),
+                                             m.size, int(step)))
 
 
 def gmmsp_net_forward(n, lab_ptr: int, B: int, W: int, H: int, out) -> None:
@@ -641,6 +667,7 @@ class SuperpixelsBatch:
         p.input_format = GMMSP_GRAY8 if gray_input else (GMMSP_LAB32 if lab_input else GMMSP_RGB8)
         p.precision = int(precision)
         p.colour_model = colour_model(colour)
+        self.params = (int(spacing), int(K), int(p.colour_model), int(precision))
         self.shapes = [(int(h), int(w)) for (h, w) in shapes]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.b = gmmsp_batch_create([w for _, w in self.shapes], [h for h, _ in self.shapes], p, self.stream)
@@ -655,8 +682,29 @@ class SuperpixelsBatch:
                                  want_loglik)
         return (self.labels, ll) if want_loglik else self.labels
 
-    def autotune(self, images, reps: int = 3):
-        return gmmsp_batch_autotune(self.b, images, [self._pitch(t) for t in images], self.labels, reps)
+    def autotune(self, images, reps: int = 3, cache: str | None = None):
+        """Times the E + M pass variants and the finalize variants and keeps the fastest;
+        returns (blocks per SM, {blocks per SM: ms}).  With `cache` (a JSON file path) a
+        tuning stored there for this GPU and batch shape is applied without timing, and a
+        new tuning is stored."""
+        key = None
+        if cache:
+            import torch
+            from . import tuning_cache
+            spacing, K, colour, precision = self.params
+            key = tuning_cache.batch_key(torch.cuda.get_device_name(), self.shapes, spacing, K, colour, precision)
+            hit = tuning_cache.lookup(cache, key)
+            if hit is not None:
+                gmmsp_batch_set_tuning(self.b, hit["blocks_per_sm"], hit["finalize16"])
+                return hit["blocks_per_sm"], {int(k): float(v) for k, v in hit.get("em_pass_ms", {}).items()}
+        best, times = gmmsp_batch_autotune(self.b, images, [self._pitch(t) for t in images], self.labels, reps)
+        if key is not None:
+            from . import tuning_cache
+            t = self.tuning()
+            tuning_cache.store(cache, key, {"blocks_per_sm": int(best), "finalize16": bool(t["finalize16"]),
+                                            "em_pass_ms": {str(k): v for k, v in times.items()},
+                                            "finalize_ms": t["finalize_ms"]})
+        return best, times
 
     def set_launch(self, blocks_per_sm: int) -> None:
         gmmsp_batch_set_launch(self.b, blocks_per_sm)

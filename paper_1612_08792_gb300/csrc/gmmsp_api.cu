@@ -282,6 +282,7 @@ const char* gmmsp_last_error(gmmsp_ctx c) { return c ? c->err.c_str() : "null co
 
 gmmsp_status gmmsp_init(gmmsp_ctx* out, const void* image_dev, int width, int height,
                         int pitch_bytes, const gmmsp_params* p, void* stream) {
+  GMMSP_NVTX("gmmsp_init");
   if (!out) return GMMSP_E_INVALID;
   *out = nullptr;
   if (!p || !image_dev || width < 1 || height < 1) return GMMSP_E_INVALID;
@@ -356,6 +357,7 @@ gmmsp_status gmmsp_init(gmmsp_ctx* out, const void* image_dev, int width, int he
 }
 
 gmmsp_status gmmsp_reinit(gmmsp_ctx c, const void* image_dev, int pitch_bytes) {
+  GMMSP_NVTX("gmmsp_reinit");
   if (!c) return GMMSP_E_INVALID;
   if (!image_dev) return fail(c, GMMSP_E_INVALID, "null image");
   if (pitch_bytes < row_bytes(c->p.input_format, c->g.W)) return fail(c, GMMSP_E_INVALID, "pitch too small");
@@ -366,6 +368,7 @@ gmmsp_status gmmsp_reinit(gmmsp_ctx c, const void* image_dev, int pitch_bytes) {
 }
 
 gmmsp_status gmmsp_em_iters(gmmsp_ctx c, int iters, double* loglik_host) {
+  GMMSP_NVTX("gmmsp_em_iters");
   gmmsp_status st = check_ready(c);
   if (st != GMMSP_OK) return st;
   if (iters < 0) return fail(c, GMMSP_E_INVALID, "iters < 0");
@@ -386,6 +389,7 @@ gmmsp_status gmmsp_em_iters(gmmsp_ctx c, int iters, double* loglik_host) {
 }
 
 gmmsp_status gmmsp_labels(gmmsp_ctx c, int32_t* labels_dev, double* loglik_host) {
+  GMMSP_NVTX("gmmsp_labels");
   gmmsp_status st = check_ready(c);
   if (st != GMMSP_OK) return st;
   if (!labels_dev) return fail(c, GMMSP_E_INVALID, "null labels");
@@ -402,6 +406,7 @@ gmmsp_status gmmsp_labels(gmmsp_ctx c, int32_t* labels_dev, double* loglik_host)
 
 gmmsp_status gmmsp_segment(gmmsp_ctx c, const void* image_dev, int pitch_bytes, int iters,
                            int32_t* labels_dev, double* loglik_host) {
+  GMMSP_NVTX("gmmsp_segment");
   if (!c) return GMMSP_E_INVALID;
   if (!image_dev || !labels_dev) return fail(c, GMMSP_E_INVALID, "null image or labels");
   if (iters < 0 || iters + 1 > kLlkCap) return fail(c, GMMSP_E_INVALID, "iters out of range");
@@ -527,6 +532,7 @@ gmmsp_status gmmsp_set_params(gmmsp_ctx c, const double* mu_host, const double* 
 }
 
 gmmsp_status gmmsp_connectivity(gmmsp_ctx c, int32_t* labels_dev, gmmsp_conn_stats* stats_host) {
+  GMMSP_NVTX("gmmsp_connectivity");
   gmmsp_status st = check_ready(c);
   if (st != GMMSP_OK) return st;
   if (!labels_dev) return fail(c, GMMSP_E_INVALID, "null labels");
@@ -537,6 +543,7 @@ gmmsp_status gmmsp_connectivity(gmmsp_ctx c, int32_t* labels_dev, gmmsp_conn_sta
 }
 
 gmmsp_status gmmsp_init_from_net(gmmsp_ctx c, gmmsp_net n) {
+  GMMSP_NVTX("gmmsp_init_from_net");
   gmmsp_status st = check_ready(c);
   if (st != GMMSP_OK) return st;
   if (!n) return fail(c, GMMSP_E_INVALID, "null network");

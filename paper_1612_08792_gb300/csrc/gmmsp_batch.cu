@@ -293,6 +293,7 @@ gmmsp_status gmmsp_batch_info(gmmsp_batch b, long long* total_pixels, int* total
 
 gmmsp_status gmmsp_batch_segment(gmmsp_batch b, const void* const* images_dev, const int* pitches, int iters,
                                  int32_t* const* labels_dev, double* loglik_host) {
+  GMMSP_NVTX("gmmsp_batch_segment");
   if (!b) return GMMSP_E_INVALID;
   if (!images_dev || !pitches || !labels_dev || iters < 0) return bfail(b, GMMSP_E_INVALID, "bad arguments");
   if (b->state == GMMSP_E_CUDA || b->state == GMMSP_E_NOMEM) return GMMSP_E_STATE;
@@ -359,6 +360,14 @@ gmmsp_status gmmsp_batch_get_params(gmmsp_batch b, int i, double* mu_host, doubl
   return GMMSP_OK;
 }
 
+gmmsp_status gmmsp_batch_set_tuning(gmmsp_batch b, int blocks_per_sm, int finalize16) {
+  if (!b || blocks_per_sm < 1 || blocks_per_sm > 16 || finalize16 < 0 || finalize16 > 1) return GMMSP_E_INVALID;
+  b->blocks_per_sm = blocks_per_sm;
+  b->fin16 = finalize16 != 0;
+  drop_graph(b);
+  return GMMSP_OK;
+}
+
 gmmsp_status gmmsp_batch_set_launch(gmmsp_batch b, int blocks_per_sm) {
   if (!b || blocks_per_sm < 1 || blocks_per_sm > 16) return GMMSP_E_INVALID;
   b->blocks_per_sm = blocks_per_sm;
@@ -367,6 +376,7 @@ gmmsp_status gmmsp_batch_set_launch(gmmsp_batch b, int blocks_per_sm) {
 
 gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void* const* images_dev, const int* pitches,
                                   int32_t* const* labels_dev, int reps, int* best, double* times_ms) {
+  GMMSP_NVTX("gmmsp_batch_autotune");
   if (!b || reps < 1) return GMMSP_E_INVALID;
   gmmsp_status st = upload_table(b, images_dev, pitches, labels_dev);
   if (st != GMMSP_OK) return st;
@@ -451,6 +461,7 @@ gmmsp_status gmmsp_batch_set_init_net(gmmsp_batch b, gmmsp_net net) {
 }
 
 gmmsp_status gmmsp_batch_connectivity(gmmsp_batch b, int32_t* const* labels_dev, gmmsp_conn_stats* stats_host) {
+  GMMSP_NVTX("gmmsp_batch_connectivity");
   if (!b || !labels_dev) return GMMSP_E_INVALID;
   std::vector<int> W(b->n), H(b->n), K(b->n);
   std::vector<const float*> lab(b->n);
@@ -475,6 +486,7 @@ gmmsp_status gmmsp_batch_lab(gmmsp_batch b, const float** lab_dev) {
 }
 
 gmmsp_status gmmsp_batch_targets(gmmsp_batch b, float* target_dev) {
+  GMMSP_NVTX("gmmsp_batch_targets");
   if (!b || !target_dev) return GMMSP_E_INVALID;
   if (!b->uniform) return bfail(b, GMMSP_E_INVALID, "targets need images of one size");
   if (b->p.colour_model != GMMSP_COLOUR_FULL) return bfail(b, GMMSP_E_INVALID, "targets need the full colour model");

@@ -1066,7 +1066,32 @@ gmmsp_status gmmsp_net_get_weights(gmmsp_net n, float* host, long long count) {
   return GMMSP_OK;
 }
 
+gmmsp_status gmmsp_net_get_adam(gmmsp_net n, float* m_host, float* v_host, long long count, long long* step) {
+  if (!n) return GMMSP_E_INVALID;
+  if (!m_host || !v_host || !step || count != n->pl.total) return nfail(n, GMMSP_E_INVALID, "bad arguments");
+  GN_CHECK(n, cudaMemcpyAsync(m_host, n->m, size_t(count) * 4, cudaMemcpyDeviceToHost, n->stream));
+  GN_CHECK(n, cudaMemcpyAsync(v_host, n->vv, size_t(count) * 4, cudaMemcpyDeviceToHost, n->stream));
+  GN_CHECK(n, cudaStreamSynchronize(n->stream));
+  *step = n->adam_t;
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_net_set_adam(gmmsp_net n, const float* m_host, const float* v_host, long long count,
+                                long long step) {
+  if (!n) return GMMSP_E_INVALID;
+  if (!m_host || !v_host || count != n->pl.total || step < 0) return nfail(n, GMMSP_E_INVALID, "bad arguments");
+  for (long long i = 0; i < count; ++i)
+    if (!isfinite(m_host[i]) || !(v_host[i] >= 0.f) || !isfinite(v_host[i]))
+      return nfail(n, GMMSP_E_INVALID, "non-finite or negative optimiser state");
+  GN_CHECK(n, cudaMemcpyAsync(n->m, m_host, size_t(count) * 4, cudaMemcpyHostToDevice, n->stream));
+  GN_CHECK(n, cudaMemcpyAsync(n->vv, v_host, size_t(count) * 4, cudaMemcpyHostToDevice, n->stream));
+  GN_CHECK(n, cudaStreamSynchronize(n->stream));
+  n->adam_t = step;
+  return GMMSP_OK;
+}
+
 gmmsp_status gmmsp_net_forward(gmmsp_net n, const float* lab_dev, int B, int W, int H, float* out_dev) {
+  GMMSP_NVTX("gmmsp_net_forward");
   if (!n) return GMMSP_E_INVALID;
   Geom g;
   if (!lab_dev || !out_dev || B < 1 || !net_geom(n, W, H, &g)) return nfail(n, GMMSP_E_INVALID, "bad arguments");
@@ -1078,6 +1103,7 @@ gmmsp_status gmmsp_net_forward(gmmsp_net n, const float* lab_dev, int B, int W, 
 
 gmmsp_status gmmsp_net_grad(gmmsp_net n, const float* lab_dev, int B, int W, int H, const float* target_dev,
                             float* grad_host, double* loss_host) {
+  GMMSP_NVTX("gmmsp_net_grad");
   if (!n) return GMMSP_E_INVALID;
   Geom g;
   if (!lab_dev || !target_dev || B < 1 || !net_geom(n, W, H, &g))
@@ -1111,6 +1137,7 @@ gmmsp_status gmmsp_net_adam(gmmsp_net n, float lr, float beta1, float beta2, flo
 
 gmmsp_status gmmsp_net_train_step(gmmsp_net n, const float* lab_dev, int B, int W, int H,
                                   const float* target_dev, float lr, double* loss_host) {
+  GMMSP_NVTX("gmmsp_net_train_step");
   gmmsp_status st = gmmsp_net_grad(n, lab_dev, B, W, H, target_dev, nullptr, nullptr);
   if (st != GMMSP_OK) return st;
   st = gmmsp_net_adam(n, lr, 0.9f, 0.999f, 1e-8f);

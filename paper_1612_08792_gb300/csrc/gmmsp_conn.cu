@@ -685,6 +685,7 @@ __global__ void k_relabel(const Img* __restrict__ imgs, Scratch S) {
 gmmsp_status enforce_connectivity_many(int n, const int* W, const int* H, const int* K, int32_t* const* labels,
                                        const float* const* lab, gmmsp_conn_stats* stats, cudaStream_t s,
                                        ConnScratch* cache) {
+  GMMSP_NVTX("enforce_connectivity_many");
   using namespace conn;
   if (n < 1 || n > 65535) return GMMSP_E_INVALID;
   std::vector<Img> host(n);

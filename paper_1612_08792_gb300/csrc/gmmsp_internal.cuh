@@ -17,7 +17,32 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define GMMSP_HAVE_NVTX 1
+#endif
+
 namespace gmmsp {
+
+// An NVTX range around a C entry point (named in profiler timelines; free
+// when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) {
+#ifdef GMMSP_HAVE_NVTX
+    nvtxRangePushA(name);
+#else
+    (void)name;
+#endif
+  }
+  ~NvtxRange() {
+#ifdef GMMSP_HAVE_NVTX
+    nvtxRangePop();
+#endif
+  }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define GMMSP_NVTX(name) ::gmmsp::NvtxRange gmmsp_nvtx_range_(name)
 
 constexpr int kSlots = 9;          // |K_i| <= 9
 constexpr int kStats = 15;         // W, S1[5], S2s[3], S2c[6]

@@ -19,6 +19,7 @@
 
 #include "../../include/gmmsp.h"
 #include "../../include/gmmsp_metrics.h"
+#include "gmmsp_internal.cuh"
 
 namespace gmmsp {
 namespace metrics {
@@ -125,6 +126,7 @@ extern "C" gmmsp_status gmmsp_segmentation_metrics_many(int n, const int32_t* co
                                                         const int32_t* const* gt_dev, const int* W, const int* H,
                                                         const int* K, const int* G, int radius, double eps,
                                                         gmmsp_seg_metrics* out, void* stream) {
+  GMMSP_NVTX("gmmsp_segmentation_metrics_many");
   if (n < 1 || n > 65535 || !labels_dev || !gt_dev || !W || !H || !K || !G || !out || radius < 0 || radius > 64 ||
       !(eps >= 0.0 && eps < 1.0))
     return GMMSP_E_INVALID;

@@ -24,8 +24,8 @@ import time
 import numpy as np
 
 from . import (SuperpixelsBatch, gmmsp_net_check, gmmsp_net_create, gmmsp_net_destroy, gmmsp_net_forward,
-               gmmsp_net_get_weights, gmmsp_net_grad, gmmsp_net_param_count, gmmsp_net_set_weights,
-               gmmsp_net_train_step, gmmsp_segmentation_metrics)
+               gmmsp_net_get_adam, gmmsp_net_get_weights, gmmsp_net_grad, gmmsp_net_param_count,
+               gmmsp_net_set_adam, gmmsp_net_set_weights, gmmsp_net_train_step, gmmsp_segmentation_metrics)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS_DIR = os.path.join(HERE, "weights")
@@ -98,15 +98,24 @@ class InitNet:
     def check(self) -> None:
         gmmsp_net_check(self.n)
 
-    def save(self, path: str, meta: dict | None = None) -> None:
+    def save(self, path: str, meta: dict | None = None, optimizer: bool = False) -> None:
+        """One .npz file: the weights, the spacing, `meta` and, with `optimizer`, the Adam
+        moments and step count (a training checkpoint that resumes exactly)."""
         os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
-        np.savez(path, weights=self.get_weights(), spacing=self.spacing,
-                 meta=json.dumps(meta or {}))
+        extra = {}
+        if optimizer:
+            m, v, step = gmmsp_net_get_adam(self.n)
+            extra = dict(adam_m=m, adam_v=v, adam_step=step)
+        np.savez(path, weights=self.get_weights(), spacing=self.spacing, meta=json.dumps(meta or {}), **extra)
 
     @classmethod
     def load(cls, path: str, stream=None) -> "InitNet":
+        """A network from save(); the optimiser state too when the file holds it."""
         z = np.load(path)
-        return cls(int(z["spacing"]), weights=z["weights"], stream=stream)
+        net = cls(int(z["spacing"]), weights=z["weights"], stream=stream)
+        if "adam_m" in z.files:
+            gmmsp_net_set_adam(net.n, z["adam_m"], z["adam_v"], int(z["adam_step"]))
+        return net
 
     def close(self) -> None:
         if getattr(self, "n", None):

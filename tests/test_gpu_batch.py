@@ -96,3 +96,25 @@ def test_batch_rejects_bad_arguments(gm):
     p.spacing = 12
     with pytest.raises(gm.GmmspError):
         gm.gmmsp_batch_create([320, 5], [240, 5], p)  # second image smaller than the spacing
+
+
+def test_tuning_cache_applies_stored_choices(gm, tmp_path):
+    import torch
+    from synth.voronoi_torch import voronoi_batch
+    path = str(tmp_path / "tuning.json")
+    buf = voronoi_batch(481, 321, 150, 8.0, [1, 2, 3, 4])
+    imgs = [buf[i] for i in range(4)]
+    a = gm.SuperpixelsBatch([(321, 481)] * 4, spacing=15)
+    best, times = a.autotune(imgs, reps=1, cache=path)
+    ref = [x.clone() for x in a.segment(imgs, iters=3)]
+    tun = a.tuning()
+    a.close()
+    b = gm.SuperpixelsBatch([(321, 481)] * 4, spacing=15)
+    b.set_launch(3 if best != 3 else 4)
+    best2, times2 = b.autotune(imgs, reps=1, cache=path)      # served from the cache
+    assert best2 == best and times2 == times
+    assert b.tuning()["blocks_per_sm"] == tun["blocks_per_sm"]
+    assert b.tuning()["finalize16"] == tun["finalize16"]
+    for x, y in zip(b.segment(imgs, iters=3), ref):
+        assert (x.cpu().numpy() == y.cpu().numpy()).mean() >= 0.9999
+    b.close()

@@ -242,3 +242,38 @@ def test_bounded_wait_gives_up_and_context_survives(gm):
     ref, _ = ocnn.forward(w, lab, v, emulate_bf16=True)
     assert rel_l2(out, ref) < 2e-3
     net.close()
+
+
+def test_checkpoint_with_optimizer_resumes_exactly(gm, tmp_path):
+    """Training k + k steps through a save/load with the Adam state equals 2k steps."""
+    import torch
+    from paper_1612_08792_gb300.learned_init import InitNet, init_weights
+    W, H, v, B = 64, 50, 9, 2
+    lab = torch.from_numpy(lab_planes([70, 71], W, H)).cuda()
+    K = (W // v) * (H // v)
+    tgt = torch.from_numpy(np.random.default_rng(72).normal(0, 1, (B * K, 10)).astype(np.float32)).cuda()
+    w0 = init_weights(19)
+    ref = InitNet(v, weights=w0)
+    for _ in range(6):
+        ref.train_step(lab.data_ptr(), B, W, H, tgt, 1e-3, want_loss=False)
+    a = InitNet(v, weights=w0)
+    for _ in range(3):
+        a.train_step(lab.data_ptr(), B, W, H, tgt, 1e-3, want_loss=False)
+    path = str(tmp_path / "ckpt.npz")
+    a.save(path, optimizer=True)
+    b = InitNet.load(path)
+    m, v2, step = gm.gmmsp_net_get_adam(b.n)
+    assert step == 3 and np.all(v2 >= 0)
+    for _ in range(3):
+        b.train_step(lab.data_ptr(), B, W, H, tgt, 1e-3, want_loss=False)
+    np.testing.assert_array_equal(b.get_weights(), ref.get_weights())
+    # without the optimiser state the resumed run differs (Adam restarts)
+    a.save(path)
+    c = InitNet.load(path)
+    for _ in range(3):
+        c.train_step(lab.data_ptr(), B, W, H, tgt, 1e-3, want_loss=False)
+    assert not np.array_equal(c.get_weights(), ref.get_weights())
+    with pytest.raises(gm.GmmspError):
+        gm.gmmsp_net_set_adam(c.n, m, -np.ones_like(v2), 1)
+    for net in (ref, a, b, c):
+        net.close()
