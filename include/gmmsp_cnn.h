@@ -138,6 +138,21 @@ void gmmsp_net_destroy(gmmsp_net n);
  *   network outputs) from b's current theta, e.g. after many EM iterations.
  *   All images of b must have one size; the full colour model only. */
 gmmsp_status gmmsp_init_from_net(gmmsp_ctx c, gmmsp_net n);
+
+/* gmmsp_set_init: replaces theta of a single-image context by theta_0 built
+ * from a caller's per-superpixel predictions in the network's output
+ * parametrisation (device float32, K x 5 each, superpixel k = k_y n_x + k_x):
+ *   dmu_dev     mean offsets from the cell's centre pixel (x_c, y_c, z_c):
+ *               (dx, dy) in units of the spacing v, (dL, da, db) in units
+ *               of 10 CIELAB;
+ *   logeig_dev  logs of the covariance diagonals, Sigma_s in units of v^2
+ *               (2 values), Sigma_c in units of lambda_c^2 (3 values),
+ *               clipped to [-10, 10];
+ * the spatial mean is clipped to the superpixel's window (Eq. Ik) and the
+ * eigenvalues are floored at eps_s, eps_c (Eq. mlams, mlamc).  Not for the
+ * grayscale model (GMMSP_E_INVALID).  A non-finite result is reported as
+ * GMMSP_E_NUMERIC at the next synchronising call. */
+gmmsp_status gmmsp_set_init(gmmsp_ctx c, const float *dmu_dev, const float *logeig_dev);
 gmmsp_status gmmsp_batch_set_init_net(gmmsp_batch b, gmmsp_net n);
 gmmsp_status gmmsp_batch_lab(gmmsp_batch b, const float **lab_dev);
 gmmsp_status gmmsp_batch_targets(gmmsp_batch b, float *target_dev);

@@ -31,7 +31,7 @@ __all__ = [
     "gmmsp_batch_get_tuning", "gmmsp_batch_set_init_net", "gmmsp_batch_lab", "gmmsp_batch_targets",
     "gmmsp_net_param_count", "gmmsp_net_create", "gmmsp_net_set_weights", "gmmsp_net_get_weights",
     "gmmsp_net_forward", "gmmsp_net_grad", "gmmsp_net_adam", "gmmsp_net_train_step", "gmmsp_net_get_activation",
-    "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_net_get_adam", "gmmsp_net_set_adam", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
+    "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_net_get_adam", "gmmsp_net_set_adam", "gmmsp_set_init", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
     "GMMSP_OK", "GMMSP_E_INVALID", "GMMSP_E_CUDA", "GMMSP_E_NOMEM", "GMMSP_E_NUMERIC", "GMMSP_E_TIMEOUT",
     "GMMSP_E_STATE", "gmmsp_segmentation_metrics", "gmmsp_enforce_connectivity", "gmmsp_connectivity",
     "gmmsp_batch_connectivity", "gmmsp_segmentation_metrics_many", "GMMSP_GRAY8", "GMMSP_COLOUR_FULL", "GMMSP_COLOUR_SPLIT", "GMMSP_COLOUR_GRAY",
@@ -430,6 +430,7 @@ def _net_lib():
             "gmmsp_net_last_error": (ctypes.c_char_p, [P]),
             "gmmsp_net_destroy": (None, [P]),
             "gmmsp_init_from_net": (I, [P, P]),
+            "gmmsp_set_init": (I, [P, P, P]),
             "gmmsp_batch_set_init_net": (I, [P, P]),
             "gmmsp_batch_lab": (I, [P, PP]),
             "gmmsp_batch_targets": (I, [P, P]),
@@ -534,6 +535,14 @@ def gmmsp_net_destroy(n) -> None:
 
 def gmmsp_init_from_net(ctx, n) -> None:
     _check(ctx, _net_lib().gmmsp_init_from_net(ctx, n))
+
+
+def gmmsp_set_init(ctx, dmu, logeig) -> None:
+    """theta_0 from (K, 5) float32 CUDA arrays of mean offsets and log-eigenvalues (see gmmsp_cnn.h)."""
+    for t in (dmu, logeig):
+        if t.dim() != 2 or t.shape[1] != 5 or not t.is_contiguous():
+            raise ValueError("dmu and logeig must be contiguous (K, 5) arrays")
+    _check(ctx, _net_lib().gmmsp_set_init(ctx, _dptr(dmu), _dptr(logeig)))
 
 
 def gmmsp_batch_set_init_net(b, n) -> None:
@@ -871,6 +880,13 @@ class Superpixels:
     def init_from_net(self, net) -> None:
         """Replace theta by the network's theta_0 for the current image."""
         gmmsp_init_from_net(self.ctx, net.n)
+
+    def set_init(self, dmu, logeig) -> None:
+        """Replace theta by theta_0 from per-superpixel predictions: (K, 5) float32 CUDA
+        arrays of mean offsets and log covariance diagonals (include/gmmsp_cnn.h)."""
+        if dmu.shape[0] != self.grid.K or logeig.shape[0] != self.grid.K:
+            raise ValueError("one row per superpixel")
+        gmmsp_set_init(self.ctx, dmu, logeig)
 
     def get_params(self):
         return gmmsp_get_params(self.ctx)

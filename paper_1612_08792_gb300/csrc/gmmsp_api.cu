@@ -542,6 +542,17 @@ gmmsp_status gmmsp_connectivity(gmmsp_ctx c, int32_t* labels_dev, gmmsp_conn_sta
   return st;
 }
 
+gmmsp_status gmmsp_set_init(gmmsp_ctx c, const float* dmu_dev, const float* logeig_dev) {
+  GMMSP_NVTX("gmmsp_set_init");
+  gmmsp_status st = check_ready(c);
+  if (st != GMMSP_OK) return st;
+  if (!dmu_dev || !logeig_dev) return fail(c, GMMSP_E_INVALID, "null array");
+  if (c->g.cm == gmmsp::kColourGray) return fail(c, GMMSP_E_INVALID, "theta_0 arrays need a colour model with a, b");
+  GM_CHECK(c, gmmsp::launch_init_from_outputs(dmu_dev, 5, logeig_dev, 5, c->lab, 1, c->g, c->p.lambda_c, c->p.eps_s,
+                                              c->p.eps_c, c->theta, c->gp, c->counters, c->stream));
+  return GMMSP_OK;
+}
+
 gmmsp_status gmmsp_init_from_net(gmmsp_ctx c, gmmsp_net n) {
   GMMSP_NVTX("gmmsp_init_from_net");
   gmmsp_status st = check_ready(c);

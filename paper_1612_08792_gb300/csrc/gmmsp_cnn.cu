@@ -618,10 +618,13 @@ __global__ void k_targets(const double* __restrict__ theta, const float* __restr
 // theta_0 from the network outputs (the inverse of the target map): mean
 // clipped to the superpixel's window (Eq. Ik), axis-aligned covariances with
 // the diagonal (their eigenvalues) floored at eps (Eq. mlams, mlamc); then
-// the packed E-step coefficients.
-__global__ void k_init_from_net(const float* __restrict__ net, const float* __restrict__ lab, int B, Geom g,
-                                double lambda_c, double eps_s, double eps_c, double* __restrict__ theta,
-                                float* __restrict__ gp, unsigned long long* __restrict__ counters) {
+// the packed E-step coefficients.  Superpixel i reads its 5 mean offsets at
+// dmu + i ds and its 5 log-eigenvalues at logeig + i ls (the network's output
+// rows: ds = ls = 16; a caller's arrays: 5).
+__global__ void k_init_from_net(const float* __restrict__ dmu, int ds, const float* __restrict__ logeig, int ls,
+                                const float* __restrict__ lab, int B, Geom g, double lambda_c, double eps_s,
+                                double eps_c, double* __restrict__ theta, float* __restrict__ gp,
+                                unsigned long long* __restrict__ counters) {
   const long long total = (long long)B * g.K;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -630,7 +633,12 @@ __global__ void k_init_from_net(const float* __restrict__ net, const float* __re
     const int x = kx * g.v + g.v / 2, y = ky * g.v + g.v / 2;
     const long long N = (long long)g.W * g.H, j = (long long)y * g.W + x;
     const float* P = lab + (long long)img * 3 * N;
-    const float* o = net + i * kOut;
+    float o[10];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      o[q] = dmu[i * ds + q];
+      o[5 + q] = logeig[i * ls + q];
+    }
     const double v = g.v, l2 = lambda_c * lambda_c;
     double mu[5] = {x + v * double(o[0]), y + v * double(o[1]), double(P[j]) + kColourUnit * double(o[2]),
                     double(P[N + j]) + kColourUnit * double(o[3]),
@@ -978,9 +986,16 @@ cudaError_t net_enqueue_init(gmmsp_net n, const float* lab, int B, const Geom& g
                              cudaStream_t s) {
   if ((long long)B * g.K > n->cap_cells) return cudaErrorInvalidValue;
   if (enqueue_forward(n, lab, B, g, n->out, false, s) != GMMSP_OK) return cudaErrorLaunchFailure;
+  return launch_init_from_outputs(n->out, kOut, n->out + 5, kOut, lab, B, g, lambda_c, eps_s, eps_c, theta, gp,
+                                  counters, s);
+}
+
+cudaError_t launch_init_from_outputs(const float* dmu, int ds, const float* logeig, int ls, const float* lab, int B,
+                                     const Geom& g, double lambda_c, double eps_s, double eps_c, double* theta,
+                                     float* gp, unsigned long long* counters, cudaStream_t s) {
   const long long total = (long long)B * g.K;
-  k_init_from_net<<<grid_for(total, 128), 128, 0, s>>>(n->out, lab, B, g, lambda_c, eps_s, eps_c, theta, gp,
-                                                       counters);
+  k_init_from_net<<<grid_for(total, 128), 128, 0, s>>>(dmu, ds, logeig, ls, lab, B, g, lambda_c, eps_s, eps_c,
+                                                       theta, gp, counters);
   return cudaGetLastError();
 }
 

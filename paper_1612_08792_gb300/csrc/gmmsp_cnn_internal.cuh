@@ -27,6 +27,13 @@ cudaError_t net_enqueue_init(gmmsp_net n, const float* lab, int B, const Geom& g
                              double eps_c, double* theta, float* gp, unsigned long long* counters,
                              cudaStream_t s);
 
+// theta_0 and the packed coefficients of B K superpixels from the network's
+// output parametrisation given as two device arrays: superpixel i's 5 mean
+// offsets at dmu + i ds and 5 log-eigenvalues at logeig + i ls.
+cudaError_t launch_init_from_outputs(const float* dmu, int ds, const float* logeig, int ls, const float* lab, int B,
+                                     const Geom& g, double lambda_c, double eps_s, double eps_c, double* theta,
+                                     float* gp, unsigned long long* counters, cudaStream_t s);
+
 // Training targets (GMMSP_NET_OUTPUTS floats per superpixel) from fitted
 // parameters theta of B images of geometry g.
 cudaError_t launch_targets(const double* theta, const float* lab, int B, const Geom& g, double lambda_c,

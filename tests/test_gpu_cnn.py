@@ -277,3 +277,37 @@ def test_checkpoint_with_optimizer_resumes_exactly(gm, tmp_path):
         gm.gmmsp_net_set_adam(c.n, m, -np.ones_like(v2), 1)
     for net in (ref, a, b, c):
         net.close()
+
+
+def test_set_init_from_arrays_matches_oracle(gm):
+    """theta_0 from caller-provided predictions equals the oracle's map of the same values."""
+    import torch
+    W, H, v = 481, 321, 15
+    lab = lab_planes([80], W, H)
+    K = (W // v) * (H // v)
+    rng = np.random.default_rng(81)
+    out = np.zeros((K, 16), dtype=np.float32)
+    out[:, :5] = rng.normal(0, 0.6, (K, 5))
+    out[:, 5:10] = rng.normal(0, 1.5, (K, 5))
+    out[::7, 5:10] = 30.0                       # clipped at 10
+    out[::11, 7:10] = -20.0                     # floored at eps_c
+    img0 = torch.from_numpy(np.ascontiguousarray(lab[0].transpose(1, 2, 0))).cuda()
+    sp = gm.Superpixels(img0, spacing=v)
+    sp.set_init(torch.from_numpy(np.ascontiguousarray(out[:, :5])).cuda(),
+                torch.from_numpy(np.ascontiguousarray(out[:, 5:10])).cuda())
+    mu, cs, cc = sp.get_params()
+    rmu, rcs, rcc = ocnn.theta0_from_outputs(out, lab[0], v)
+    assert parity.mean_rel_err(mu, rmu) < 1e-9
+    assert parity.cov_rel_err(cs, rcs) < 1e-9
+    assert parity.cov_rel_err(cc, rcc) < 1e-9
+    sp.em_iters(2)                               # and EM runs from there
+    labels, ll = sp.labels(want_loglik=True)
+    assert np.isfinite(ll)
+    with pytest.raises(ValueError):
+        sp.set_init(torch.zeros((K - 1, 5), device="cuda"), torch.zeros((K - 1, 5), device="cuda"))
+    sp.close()
+    g8 = torch.from_numpy((lab[0, 0] * 2.55).clip(0, 255).astype(np.uint8)).cuda()
+    sg = gm.Superpixels(g8, spacing=v, colour="gray")
+    with pytest.raises(gm.GmmspError):
+        sg.set_init(torch.zeros((K, 5), device="cuda"), torch.zeros((K, 5), device="cuda"))
+    sg.close()
