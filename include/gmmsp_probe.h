@@ -25,6 +25,8 @@ typedef struct {
     double mufu_ex2_tops;        /* ex2.approx.f32 results per second, x 1e12        */
     double fp32_fma_latency_clk; /* dependent FFMA chain, SM clocks per FMA          */
     double fp64_fma_latency_clk; /* dependent DFMA chain, SM clocks per DFMA         */
+    double fp32x2_fma_tflops;    /* packed fma.rn.f32x2 (two FMAs per instruction),
+                                    all SMs, 4 flops per instruction                 */
 } gmmsp_peaks;
 
 int gmmsp_probe_peaks(gmmsp_peaks *out, char *err, int err_len);

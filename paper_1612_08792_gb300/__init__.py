@@ -272,7 +272,8 @@ class gmmsp_peaks(ctypes.Structure):
     _fields_ = [("sm_count", ctypes.c_int), ("clock_mhz", ctypes.c_int),
                 ("fp32_fma_tflops", ctypes.c_double), ("fp64_fma_tflops", ctypes.c_double),
                 ("fp64_fma_tflops_lane1", ctypes.c_double), ("mufu_ex2_tops", ctypes.c_double),
-                ("fp32_fma_latency_clk", ctypes.c_double), ("fp64_fma_latency_clk", ctypes.c_double)]
+                ("fp32_fma_latency_clk", ctypes.c_double), ("fp64_fma_latency_clk", ctypes.c_double),
+                ("fp32x2_fma_tflops", ctypes.c_double)]
 
 
 def gmmsp_probe_peaks() -> dict:

@@ -29,6 +29,25 @@ __global__ void k_ffma(float* out, int iters) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// The same chains as k_ffma, two per packed fma.rn.f32x2 (sm_100 and later):
+// half the instructions for the same number of FMAs.
+__global__ void k_ffma2(float* out, int iters) {
+  float2 a[kChains / 2];
+#pragma unroll
+  for (int j = 0; j < kChains / 2; ++j) a[j] = make_float2(threadIdx.x * 1e-3f + 2 * j, threadIdx.x * 1e-3f + 2 * j + 1);
+  const float2 b = make_float2(0.9999f, 0.9999f), c = make_float2(1e-4f, 1e-4f);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < kChains / 2; ++j) a[j] = __ffma2_rn(a[j], b, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < kChains / 2; ++j) s += a[j].x + a[j].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __global__ void k_dfma(double* out, int iters, int active_lanes) {
   if ((threadIdx.x & 31) >= active_lanes) return;
   double a[kChains];
@@ -121,6 +140,8 @@ extern "C" int gmmsp_probe_peaks(gmmsp_peaks* out, char* err, int err_len) {
   const int it32 = 256, it64 = 1024, itx = 4096;
   float ms = time_ms([&] { k_ffma<<<blocks, threads>>>((float*)buf, it32); });
   out->fp32_fma_tflops = double(blocks) * threads * it32 * 4 * kChains * 2 / (ms * 1e-3) / 1e12;
+  ms = time_ms([&] { k_ffma2<<<blocks, threads>>>((float*)buf, it32); });
+  out->fp32x2_fma_tflops = double(blocks) * threads * it32 * 4 * kChains * 2 / (ms * 1e-3) / 1e12;
   ms = time_ms([&] { k_dfma<<<blocks, threads>>>((double*)buf, it64, 32); });
   out->fp64_fma_tflops = double(blocks) * threads * it64 * kChains * 2 / (ms * 1e-3) / 1e12;
   ms = time_ms([&] { k_dfma<<<blocks, threads>>>((double*)buf, it64, 1); });

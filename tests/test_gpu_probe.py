@@ -14,6 +14,7 @@ def test_probe_peaks():
     r = gm.gmmsp_probe_peaks()
     assert r["sm_count"] >= 100
     assert 10.0 < r["fp32_fma_tflops"] < 200.0
+    assert 10.0 < r["fp32x2_fma_tflops"] < 400.0
     assert 0.1 < r["fp64_fma_tflops"] < 100.0
     assert r["mufu_ex2_tops"] > 1.0
     assert r["fp32_fma_latency_clk"] > 1.0 and r["fp64_fma_latency_clk"] > 1.0
