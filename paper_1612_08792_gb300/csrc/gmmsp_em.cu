@@ -193,7 +193,8 @@ struct EmSmem {
   float4 Z[kEmWarps][32];                           // (L, a, b, -) of those pixels
   float2 XY[kEmWarps][32];                          // their position in the cell
   float part[kEmWarps][kSlots * kStats + 1 + 3];    // per-warp sums (row 135: log-likelihood)
-  float red[kEmWarps][27][kStats + 1];              // per-lane sums before the 3-lane add
+  float red[kEmWarps][27][kStats + 2];              // per-lane sums before the 3-lane add (odd row
+                                                    // stride: the 27 lanes' stores hit 27 banks)
 };
 
 template <int WPC>

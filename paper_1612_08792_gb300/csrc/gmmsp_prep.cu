@@ -31,10 +31,17 @@ struct Rgb2LabConst {
 };
 
 __device__ __forceinline__ float cielab_f(float t) {
-  // CIE 1976: cube root above (6/29)^3, the linear segment below.
+  // CIE 1976: cube root above (6/29)^3, the linear segment below.  The cube
+  // root is taken as 2^(log2(t) / 3) on the special-function unit
+  // (lg2.approx, ex2.approx; t is a normal number there): relative error
+  // about 3e-7, i.e. under 3e-4 in L*, a*, b*, at two instructions instead
+  // of a full-precision cbrtf, three times per pixel.
   const float d3 = 216.f / 24389.f;             // (6/29)^3
   const float slope = 841.f / 108.f;            // 1 / (3 (6/29)^2)
-  return t > d3 ? cbrtf(t) : fmaf(slope, t, 4.f / 29.f);
+  float lg, cr;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(t));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(cr) : "f"(lg * (1.f / 3.f)));
+  return t > d3 ? cr : fmaf(slope, t, 4.f / 29.f);
 }
 
 // sRGB decoding of the 256 code values (the transfer curve of IEC 61966-2-1).
