@@ -90,24 +90,34 @@ __device__ __forceinline__ Cell make_cell(const Geom& g, int cell) {
 }
 
 // Copies the packed parameters of the cell's candidate slots into sp[36]
-// (float4); slots off the grid are zero and never read.
+// (float4), with the spatial mean moved from the candidate's cell origin to
+// this cell's (mu_x + (s mod 3 - 1) v, mu_y + (s / 3 - 1) v), so that every
+// candidate sees the pixel's own coordinates in the cell; slots off the grid
+// are zero and never read.
+__device__ __forceinline__ float4 staged_param(const Geom& g, const Cell& c, const float* gp, int i) {
+  const int s = i >> 2, q = i & 3;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if ((c.mask >> s) & 1u) {
+    const int k = (c.cy - 1 + s / 3) * g.nx + (c.cx - 1 + s % 3);
+    v = __ldg(reinterpret_cast<const float4*>(gp) + k * 4 + q);
+    if (q == 0) {
+      v.x += float((s % 3 - 1) * g.v);
+      v.y += float((s / 3 - 1) * g.v);
+    }
+  }
+  return v;
+}
+
 __device__ __forceinline__ void stage_params(const Geom& g, const Cell& c, const float* gp,
                                              float4* sp, int lane) {
-  for (int i = lane; i < kSlots * 4; i += 32) {
-    const int s = i >> 2, q = i & 3;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if ((c.mask >> s) & 1u) {
-      const int k = (c.cy - 1 + s / 3) * g.nx + (c.cx - 1 + s % 3);
-      v = __ldg(reinterpret_cast<const float4*>(gp) + k * 4 + q);
-    }
-    sp[i] = v;
-  }
+  for (int i = lane; i < kSlots * 4; i += 32) sp[i] = staged_param(g, c, gp, i);
   __syncwarp();
 }
 
 // log2 p(z; theta_k) for one candidate: the log normaliser plus the two
 // quadratic forms, with -1/2 log2(e) Sigma^{-1} folded into the coefficients.
-// fx, fy are the pixel's coordinates relative to the candidate's cell origin.
+// fx, fy are the pixel's coordinates relative to the cell origin (the staged
+// mean is relative to the same origin).
 template <int CM>
 __device__ __forceinline__ float log2_density(const float4* P, float fx, float fy, float4 z) {
   const float4 p0 = P[0], p1 = P[1], p2 = P[2], p3 = P[3];
@@ -132,25 +142,18 @@ __device__ __forceinline__ float log2_density(const float4* P, float fx, float f
   return q;
 }
 
-// Coordinates of pixel (rx, ry) of a cell relative to the cell origins of
-// the candidate columns/rows cx-1, cx, cx+1: rx + v, rx, rx - v.
-__device__ __forceinline__ void rel_coords(int rx, int ry, int v, float (&fxs)[3], float (&fys)[3]) {
-  fxs[0] = float(rx + v); fxs[1] = float(rx); fxs[2] = float(rx - v);
-  fys[0] = float(ry + v); fys[1] = float(ry); fys[2] = float(ry - v);
-}
-
 // E part for one pixel: the posteriors of its candidates (Eq. Rik) into
 // R[0..8] (zero for slots off the grid) and ln-sum-exp in log2 units into ll.
 template <bool FULL, int CM>
-__device__ __forceinline__ void e_pixel(const float4* sp, unsigned mask, const float (&fxs)[3],
-                                        const float (&fys)[3], float4 z, float (&R)[kSlots],
+__device__ __forceinline__ void e_pixel(const float4* sp, unsigned mask, float fx, float fy, float4 z,
+                                        float (&R)[kSlots],
                                         float& ll) {
   float m = -INFINITY;
 #pragma unroll
   for (int s = 0; s < kSlots; ++s) {
     R[s] = 0.f;
     if (FULL || ((mask >> s) & 1u)) {
-      R[s] = log2_density<CM>(sp + 4 * s, fxs[s % 3], fys[s / 3], z);
+      R[s] = log2_density<CM>(sp + 4 * s, fx, fy, z);
       m = fmaxf(m, R[s]);
     }
   }
@@ -216,9 +219,10 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
   float cx = 0.f, cy = 0.f, mL = 0.f, ma = 0.f, mb = 0.f;
   {
     const float4 p0 = sp[4 * ms], p1 = sp[4 * ms + 1];
-    // d_x = rx + (1 - ms % 3) v - mu_x (mu_x relative to the candidate's cell origin)
-    cx = float((1 - ms % 3) * g.v) - (SHIFT ? p0.x : 0.f);
-    cy = float((1 - ms / 3) * g.v) - (SHIFT ? p0.y : 0.f);
+    // SHIFT: d_x = rx - mu_x (the staged mean, relative to this cell's origin);
+    // raw moments: x relative to the candidate's cell origin, rx + (1 - ms % 3) v
+    cx = SHIFT ? -p0.x : float((1 - ms % 3) * g.v);
+    cy = SHIFT ? -p0.y : float((1 - ms / 3) * g.v);
     if (SHIFT) { mL = p0.z; ma = p0.w; mb = p1.x; }
   }
   // The colour of this lane's next pixel is loaded one batch ahead.
@@ -244,9 +248,7 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
     int rx = 0, ry = 0;
     if (p < npx) {
       locate(p, rx, ry);
-      float fxs[3], fys[3];
-      rel_coords(rx, ry, g.v, fxs, fys);
-      e_pixel<FULL, CM>(sp, c.mask, fxs, fys, z, R, ll);
+      e_pixel<FULL, CM>(sp, c.mask, float(rx), float(ry), z, R, ll);
     } else {
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) R[s] = 0.f;
@@ -311,15 +313,7 @@ __device__ __forceinline__ void em_cell_block(const Src& lab, const Geom& g, con
   Cell c = {};
   if (active) c = make_cell(g, cell);
   if (active) {
-    for (int i = t; i < kSlots * 4; i += 32 * WPC) {
-      const int s = i >> 2, q = i & 3;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if ((c.mask >> s) & 1u) {
-        const int k = (c.cy - 1 + s / 3) * g.nx + (c.cx - 1 + s % 3);
-        v = __ldg(reinterpret_cast<const float4*>(gp) + k * 4 + q);
-      }
-      sm.sp[slot][i] = v;
-    }
+    for (int i = t; i < kSlots * 4; i += 32 * WPC) sm.sp[slot][i] = staged_param(g, c, gp, i);
   }
   if (WPC == 1) __syncwarp(); else __syncthreads();
 
@@ -470,7 +464,6 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
   }
   for (int p0 = lane; p0 - lane < npx; p0 += 32 * kLabelPPL) {
     float4 z[kLabelPPL];
-    float fxs[kLabelPPL][3], fys[kLabelPPL][3];
     int rx[kLabelPPL], ry[kLabelPPL];
 #pragma unroll
     for (int j = 0; j < kLabelPPL; ++j) {
@@ -482,7 +475,6 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
         zn[j] = load_z<CM>(lab, c.x0 + x1, c.y0 + y1);
       }
       locate(p0 + 32 * j, rx[j], ry[j]);
-      rel_coords(rx[j], ry[j], g.v, fxs[j], fys[j]);
     }
     float e[kLabelPPL][kSlots];
     float m[kLabelPPL];
@@ -497,7 +489,7 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
       if (FULL || ((c.mask >> s) & 1u)) {
 #pragma unroll
         for (int j = 0; j < kLabelPPL; ++j) {
-          e[j][s] = log2_density<CM>(sp + 4 * s, fxs[j][s % 3], fys[j][s / 3], z[j]);
+          e[j][s] = log2_density<CM>(sp + 4 * s, float(rx[j]), float(ry[j]), z[j]);
           if (e[j][s] > m[j]) { m[j] = e[j][s]; best[j] = s; }
         }
       } else {
