@@ -31,6 +31,16 @@ typedef struct {
 
 int gmmsp_probe_peaks(gmmsp_peaks *out, char *err, int err_len);
 
+/*
+ * gmmsp_probe_smem_patterns launches one short kernel per shared-memory load
+ * pattern of the EM kernels (k_lds_pattern<0..9>: warp-uniform 16-, 8- and
+ * 4-byte loads, three-address loads, the posterior-row layouts) and
+ * synchronises.  It measures nothing itself: run it under a profiler and read
+ * the shared-memory wavefronts per load instruction of each kernel.  Returns 0,
+ * or 2 on a CUDA error (message in err).
+ */
+int gmmsp_probe_smem_patterns(char *err, int err_len);
+
 #ifdef __cplusplus
 }
 #endif

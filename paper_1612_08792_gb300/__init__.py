@@ -24,7 +24,7 @@ __all__ = [
     "gmmsp_params", "load_library", "library_path", "Superpixels",
     "gmmsp_default_params", "gmmsp_init", "gmmsp_reinit", "gmmsp_em_iters", "gmmsp_labels",
     "gmmsp_segment", "gmmsp_get_lab", "gmmsp_get_grid", "gmmsp_get_params", "gmmsp_set_params", "gmmsp_get_stats",
-    "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_set_timing", "gmmsp_get_timing", "gmmsp_set_launch", "gmmsp_get_launch",
+    "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_probe_smem_patterns", "gmmsp_set_timing", "gmmsp_get_timing", "gmmsp_set_launch", "gmmsp_get_launch",
     "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "SuperpixelsBatch",
     "gmmsp_batch_create", "gmmsp_batch_segment", "gmmsp_batch_get_params", "gmmsp_batch_autotune",
     "gmmsp_batch_set_launch", "gmmsp_batch_set_tuning", "gmmsp_batch_info", "gmmsp_batch_destroy", "gmmsp_status_string", "gmmsp_destroy",
@@ -287,6 +287,17 @@ def gmmsp_probe_peaks() -> dict:
     if st != 0:
         raise GmmspError(2, err.value.decode())
     return {name: getattr(out, name) for name, _ in gmmsp_peaks._fields_}
+
+
+def gmmsp_probe_smem_patterns() -> None:
+    """Launches the shared-memory load-pattern kernels (for a profiler to count)."""
+    lib = load_library()
+    f = lib.gmmsp_probe_smem_patterns
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_char_p, ctypes.c_int]
+    err = ctypes.create_string_buffer(256)
+    if f(err, 256) != 0:
+        raise GmmspError(2, err.value.decode())
 
 
 def gmmsp_segment_lab_noalloc(lab, width: int, height: int, pitch_bytes: int, params: gmmsp_params,

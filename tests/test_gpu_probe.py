@@ -22,3 +22,10 @@ def test_probe_peaks():
     if out:
         with open(out, "w") as fh:
             json.dump(r, fh, indent=1)
+
+
+def test_probe_smem_patterns_run():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    gm.gmmsp_probe_smem_patterns()
