@@ -101,3 +101,14 @@ def test_superpixel_without_weight_keeps_its_parameters(gm):
     assert ref.dead > 0 and dead == ref.dead
     np.testing.assert_allclose(mu[1], th.mu[1], rtol=1e-6)
     check(dict(labels=labels.cpu().numpy(), ll=np.array(ll + [ll_last]), mu=mu, cs=cs, cc=cc, dead=dead), ref)
+
+
+@pytest.mark.parametrize("W,H,v", [(320, 240, 80), (400, 130, 120), (257, 199, 64)])
+def test_large_spacing(gm, W, H, v):
+    """Cells of up to 120 x 120 pixels (with remainders): candidate means staged relative to
+    the processed cell reach about 2 v, and a cell's pixel loop runs hundreds of batches."""
+    lab32 = lab_of(W, H, 12, 3)
+    ref = oracle.em(lab32.astype(np.float64), W, H, spacing=v, T=5)
+    got = run(gm, lab32, v, 5)
+    assert got["grid"].K == ref.grid.K
+    check(got, ref)
