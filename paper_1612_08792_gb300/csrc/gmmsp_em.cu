@@ -186,7 +186,7 @@ __device__ __forceinline__ void e_pixel(const float4* sp, unsigned mask, float f
 // instead of 9 x 15, which keeps the register count (and so the occupancy)
 // of the kernel independent of the candidate count.  At the end the three
 // lanes of each slot, then the WPC warps, are added through shared memory and
-// written once per cell as FP64 (no global atomics).
+// written once per cell as FP32 (no global atomics).
 constexpr int kRStride = 12;  // floats per pixel row of posteriors
 
 template <int WPC>
