@@ -95,6 +95,7 @@ bool geom_of(int W, int H, int K_req, int spacing, Geom* g) {
     v = lo;
   }
   if (v < 1 || v > W || v > H) return false;
+  if ((long long)W * H > 2147483647LL) return false;  // pixel offsets are 32-bit in the kernels
   g->W = W; g->H = H; g->v = int(v);
   g->nx = int(W / v); g->ny = int(H / v);
   g->K = g->nx * g->ny;
