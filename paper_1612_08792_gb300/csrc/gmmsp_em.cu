@@ -400,10 +400,13 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
     float e[kLabelPPL][kSlots];
     float m[kLabelPPL];
     int best[kLabelPPL];
+    // start at the cell's first candidate, so that the label is one of the
+    // pixel's candidates (Eq. obtLi) even where no density compares (NaN input)
+    const int first = __ffs(c.mask) - 1;
 #pragma unroll
     for (int j = 0; j < kLabelPPL; ++j) {
       m[j] = -INFINITY;
-      best[j] = 0;
+      best[j] = first;
     }
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {

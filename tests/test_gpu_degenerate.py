@@ -112,3 +112,36 @@ def test_large_spacing(gm, W, H, v):
     got = run(gm, lab32, v, 5)
     assert got["grid"].K == ref.grid.K
     check(got, ref)
+
+
+def test_nan_pixels_keep_labels_in_candidate_sets(gm):
+    """A NaN pixel in a corner cell (no density compares) and one in the remainder corner: every label
+    still names one of its pixel's candidates (Eq. Ik, obtLi), on the context and allocation-free paths,
+    and the context path reports the input as GMMSP_E_NUMERIC."""
+    import torch
+    W, H, v, T = 97, 61, 8, 3                       # remainder strips 1 and 5 pixels wide
+    lab = oracle.rgb2lab(voronoi_image(W, H, 12, 8.0, 17)).astype(np.float32)
+    lab[0, 0] = np.nan
+    lab[H - 1, W - 1, 1] = np.nan
+    g = oracle.grid(W, H, spacing=v)
+    cand, _ = oracle.candidates(g)
+
+    def in_candidates(labels):
+        return bool(np.all(np.any(cand == labels.reshape(-1, 1), axis=1)))
+
+    dev = torch.from_numpy(lab).cuda()
+    p = gm.gmmsp_default_params()
+    p.spacing = v
+    out = torch.full((H, W), -1, dtype=torch.int32, device="cuda")
+    gm.gmmsp_segment_lab_noalloc(dev, W, H, W * 12, p, T, out)
+    torch.cuda.synchronize()
+    assert in_candidates(out.cpu().numpy())
+    sp = gm.Superpixels(dev, spacing=v)
+    sp.em_iters(T)
+    labels = sp.labels()
+    torch.cuda.synchronize()
+    assert in_candidates(labels.cpu().numpy())
+    with pytest.raises(gm.GmmspError) as ei:
+        sp.labels(want_loglik=True)
+    assert ei.value.status == 4
+    sp.close()
