@@ -284,6 +284,11 @@ gmmsp_status gmmsp_batch_get_tuning(gmmsp_batch b, int *blocks_per_sm, int *fina
  * finalize applies: mixed precision, full colour model). */
 gmmsp_status gmmsp_batch_set_tuning(gmmsp_batch b, int blocks_per_sm, int finalize16);
 gmmsp_status gmmsp_batch_info(gmmsp_batch b, long long *total_pixels, int *total_k, int *total_cells);
+/* Copies image i's CIELAB colours (Sec. III-A, after the conversion of Sec.
+ * IV) as the last gmmsp_batch_segment left them on the device to the host as
+ * W H x (L, a, b) float32 (synchronises the batch's stream).
+ * Errors: GMMSP_E_INVALID for NULL or i outside [0, n). */
+gmmsp_status gmmsp_batch_get_lab(gmmsp_batch b, int i, float *lab_host);
 const char *gmmsp_batch_last_error(gmmsp_batch b);
 void gmmsp_batch_destroy(gmmsp_batch b);
 
@@ -303,11 +308,16 @@ void gmmsp_batch_destroy(gmmsp_batch b);
  *   lab_dev      device rows of W x (L, a, b) float32, 4-byte aligned;
  *   pitch_bytes  row pitch, >= 12 W, a multiple of 4;
  *   p            spacing or K, eps_s, eps_c, lambda_c as for gmmsp_init
- *                (input_format is ignored; precision must be MIXED and
- *                colour_model FULL);
+ *                (finite and > 0; input_format is ignored; precision must be
+ *                MIXED and colour_model FULL);
  *   labels_dev   device int32[W H], written (argmax posterior, Eq. obtLi);
  *   stream       cudaStream_t to queue on; the call does not synchronise;
  *   err          NULL, or err_len bytes receiving a message on failure.
+ * Non-finite input is not detected here (the context and batch paths report
+ * it as GMMSP_E_NUMERIC; this call never synchronises to read a counter):
+ * the parameters of the superpixels it reaches become NaN, and the labels of
+ * their pixels are then unspecified, though each still names one of its
+ * pixel's candidate superpixels (Eq. Ik).
  * Limits: the cell grid ceil(W/v) x ceil(H/v) may hold at most
  * GMMSP_NOALLOC_MAX_CELLS cells (e.g. 481x321 at v >= 8, 1920x1080 at
  * v >= 30); larger grids return GMMSP_E_INVALID with the sizes in err.

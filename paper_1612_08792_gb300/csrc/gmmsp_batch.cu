@@ -9,6 +9,7 @@
 // per-image log-likelihoods.  Images, cells and superpixels are numbered
 // consecutively over the batch (offsets in the table).
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -188,7 +189,9 @@ gmmsp_status gmmsp_batch_create(gmmsp_batch* out, int n, const int* widths, cons
   if (p->colour_model < GMMSP_COLOUR_FULL || p->colour_model > GMMSP_COLOUR_GRAY) return GMMSP_E_INVALID;
   if (p->colour_model != GMMSP_COLOUR_FULL && p->precision != GMMSP_PREC_MIXED) return GMMSP_E_INVALID;
   if (p->input_format == GMMSP_GRAY8 && p->colour_model != GMMSP_COLOUR_GRAY) return GMMSP_E_INVALID;
-  if (!(p->eps_s > 0.f) || !(p->eps_c > 0.f) || !(p->lambda_c > 0.f)) return GMMSP_E_INVALID;
+  if (!(p->eps_s > 0.f) || !(p->eps_c > 0.f) || !(p->lambda_c > 0.f) || !isfinite(p->eps_s) ||
+      !isfinite(p->eps_c) || !isfinite(p->lambda_c))
+    return GMMSP_E_INVALID;
   if (p->spacing <= 0 && p->K <= 0) return GMMSP_E_INVALID;
   gmmsp_batch b = new (std::nothrow) gmmsp_batch_s();
   if (!b) return GMMSP_E_NOMEM;
@@ -357,6 +360,22 @@ gmmsp_status gmmsp_batch_get_params(gmmsp_batch b, int i, double* mu_host, doubl
     if (mu_host) memcpy(mu_host + 5 * size_t(k), t, 5 * sizeof(double));
     if (cov_s_host) memcpy(cov_s_host + 3 * size_t(k), t + 5, 3 * sizeof(double));
     if (cov_c_host) memcpy(cov_c_host + 6 * size_t(k), t + 8, 6 * sizeof(double));
+  }
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_batch_get_lab(gmmsp_batch b, int i, float* lab_host) {
+  if (!b || !lab_host || i < 0 || i >= b->n) return GMMSP_E_INVALID;
+  const BatchImage& im = b->host[i];
+  const size_t N = size_t(im.g.W) * im.g.H;
+  std::vector<float> tmp(3 * N);
+  GB_CHECK(b, cudaMemcpyAsync(tmp.data(), b->lab + 3 * size_t(im.pix_off), 3 * N * sizeof(float),
+                              cudaMemcpyDeviceToHost, b->stream));
+  GB_CHECK(b, cudaStreamSynchronize(b->stream));
+  for (size_t q = 0; q < N; ++q) {
+    lab_host[3 * q + 0] = tmp[q];
+    lab_host[3 * q + 1] = tmp[N + q];
+    lab_host[3 * q + 2] = tmp[2 * N + q];
   }
   return GMMSP_OK;
 }

@@ -13,10 +13,11 @@
 // output; nothing is allocated or freed.
 //
 // The kernels are the ones gmmsp_segment runs, instantiated to read the
-// caller's (L, a, b) float32 rows directly instead of the context's float4
+// caller's (L, a, b) float32 rows directly instead of the context's planar
 // copy of the image, so the results are those of gmmsp_init with
 // GMMSP_LAB32 input followed by gmmsp_em_iters and gmmsp_labels.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -120,9 +121,11 @@ extern "C" gmmsp_status gmmsp_segment_lab_noalloc(const float* lab_dev, int widt
     return GMMSP_E_INVALID;
   }
   if (p->precision != GMMSP_PREC_MIXED || p->colour_model != GMMSP_COLOUR_FULL || !(p->eps_s > 0.f) ||
-      !(p->eps_c > 0.f) || !(p->lambda_c > 0.f) || iters < 0 || (p->spacing <= 0 && p->K <= 0)) {
+      !(p->eps_c > 0.f) || !(p->lambda_c > 0.f) || !isfinite(p->eps_s) || !isfinite(p->eps_c) ||
+      !isfinite(p->lambda_c) || iters < 0 || (p->spacing <= 0 && p->K <= 0)) {
     set_err(err, err_len,
-            "invalid parameters (mixed precision and the full colour model only; eps, lambda_c > 0; iters >= 0)");
+            "invalid parameters (mixed precision and the full colour model only; eps, lambda_c finite and > 0; "
+            "iters >= 0)");
     return GMMSP_E_INVALID;
   }
   Geom g;
