@@ -24,11 +24,11 @@ __all__ = [
     "gmmsp_params", "load_library", "library_path", "Superpixels",
     "gmmsp_default_params", "gmmsp_init", "gmmsp_reinit", "gmmsp_em_iters", "gmmsp_labels",
     "gmmsp_segment", "gmmsp_get_lab", "gmmsp_get_grid", "gmmsp_get_params", "gmmsp_set_params", "gmmsp_get_stats",
-    "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_probe_smem_patterns", "gmmsp_set_timing", "gmmsp_get_timing", "gmmsp_set_launch", "gmmsp_get_launch",
+    "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_probe_fp64_helpers", "gmmsp_set_timing", "gmmsp_get_timing", "gmmsp_set_launch", "gmmsp_get_launch",
     "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "SuperpixelsBatch",
     "gmmsp_batch_create", "gmmsp_batch_segment", "gmmsp_batch_get_params", "gmmsp_batch_autotune",
     "gmmsp_batch_set_launch", "gmmsp_batch_set_tuning", "gmmsp_batch_info", "gmmsp_batch_destroy", "gmmsp_status_string", "gmmsp_destroy",
-    "gmmsp_batch_get_tuning", "gmmsp_batch_set_init_net", "gmmsp_batch_lab", "gmmsp_batch_targets",
+    "gmmsp_batch_get_tuning", "gmmsp_batch_set_init_net", "gmmsp_batch_lab", "gmmsp_batch_targets", "gmmsp_batch_get_lab",
     "gmmsp_net_param_count", "gmmsp_net_create", "gmmsp_net_set_weights", "gmmsp_net_get_weights",
     "gmmsp_net_forward", "gmmsp_net_grad", "gmmsp_net_adam", "gmmsp_net_train_step", "gmmsp_net_get_activation",
     "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_net_get_adam", "gmmsp_net_set_adam", "gmmsp_set_init", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
@@ -289,15 +289,24 @@ def gmmsp_probe_peaks() -> dict:
     return {name: getattr(out, name) for name, _ in gmmsp_peaks._fields_}
 
 
-def gmmsp_probe_smem_patterns() -> None:
-    """Launches the shared-memory load-pattern kernels (for a profiler to count)."""
+def gmmsp_probe_fp64_helpers(x):
+    """The finalize's FP64 reciprocal, square root and log2 helpers on a float64 CUDA tensor x:
+    returns (1/x, sqrt(x), log2(x)) as CUDA tensors (float64, float64, float32)."""
+    import torch
     lib = load_library()
-    f = lib.gmmsp_probe_smem_patterns
+    f = lib.gmmsp_probe_fp64_helpers
     f.restype = ctypes.c_int
-    f.argtypes = [ctypes.c_char_p, ctypes.c_int]
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
+    x = x.contiguous()
+    rcp, sq = torch.empty_like(x), torch.empty_like(x)
+    lg = torch.empty(x.shape, dtype=torch.float32, device=x.device)
     err = ctypes.create_string_buffer(256)
-    if f(err, 256) != 0:
-        raise GmmspError(2, err.value.decode())
+    st = f(_dptr(x), int(x.numel()), _dptr(rcp), _dptr(sq), _dptr(lg),
+           _stream_handle(torch.cuda.current_stream()), err, 256)
+    if st != 0:
+        raise GmmspError(st, err.value.decode())
+    return rcp, sq, lg
 
 
 def gmmsp_segment_lab_noalloc(lab, width: int, height: int, pitch_bytes: int, params: gmmsp_params,
@@ -330,6 +339,7 @@ def _batch_lib():
             "gmmsp_batch_set_launch": (I, [P, I]),
             "gmmsp_batch_set_tuning": (I, [P, I, I]),
             "gmmsp_batch_info": (I, [P, ctypes.POINTER(ctypes.c_longlong), pint, pint]),
+            "gmmsp_batch_get_lab": (I, [P, I, P]),
             "gmmsp_batch_get_tuning": (I, [P, pint, pint, P]),
             "gmmsp_batch_last_error": (ctypes.c_char_p, [P]),
             "gmmsp_batch_destroy": (None, [P]),
@@ -403,6 +413,12 @@ def gmmsp_batch_info(b):
     pix, K, cells = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
     _bcheck(b, _batch_lib().gmmsp_batch_info(b, ctypes.byref(pix), ctypes.byref(K), ctypes.byref(cells)))
     return pix.value, K.value, cells.value
+
+
+def gmmsp_batch_get_lab(b, i, H, W):
+    out = np.zeros((H, W, 3), dtype=np.float32)
+    _bcheck(b, _batch_lib().gmmsp_batch_get_lab(b, int(i), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
 
 
 def gmmsp_batch_get_tuning(b):
@@ -501,14 +517,16 @@ def gmmsp_net_set_adam(n, m, v, step: int) -> None:
                                              m.size, int(step)))
 
 
-def gmmsp_net_forward(n, lab_ptr: int, B: int, W: int, H: int, out) -> None:
-    _ncheck(n, _net_lib().gmmsp_net_forward(n, int(lab_ptr), int(B), int(W), int(H), _dptr(out)))
+def gmmsp_net_forward(n, lab, B: int, W: int, H: int, out) -> None:
+    """lab: B images of CIELAB planes, a float32 CUDA tensor (kept referenced while the work is
+    queued) or a device address the caller keeps alive until the work has run."""
+    _ncheck(n, _net_lib().gmmsp_net_forward(n, _dptr(lab), int(B), int(W), int(H), _dptr(out)))
 
 
-def gmmsp_net_grad(n, lab_ptr: int, B: int, W: int, H: int, target, want_grad: bool = True):
+def gmmsp_net_grad(n, lab, B: int, W: int, H: int, target, want_grad: bool = True):
     g = np.zeros(gmmsp_net_param_count(), dtype=np.float32) if want_grad else None
     loss = ctypes.c_double()
-    _ncheck(n, _net_lib().gmmsp_net_grad(n, int(lab_ptr), int(B), int(W), int(H), _dptr(target),
+    _ncheck(n, _net_lib().gmmsp_net_grad(n, _dptr(lab), int(B), int(W), int(H), _dptr(target),
                                          g.ctypes.data_as(ctypes.c_void_p) if g is not None else None,
                                          ctypes.byref(loss)))
     return loss.value, g
@@ -518,10 +536,10 @@ def gmmsp_net_adam(n, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: 
     _ncheck(n, _net_lib().gmmsp_net_adam(n, lr, beta1, beta2, eps))
 
 
-def gmmsp_net_train_step(n, lab_ptr: int, B: int, W: int, H: int, target, lr: float,
+def gmmsp_net_train_step(n, lab, B: int, W: int, H: int, target, lr: float,
                          want_loss: bool = True):
     loss = ctypes.c_double()
-    _ncheck(n, _net_lib().gmmsp_net_train_step(n, int(lab_ptr), int(B), int(W), int(H), _dptr(target),
+    _ncheck(n, _net_lib().gmmsp_net_train_step(n, _dptr(lab), int(B), int(W), int(H), _dptr(target),
                                                float(lr), ctypes.byref(loss) if want_loss else None))
     return loss.value if want_loss else None
 
@@ -742,6 +760,11 @@ class SuperpixelsBatch:
 
     def get_params(self, i: int, K: int):
         return gmmsp_batch_get_params(self.b, i, K)
+
+    def get_lab(self, i: int):
+        """Image i's CIELAB colours (H, W, 3) float32 as the last segment converted them."""
+        H, W = self.shapes[i]
+        return gmmsp_batch_get_lab(self.b, i, H, W)
 
     def set_init_net(self, net) -> None:
         """Start every later segment from the network's theta_0 (None: the paper's start)."""

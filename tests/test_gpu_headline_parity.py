@@ -1,0 +1,115 @@
+"""The batch kernels that the bench's workloads run, against the FP64 oracle.
+
+Every launch variant the batch autotuner can pick (3-5 blocks per SM: the
+persistent E + M kernel; 6, 7: the one-cell-per-warp kernels with capped
+registers; each with the one-thread and the 16-lane finalize) runs Algorithm 1,
+steps 2-7 (Eq. Rik, UpdateMu, UpdateSigS/C, mlams/mlamc, obtLi) on the learned
+start's workload (481 x 321 at spacing 15) and on uneven sizes of the batched
+workload; every image's means, covariances, final log-likelihood and labels
+are compared with the oracle at the parity bar.  The learned start is then
+checked end to end: the GPU's theta_0 from the trained network, given to the
+oracle, must give the GPU's theta_2, labels and L(theta_2).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import voronoi_image
+from synth.voronoi import batch_regions
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+V = 15
+T = 10
+SIZES = [(481, 321), (481, 321), (481, 321), (320, 240), (640, 480), (1280, 720), (97, 61), (37, 23)]
+LEARN_W, LEARN_H, LEARN_B = 481, 321, 4
+
+
+@pytest.fixture(scope="module")
+def gm():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_08792_gb300 as gm
+    torch.cuda.set_device(0)
+    return gm
+
+
+def make_lab(W, H, seed):
+    regions = 150 if (W, H) == (481, 321) else batch_regions(W, H)
+    return oracle.rgb2lab(voronoi_image(W, H, regions, 8.0, seed)).astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def plain_case():
+    labs = [make_lab(W, H, 2_000_000 + i) for i, (W, H) in enumerate(SIZES)]
+    refs = [oracle.em(lab.astype(np.float64), W, H, spacing=V, T=T) for lab, (W, H) in zip(labs, SIZES)]
+    return labs, refs
+
+
+def check_image(mu, cs, cc, labels, ll, ref, what):
+    em = parity.mean_rel_err(mu, ref.theta.mu)
+    es = parity.cov_rel_err(cs, ref.theta.cs)
+    ec = parity.cov_rel_err(cc, ref.theta.cc)
+    assert em <= parity.MEAN_TOL and es <= parity.COV_TOL and ec <= parity.COV_TOL, (what, em, es, ec)
+    agree, ndiff, worst = parity.label_report(labels, ref.labels, ref.margin)
+    assert agree >= parity.LABEL_AGREE and worst < parity.MARGIN_TOL, (what, agree, ndiff, worst)
+    assert abs(ll - ref.loglik[-1]) <= parity.LL_RTOL * abs(ref.loglik[-1]), (what, ll, ref.loglik[-1])
+
+
+@pytest.mark.parametrize("fin16", [False, True])
+@pytest.mark.parametrize("bps", [3, 4, 5, 6, 7])
+def test_batch_launch_variants_match_oracle(gm, plain_case, bps, fin16):
+    import torch
+    labs, refs = plain_case
+    dev = [torch.from_numpy(x).cuda() for x in labs]
+    bt = gm.SuperpixelsBatch([(H, W) for (W, H) in SIZES], spacing=V, lab_input=True)
+    gm.gmmsp_batch_set_tuning(bt.b, bps, fin16)
+    assert bt.tuning()["blocks_per_sm"] == bps and bt.tuning()["finalize16"] == fin16
+    labels, ll = bt.segment(dev, iters=T, want_loglik=True)
+    torch.cuda.synchronize()
+    for i, (W, H) in enumerate(SIZES):
+        mu, cs, cc = bt.get_params(i, refs[i].grid.K)
+        check_image(mu, cs, cc, labels[i].cpu().numpy(), ll[i], refs[i], (bps, fin16, i, W, H))
+    bt.close()
+
+
+@pytest.fixture(scope="module")
+def learned_case(gm):
+    """The trained network's theta_0 on the GPU for LEARN_B images of the learned start's workload."""
+    import torch
+    from paper_1612_08792_gb300.learned_init import load_pretrained
+    labs = [make_lab(LEARN_W, LEARN_H, 3_000_000 + i) for i in range(LEARN_B)]
+    dev = [torch.from_numpy(x).cuda() for x in labs]
+    net = load_pretrained(V)
+    bt = gm.SuperpixelsBatch([(LEARN_H, LEARN_W)] * LEARN_B, spacing=V, lab_input=True)
+    bt.set_init_net(net)
+    bt.segment(dev, iters=0)
+    torch.cuda.synchronize()
+    K = (LEARN_W // V) * (LEARN_H // V)
+    theta0 = [oracle.Theta(*bt.get_params(i, K)) for i in range(LEARN_B)]
+    net.check()
+    bt.close()
+    refs = [oracle.em(lab.astype(np.float64), LEARN_W, LEARN_H, spacing=V, T=2, theta0=th)
+            for lab, th in zip(labs, theta0)]
+    yield labs, dev, net, theta0, refs
+    net.close()
+
+
+@pytest.mark.parametrize("bps", [3, 5, 6, 7])
+def test_learned_start_then_two_iterations_match_oracle(gm, learned_case, bps):
+    import torch
+    labs, dev, net, theta0, refs = learned_case
+    bt = gm.SuperpixelsBatch([(LEARN_H, LEARN_W)] * LEARN_B, spacing=V, lab_input=True)
+    bt.set_init_net(net)
+    gm.gmmsp_batch_set_tuning(bt.b, bps, bps % 2 == 1)
+    labels, ll = bt.segment(dev, iters=2, want_loglik=True)
+    torch.cuda.synchronize()
+    K = (LEARN_W // V) * (LEARN_H // V)
+    for i in range(LEARN_B):
+        # the oracle starts from exactly the GPU's theta_0 (the learned start is the only input)
+        assert np.all(np.isfinite(theta0[i].mu)) and np.all(theta0[i].cs[:, 0] > 0)
+        mu, cs, cc = bt.get_params(i, K)
+        check_image(mu, cs, cc, labels[i].cpu().numpy(), ll[i], refs[i], ("learned", bps, i))
+    bt.close()
