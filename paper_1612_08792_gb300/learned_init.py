@@ -81,19 +81,22 @@ class InitNet:
     def get_weights(self) -> np.ndarray:
         return gmmsp_net_get_weights(self.n)
 
-    def forward(self, lab_ptr: int, B: int, W: int, H: int):
-        """Outputs (B, n_y, n_x, 16) float32 on the device for B CIELAB images at lab_ptr."""
+    def forward(self, lab, B: int, W: int, H: int):
+        """Outputs (B, n_y, n_x, 16) float32 on the device for B images of CIELAB planes: a float32
+        CUDA tensor, or a device address that stays valid until the queued work has run (an address
+        whose tensor is dropped at once can be reused by the next allocation before the kernels read it)."""
         import torch
         nx, ny = W // self.spacing, H // self.spacing
         out = torch.empty((B, ny, nx, CHANNELS), dtype=torch.float32, device="cuda")
-        gmmsp_net_forward(self.n, lab_ptr, B, W, H, out)
+        gmmsp_net_forward(self.n, lab, B, W, H, out)
         return out
 
-    def grad(self, lab_ptr: int, B: int, W: int, H: int, target):
-        return gmmsp_net_grad(self.n, lab_ptr, B, W, H, target)
+    def grad(self, lab, B: int, W: int, H: int, target):
+        """(loss, flat gradient) for B images (a tensor or an address, as for forward)."""
+        return gmmsp_net_grad(self.n, lab, B, W, H, target)
 
-    def train_step(self, lab_ptr: int, B: int, W: int, H: int, target, lr: float, want_loss=True):
-        return gmmsp_net_train_step(self.n, lab_ptr, B, W, H, target, lr, want_loss)
+    def train_step(self, lab, B: int, W: int, H: int, target, lr: float, want_loss=True):
+        return gmmsp_net_train_step(self.n, lab, B, W, H, target, lr, want_loss)
 
     def check(self) -> None:
         gmmsp_net_check(self.n)

@@ -89,29 +89,50 @@ def test_forward_matches_oracle(gm, W, H, v, B):
     net.close()
 
 
-def test_gradient_matches_oracle(gm):
+GRAD_CASES = [(481, 321, 15, 2), (100, 70, 15, 3), (64, 50, 9, 2), (77, 61, 12, 1), (40, 40, 21, 2)]
+# Relative L2 error of each layer's weight and bias gradient against the BF16-emulating FP64
+# oracle.  The device's backward pass stores the activation gradients in BF16 and accumulates
+# in FP32, the oracle accumulates in FP64: the gradients differ by the BF16 rounding flips that
+# the two accumulation orders cause.  Measured on a GB300 (largest per-layer value over weights
+# and biases): 481x321 B=2 1.1e-3 (the case with the most positions, so the most flips),
+# 100x70 B=3 1.3e-6, 64x50 v=9 2.7e-7, 77x61 v=12 2.3e-7, 40x40 v=21 4.7e-8; the loss within
+# 1.1e-7 relative.  GRAD_TOL keeps a factor of about 4 over the largest.
+GRAD_TOL = 5e-3
+LOSS_RTOL = 1e-5
+
+
+@pytest.mark.parametrize("W,H,v,B", GRAD_CASES)
+def test_gradient_matches_oracle(gm, W, H, v, B):
+    import json
+    import os
     import torch
     from paper_1612_08792_gb300.learned_init import InitNet, init_weights
-    W, H, v, B = 481, 321, 15, 2
-    lab = lab_planes([30, 31], W, H)
+    lab = lab_planes(range(30, 30 + B), W, H)
     w = init_weights(11)
     net = InitNet(v, weights=w)
     K = (W // v) * (H // v)
     tgt = np.random.default_rng(12).normal(0, 1, (B, K, 10)).astype(np.float32)
-    loss, g = net.grad(torch.from_numpy(lab).cuda().data_ptr(), B, W, H, torch.from_numpy(tgt).cuda())
+    dev = torch.from_numpy(lab).cuda()        # held: a dropped temporary's memory could take the target
+    loss, g = net.grad(dev, B, W, H, torch.from_numpy(tgt).cuda())
     out, cache = ocnn.forward(w, lab, v, emulate_bf16=True)
     ref_loss, g_out = ocnn.loss(out, tgt)
     ref = ocnn.backward(cache, g_out)
-    assert loss == pytest.approx(ref_loss, rel=1e-3)
+    assert loss == pytest.approx(ref_loss, rel=LOSS_RTOL)
     o = 0
+    errs = []
     for taps, cout in ocnn.LAYERS:
         nw = cout * taps * 32
         gw, rw = g[o:o + nw], ref[o:o + nw]
         gb, rb = g[o + nw:o + nw + cout], ref[o + nw:o + nw + cout]
-        assert rel_l2(gw, rw) < 5e-2, (taps, cout, rel_l2(gw, rw))
-        assert rel_l2(gb, rb) < 5e-2, (taps, cout, rel_l2(gb, rb))
+        errs.append((rel_l2(gw, rw), rel_l2(gb, rb)))
         o += nw + cout
     cos = float(np.dot(g, ref) / np.linalg.norm(g) / np.linalg.norm(ref))
+    if os.environ.get("GMMSP_GRAD_OUT"):
+        with open(os.environ["GMMSP_GRAD_OUT"], "a") as fh:
+            fh.write(json.dumps({"case": [W, H, v, B], "layers_w_b": errs, "cos": cos,
+                                 "loss_rel": abs(loss - ref_loss) / ref_loss}) + "\n")
+    for l, (ew, eb) in enumerate(errs):
+        assert ew < GRAD_TOL and eb < GRAD_TOL, (l, ew, eb)
     assert cos > 0.999, cos
     # unused input channels of the first layer get exactly zero gradient
     assert np.all(g[:1024].reshape(32, 32)[:, 27:] == 0)
@@ -131,7 +152,8 @@ def test_theta0_and_targets_match_oracle(gm):
     sp = gm.Superpixels(img0, spacing=v)
     sp.init_from_net(net)
     mu, cs, cc = sp.get_params()
-    out = net.forward(torch.from_numpy(lab[:1]).cuda().data_ptr(), 1, W, H).cpu().numpy()[0]
+    dev0 = torch.from_numpy(lab[:1]).cuda()
+    out = net.forward(dev0, 1, W, H).cpu().numpy()[0]
     rmu, rcs, rcc = ocnn.theta0_from_outputs(out.reshape(-1, 16), lab[0], v)
     assert parity.mean_rel_err(mu, rmu) < 1e-9
     assert parity.cov_rel_err(cs, rcs) < 1e-9
@@ -237,7 +259,8 @@ def test_bounded_wait_gives_up_and_context_survives(gm):
     lab = lab_planes([60], W, H)
     w = init_weights(18)
     net = InitNet(v, weights=w)
-    out = net.forward(torch.from_numpy(lab).cuda().data_ptr(), 1, W, H).cpu().numpy()
+    dev = torch.from_numpy(lab).cuda()
+    out = net.forward(dev, 1, W, H).cpu().numpy()
     net.check()
     ref, _ = ocnn.forward(w, lab, v, emulate_bf16=True)
     assert rel_l2(out, ref) < 2e-3
