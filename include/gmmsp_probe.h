@@ -32,14 +32,19 @@ typedef struct {
 int gmmsp_probe_peaks(gmmsp_peaks *out, char *err, int err_len);
 
 /*
- * gmmsp_probe_smem_patterns launches one short kernel per shared-memory load
- * pattern of the EM kernels (k_lds_pattern<0..9>: warp-uniform 16-, 8- and
- * 4-byte loads, three-address loads, the posterior-row layouts) and
- * synchronises.  It measures nothing itself: run it under a profiler and read
- * the shared-memory wavefronts per load instruction of each kernel.  Returns 0,
- * or 2 on a CUDA error (message in err).
+ * gmmsp_probe_fp64_helpers evaluates, for each of the n device doubles x_dev,
+ * the FP64 helpers the finalize of the M-step uses instead of FP64 division,
+ * square root and logarithm (gmmsp_math.cuh): 1/x and sqrt(x) from an FP32
+ * estimate refined by two Newton-Raphson steps, and log2(x) as the exponent
+ * plus the FP32 log2 of the mantissa.  Results go to rcp_dev, sqrt_dev
+ * (doubles) and log2_dev (floats), n of each, all device memory the caller
+ * owns; the kernel is queued on stream (a cudaStream_t) without
+ * synchronising.  Inputs must be positive, finite and inside the normal FP32
+ * range (the finalize's weights, variances and determinants are).  Returns 0,
+ * 1 for NULL pointers or n < 0, 2 on a CUDA launch error (message in err).
  */
-int gmmsp_probe_smem_patterns(char *err, int err_len);
+int gmmsp_probe_fp64_helpers(const double *x_dev, int n, double *rcp_dev, double *sqrt_dev, float *log2_dev,
+                             void *stream, char *err, int err_len);
 
 #ifdef __cplusplus
 }

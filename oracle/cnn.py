@@ -216,9 +216,11 @@ def targets(mu, cs, cc, lab_img, v: int, lambda_c: float = 8.0):
 def theta0_from_outputs(out_img, lab_img, v: int, lambda_c: float = 8.0, eps_s: float = 2.0,
                         eps_c: float = 8.0):
     """theta_0 of one image from its outputs (K x >= 10): the inverse of targets(),
-    with the mean clipped to the superpixel's window (Eq. Ik: within one cell of
-    its own) and the diagonal covariances floored at eps (Eq. mlams, mlamc);
-    exponents limited to [-10, 10]."""
+    with the spatial mean clipped to the three cells around the seed's own,
+    [(k_x - 1) v, (k_x + 2) v] x [(k_y - 1) v, (k_y + 2) v] (the span of Eq. Ik's
+    window without its clamp to the image, so a border seed's mean may start up
+    to one cell outside the image), and the diagonal covariances floored at eps
+    (Eq. mlams, mlamc); exponents limited to [-10, 10]."""
     o = np.asarray(out_img, dtype=np.float64).reshape(-1, np.shape(out_img)[-1])
     lab_img = np.asarray(lab_img, dtype=np.float64)
     _, H, W = lab_img.shape

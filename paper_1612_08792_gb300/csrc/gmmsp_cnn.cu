@@ -615,8 +615,10 @@ __global__ void k_targets(const double* __restrict__ theta, const float* __restr
   }
 }
 
-// theta_0 from the network outputs (the inverse of the target map): mean
-// clipped to the superpixel's window (Eq. Ik), axis-aligned covariances with
+// theta_0 from the network outputs (the inverse of the target map): spatial
+// mean clipped to the three cells around the seed's own, [(k_x - 1) v,
+// (k_x + 2) v] x [(k_y - 1) v, (k_y + 2) v] (the span of Eq. Ik's window
+// without its clamp to the image), axis-aligned covariances with
 // the diagonal (their eigenvalues) floored at eps (Eq. mlams, mlamc); then
 // the packed E-step coefficients.  Superpixel i reads its 5 mean offsets at
 // dmu + i ds and its 5 log-eigenvalues at logeig + i ls (the network's output

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include "../../include/gmmsp_probe.h"
+#include "gmmsp_math.cuh"
 
 namespace {
 
@@ -96,47 +97,15 @@ __global__ void k_latency(double* out, long long* clk, int iters) {
   clk[1] = t2 - t1;
 }
 
-// Shared-memory load patterns of the EM kernels, one kernel per pattern so
-// that a profiler attributes the l1tex shared-memory wavefronts of each
-// (wavefronts per instruction = l1tex__data_pipe_lsu_wavefronts_mem_shared_op_ld
-// / smsp__inst_executed_op_shared_ld).  Lanes 27-31 repeat lane 0, as the M
-// part's idle lanes would.  Every index stays inside the 4096-float buffer:
-// w = warp * 1024 with warp < 4, and each pattern adds at most 555.
-//   0  16-byte load, one address for the warp (a candidate's coefficients)
-//   1  8-byte load, one address
-//   2  4-byte load, one address
-//   3  16-byte load, three addresses 16 bytes apart
-//   4  4-byte load, rows of 12 floats: pixel l / 9, slot l % 9 (the posteriors)
-//   5  the same with rows of 11 floats
-//   6  8-byte load, three addresses in rows of 12 floats
-//   7  16-byte load, eight consecutive addresses
-//   8  16-byte load, 32 consecutive addresses
-//   9  16-byte load, three addresses in rows of 12 floats (a pixel's colour)
-constexpr int kSmemIters = 1024;
-template <int MODE>
-__global__ void __launch_bounds__(128) k_lds_pattern(float* out) {
-  __shared__ __align__(16) float buf[4096];
-  for (int i = threadIdx.x; i < 4096; i += 128) buf[i] = float(i) * 1e-3f;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ms = lane < 27 ? lane % 9 : 0, ph = lane < 27 ? lane / 9 : 0;
-  const float* w = buf + warp * 1024;
-  float acc = 0.f;
-#pragma unroll 4
-  for (int i = 0; i < kSmemIters; ++i) {
-    const int o = (i * 20) & 511;  // a multiple of 4 floats, varying
-    if (MODE == 0) { const float4 v = *reinterpret_cast<const float4*>(w + o); acc += v.x + v.y + v.z + v.w; }
-    if (MODE == 1) { const float2 v = *reinterpret_cast<const float2*>(w + o); acc += v.x + v.y; }
-    if (MODE == 2) acc += w[o];
-    if (MODE == 3) { const float4 v = *reinterpret_cast<const float4*>(w + o + 4 * ph); acc += v.x + v.y + v.z + v.w; }
-    if (MODE == 4) acc += w[(o & 255) + 12 * ph + ms];
-    if (MODE == 5) acc += w[(o & 255) + 11 * ph + ms];
-    if (MODE == 6) { const float2 v = *reinterpret_cast<const float2*>(w + o + 12 * ph + 10); acc += v.x + v.y; }
-    if (MODE == 7) { const float4 v = *reinterpret_cast<const float4*>(w + o + 4 * (lane & 7)); acc += v.x + v.y + v.z + v.w; }
-    if (MODE == 8) { const float4 v = *reinterpret_cast<const float4*>(w + ((o + 4 * lane) & 1023)); acc += v.x + v.y + v.z + v.w; }
-    if (MODE == 9) { const float4 v = *reinterpret_cast<const float4*>(w + (o & 255) + 12 * ph); acc += v.x + v.y + v.z + v.w; }
-  }
-  out[blockIdx.x * 128 + threadIdx.x] = acc;
+// The finalize's FP64 helpers (gmmsp_math.cuh) on an array of inputs.
+__global__ void k_fp64_helpers(const double* __restrict__ x, int n, double* __restrict__ rcp,
+                               double* __restrict__ sq, float* __restrict__ lg2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  rcp[i] = gmmsp::Num<double>::rcp(v);
+  sq[i] = gmmsp::Num<double>::sqrt_(v);
+  lg2[i] = gmmsp::Num<double>::log2_(v);
 }
 
 template <typename F>
@@ -211,28 +180,16 @@ extern "C" int gmmsp_probe_peaks(gmmsp_peaks* out, char* err, int err_len) {
   return 0;
 }
 
-extern "C" int gmmsp_probe_smem_patterns(char* err, int err_len) {
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  float* out = nullptr;
-  const int blocks = sms * 4;
-  if (e == cudaSuccess) e = cudaMalloc(&out, size_t(blocks) * 128 * sizeof(float));
-  if (e == cudaSuccess) {
-    k_lds_pattern<0><<<blocks, 128>>>(out);
-    k_lds_pattern<1><<<blocks, 128>>>(out);
-    k_lds_pattern<2><<<blocks, 128>>>(out);
-    k_lds_pattern<3><<<blocks, 128>>>(out);
-    k_lds_pattern<4><<<blocks, 128>>>(out);
-    k_lds_pattern<5><<<blocks, 128>>>(out);
-    k_lds_pattern<6><<<blocks, 128>>>(out);
-    k_lds_pattern<7><<<blocks, 128>>>(out);
-    k_lds_pattern<8><<<blocks, 128>>>(out);
-    k_lds_pattern<9><<<blocks, 128>>>(out);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    cudaFree(out);
+extern "C" int gmmsp_probe_fp64_helpers(const double* x_dev, int n, double* rcp_dev, double* sqrt_dev,
+                                        float* log2_dev, void* stream, char* err, int err_len) {
+  if (n < 0 || (n > 0 && (!x_dev || !rcp_dev || !sqrt_dev || !log2_dev))) {
+    if (err && err_len > 0) snprintf(err, err_len, "%s", "null pointer or negative n");
+    return 1;
   }
+  if (n == 0) return 0;
+  k_fp64_helpers<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(x_dev, n, rcp_dev, sqrt_dev,
+                                                                                log2_dev);
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     if (err && err_len > 0) snprintf(err, err_len, "%s", cudaGetErrorString(e));
     return 2;
