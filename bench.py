@@ -76,6 +76,34 @@ INSTR_PER_CAND_MODEL = {"full": INSTR_PER_CAND, "split": 44, "gray": 28}
 FLOPS_PER_CAND_MODEL = {"full": FLOPS_PER_CAND, "split": 53, "gray": 33}
 
 
+# The E + M pass's other two rooflines, reported beside the binding FP32 one:
+#   HBM: DRAM bytes per launch (ncu-measured where the launch variant was captured, else the
+#        algorithmic 12 B of CIELAB per pixel plus the 544 B FP32 partial of every cell) over
+#        the pass time, against the measured copy bandwidth of MEASURED_PEAKS.json;
+#   MUFU (XU pipe): one ex2 per (pixel, candidate) and rcp + lg2 per pixel over the pass time,
+#        against 152 SMs x 32 results per clock (the project probe's measured ex2 rate per SM)
+#        x 2.07 GHz.
+MUFU_PEAK_TOPS = 152 * 32 * 2.070e9 / 1e12
+PARTIAL_BYTES_PER_CELL = 544
+
+
+def side_rooflines(units, pixels, cells, em_ms, traffic):
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    algo = 12 * pixels + PARTIAL_BYTES_PER_CELL * cells
+    nbytes = traffic if traffic else algo
+    gbs = nbytes / (em_ms * 1e-3) / 1e9
+    mufu = units + 2 * pixels
+    tops = mufu / (em_ms * 1e-3) / 1e12
+    return {"hbm": {"bytes_per_launch": int(nbytes), "bytes_source": "ncu dram bytes" if traffic else "algorithmic",
+                    "algorithmic_bytes": int(algo), "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(gbs / hbm_peak, 4),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+            "mufu": {"ops_per_launch": int(mufu), "achieved": round(tops, 3), "peak": round(MUFU_PEAK_TOPS, 3),
+                     "unit": "T MUFU results/s", "frac": round(tops / MUFU_PEAK_TOPS, 4),
+                     "peak_source": "derived: 152 SMs x 32 ex2 per clock (measured per-SM rate) x 2.07 GHz"}}
+
+
 def workload_config(v, nx, ny, K):
     return {
         "workload": f"{W}x{H} synthetic Voronoi sRGB ({REGIONS} regions, noise sigma {SIGMA:g}), "
@@ -418,6 +446,7 @@ def run_other_workload(args):
             bt = gm.SuperpixelsBatch([(h, w) for (w, h) in sizes], spacing=15, stream=stream, colour=args.colour)
             bps, tune = bt.autotune(imgs, reps=3)
         pix, K, cells = bt.info()
+        cells_total = cells
         em_ms = tune[bps]
         units = sum(candidate_units(w, h, 15, w // 15, h // 15) for (w, h) in sizes)
         step = lambda: bt.segment(imgs, ITERS)
@@ -447,6 +476,7 @@ def run_other_workload(args):
             wpc, _ = sp.autotune(reps=3)
         v, nx, ny, K = sp.grid.v, sp.grid.nx, sp.grid.ny, sp.grid.K
         pix = Wd * Hd
+        cells_total = -(-Wd // v) * -(-Hd // v)
         step = lambda: sp.segment(img, ITERS, out=labels)
         for _ in range(max(args.warmup, 3)):
             with torch.cuda.stream(stream):
@@ -479,7 +509,8 @@ def run_other_workload(args):
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
                          "em_pass_ms": round(em_ms, 4), "instr_per_launch": instr,
                          "flops": {"achieved_tflops": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
-                                   "frac": round(achieved / FP32_PEAK_TFLOPS, 4)}},
+                                   "frac": round(achieved / FP32_PEAK_TFLOPS, 4)},
+                         **side_rooflines(units, pix, cells_total, em_ms, None)},
             "gpu_launches": launches * args.steps, "clocks": clocks, **extra}
     print(json.dumps(line), flush=True)
     return 0
@@ -564,7 +595,8 @@ def run_learned(args):
     n = args.images
     N = W * H
     seeds = replica_seeds(rank, n)
-    buf = voronoi_batch(W, H, REGIONS, SIGMA, seeds)
+    regs = torch.empty((n, H, W), dtype=torch.int32, device="cuda")  # the generator's regions (ground truth)
+    buf = voronoi_batch(W, H, REGIONS, SIGMA, seeds, regions_out=regs)
     imgs = [buf[i] for i in range(n)]
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -611,6 +643,41 @@ def run_learned(args):
         _, ll_p2 = plain.segment(imgs, LEARN_T, want_loglik=True)
     llpp_l, llpp_p, llpp_p2 = (float(np.mean(x)) / N for x in (ll_l, ll_p, ll_p2))
     gap = abs(llpp_l - llpp_p) / abs(llpp_p)
+
+    # Plain EM at every iteration count T = 2..10 and the learned start at T = 1..3 on the same
+    # images: device time per step (L2 flushed), log-likelihood per pixel, and the accuracy of
+    # Sec. IV (BR, UE, ASA) against the generator's regions.  The learned start's real gain is
+    # its speed-up over the cheapest plain run within 0.5 % of plain EM's log-likelihood at T = 10.
+    sweep = {}
+    regions = [regs[i] for i in range(n)]
+    for kind, ctx, Ts in (("plain", plain, range(2, ITERS + 1)), ("learned", learned, (1, 2, 3))):
+        for T in Ts:
+            step_t = lambda: ctx.segment(imgs, T)  # noqa: E731
+            with torch.cuda.stream(stream):
+                step_t()
+            ms_t, _ = _timed_steps(step_t, stream, 3, flush, local)
+            with torch.cuda.stream(stream):
+                labels_t, ll_t = ctx.segment(imgs, T, want_loglik=True)
+            mets = gm.gmmsp_segmentation_metrics_many(labels_t, regions, 672, REGIONS, stream=stream)
+            sweep[f"{kind}_{T}"] = {"iters": T, "ms_per_step": round(float(np.median(ms_t)), 4),
+                                    "loglik_per_pixel": float(np.mean(ll_t)) / N,
+                                    **{k: round(float(np.mean([m[k] for m in mets])), 6) for k in ("br", "ue", "asa")}}
+    ll10 = sweep[f"plain_{ITERS}"]["loglik_per_pixel"]
+    within = [T for T in range(2, ITERS + 1)
+              if abs(sweep[f"plain_{T}"]["loglik_per_pixel"] - ll10) / abs(ll10) <= 0.005]
+    t_eq = min(within)
+    same_time = max([T for T in range(2, ITERS + 1)
+                     if sweep[f"plain_{T}"]["ms_per_step"] <= sweep[f"learned_{LEARN_T}"]["ms_per_step"]],
+                    default=None)
+    plain_sweep = {
+        "runs": sweep,
+        "plain_iters_within_0.5pct_of_plain_10": t_eq,
+        "learned_speedup_vs_that_plain": round(sweep[f"plain_{t_eq}"]["ms_per_step"] /
+                                               sweep[f"learned_{LEARN_T}"]["ms_per_step"], 3),
+        "plain_iters_at_learned_time": same_time,
+        "how": "same images as the headline step; 3 timed steps per run (median), L2 flushed before each; "
+               "BR (2 px), UE (eps 0.05), ASA against the generator's Voronoi regions",
+    }
 
     # the network alone (events on its stream) and the E + M pass at the chosen launch shape
     lab_ptr = learned.lab_ptr()
@@ -699,6 +766,7 @@ def run_learned(args):
         "loglik_per_pixel": {"learned": llpp_l, "plain": llpp_p, f"plain_{LEARN_T}_iters": llpp_p2,
                              "rel_gap": gap, "target": 0.005},
         "label_agreement_with_plain": round(agree, 5),
+        "plain_sweep": plain_sweep,
         "roofline": {"kernel": "k_em_pass_batch (fused E-step + M-step partials)", "bound": "alu",
                      "achieved": round(achieved_i, 3), "peak": round(FP32_PEAK_TINST, 3),
                      "unit": "T FP32-lane-instr/s", "frac": round(achieved_i / FP32_PEAK_TINST, 4),
@@ -708,7 +776,10 @@ def run_learned(args):
                      "em_pass_ms": round(em_ms, 5), "instr_per_launch": instr,
                      "flops": {"achieved_tflops": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
                                "frac": round(achieved / FP32_PEAK_TFLOPS, 4)},
-                     "timing": "batch E+M pass alone, mean of repeated launches (autotuner)"},
+                     "timing": "batch E+M pass alone, mean of repeated launches (autotuner)",
+                     **side_rooflines(units, n * N, n * 726, em_ms,
+                                      EM_BATCH_TRAFFIC_PER_IMAGE[bps] * n if bps in EM_BATCH_TRAFFIC_PER_IMAGE
+                                      else None)},
         "tuning": tuning,
         "net_roofline": {"kernels": "k_pix + 4 x k_gemm (forward)", "bound": "tensor",
                          "achieved": round(net_tflops, 3), "peak": bf16_peak, "unit": "TFLOP/s",
