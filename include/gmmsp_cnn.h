@@ -15,7 +15,9 @@
  *   x0: the 3 x 3 pixel patches of each cell (27 values: L/50 - 1, a/50, b/50
  *       of 9 pixels, 5 zeros), f x f patches per cell;
  *   h1 = ReLU(W1 x0 + b1), h2 = ReLU(W2 h1 + b2)       (1 x 1 layers);
- *   c0 = mean of h2 over the cell's patches             (the n_x x n_y grid);
+ *   c0 = mean of h2 over the cell's patches             (the n_x x n_y grid),
+ *        channels 29-31 replaced by the scaled colour of the cell's start
+ *        pixel (x_c, y_c) below, so that the cell layers see z_c;
  *   c_l = ReLU(conv3x3(c_{l-1}) + b), l = 1..3          (zero padding);
  *   out = conv3x3(c3) + b6, 16 channels of which 10 are used.
  * Outputs per superpixel k with start point (x_c, y_c) = (k_x v + v/2,

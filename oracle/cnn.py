@@ -13,7 +13,8 @@ the plain definition of the network that the CUDA path implements:
       (L/50 - 1, a/50, b/50 of the 9 pixels, channel (3 dy + dx) 3 + colour)
       and 5 zeros; f x f patches per cell
   h1 = ReLU(W1 x0 + b1), h2 = ReLU(W2 h1 + b2)        1 x 1 layers, 32 channels
-  c0 = mean of h2 over the cell's patches              the n_x x n_y grid
+  c0 = mean of h2 over the cell's patches              the n_x x n_y grid; channels
+       29-31 replaced by the start point's pixel inputs (L/50 - 1, a/50, b/50)
   c_l = ReLU(conv3x3(c_{l-1}) + b_l), l = 1, 2, 3      zero padding
   out = conv3x3(c3) + b6                               16 channels, 10 used
 
@@ -47,6 +48,16 @@ USED = 10     # used outputs
 LAYERS = [(1, C), (1, C), (9, C), (9, C), (9, C), (9, OUT)]  # (taps, cout); cin = 32
 IN_SCALE = 0.02
 COLOUR_UNIT = 10.0
+START_CH = 29  # c0 channels START_CH.. START_CH + 2 carry the start pixel's scaled colour
+
+
+def start_inputs(x0, v: int):
+    """The x0 inputs of the start pixel (k_x v + v // 2, k_y v + v // 2) of every cell:
+    (B, n_y, n_x, 3), taken from the patch and the position inside it that hold it."""
+    c = v // 2
+    q, d = c // 3, c % 3
+    ch = (d * 3 + d) * 3
+    return x0[:, :, :, q, q, ch:ch + 3]
 
 
 def param_count() -> int:
@@ -143,7 +154,9 @@ def forward(flat, lab, v: int, emulate_bf16: bool = False):
     x0 = rnd(patches(lab, v))
     h1 = rnd(np.maximum(x0 @ Wq[0].T + bs[0], 0.0))
     h2 = rnd(np.maximum(h1 @ Wq[1].T + bs[1], 0.0))
-    c0 = rnd(h2.mean(axis=(3, 4)))
+    c0 = h2.mean(axis=(3, 4))
+    c0[..., START_CH:START_CH + 3] = start_inputs(x0, v)
+    c0 = rnd(c0)
     c = [c0]
     for l in (2, 3, 4):
         c.append(rnd(np.maximum(conv3x3(c[-1], Wq[l], bs[l]), 0.0)))
@@ -176,6 +189,8 @@ def backward(cache, g_out):
         g = rnd(gx * (x > 0)) if l > 2 else rnd(gx)   # c0 is a mean, without a ReLU
     h1, h2, x0 = cache["h1"], cache["h2"], cache["x0"]
     ff = h2.shape[3] * h2.shape[4]
+    g = g.copy()
+    g[..., START_CH:START_CH + 3] = 0.0      # those c0 channels are inputs, not pooled h2
     g2 = rnd(g[:, :, :, None, None, :] / ff * (h2 > 0))
     rows = lambda a: a.reshape(-1, a.shape[-1])  # noqa: E731  (all patch positions)
     grads[1] = (rows(g2).T @ rows(h1), rows(g2).sum(axis=0))

@@ -51,6 +51,7 @@ constexpr int kChunk = 2048;               // positions per weight-gradient bloc
 constexpr int kLossBlocks = 128;
 
 constexpr float kInScale = 0.02f;    // L, a, b -> about [-1, 1] (L shifted by 50)
+constexpr int kStartCh = 29;         // c0 channels 29-31: the start pixel's scaled colour (not pooled)
 constexpr float kColourUnit = 10.f;  // colour mean offsets in units of 10
 
 // Flat parameter vector W1, b1, ..., W6, b6 with W[cout][taps * 32 + cin].
@@ -397,6 +398,10 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
   const bool valid = lc < a.cpb && cell < a.cells;
   const long long grow = (long long)blockIdx.x * 128 + tid;  // row of the training buffers
   uint32_t u[16];
+  // the Sec. III-C start pixel (k_x v + v/2, k_y v + v/2) lies in patch (qs, qs) at (ds, ds)
+  const int qs = (a.v / 2) / 3, ds = (a.v / 2) % 3;
+  const bool start_row = valid && q == qs * a.f + qs;
+  float zs[3] = {0.f, 0.f, 0.f};
   {
     float in[32];
 #pragma unroll
@@ -418,10 +423,16 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
           in[c + 0] = fmaf(__ldg(P + i), kInScale, -1.f);
           in[c + 1] = __ldg(P + N + i) * kInScale;
           in[c + 2] = __ldg(P + 2 * N + i) * kInScale;
+          if (start_row && dy == ds && dx == ds) {
+            zs[0] = in[c + 0];
+            zs[1] = in[c + 1];
+            zs[2] = in[c + 2];
+          }
         }
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) u[i] = pack2(in[2 * i], in[2 * i + 1]);
+
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -489,10 +500,14 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
       for (int idx = tid; idx < a.cpb * kC; idx += 128) {
         const int l = idx >> 5, ch = idx & 31;
         const long long cl = (long long)blockIdx.x * a.cpb + l;
-        if (cl >= a.cells) continue;
+        if (cl >= a.cells || ch >= kStartCh) continue;
         float s = 0.f;
         for (int p = 0; p < ff; ++p) s += sH[l * ff + p][ch];
         a.c0[cl * kC + ch] = __float2bfloat16(s / float(ff));
+      }
+      if (start_row) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a.c0[cell * kC + kStartCh + c] = __float2bfloat16(zs[c]);
       }
     }
   }
@@ -507,7 +522,8 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
 
 // ------------------------------------------------------------ elementwise
 // Gradient of the pre-activation of h2 from the gradient of c0 (average
-// pooling, then the ReLU of h2): g[row] = g_c0[cell(row)] / f^2 where h2 > 0.
+// pooling, then the ReLU of h2): g[row] = g_c0[cell(row)] / f^2 where h2 > 0,
+// for the pooled channels (channels kStartCh.. are the start pixel's inputs).
 __global__ void k_pool_bwd(const __nv_bfloat16* __restrict__ gc0, const __nv_bfloat16* __restrict__ h2,
                            long long nrows, int cpb, int ff, long long cells, __nv_bfloat16* __restrict__ g) {
   const float inv = 1.f / float(ff);
@@ -519,7 +535,8 @@ __global__ void k_pool_bwd(const __nv_bfloat16* __restrict__ gc0, const __nv_bfl
     const int lc = int(row & 127) / ff;
     const long long cell = blk * cpb + lc;
     float v = 0.f;
-    if (lc < cpb && cell < cells && __bfloat162float(h2[i]) > 0.f) v = __bfloat162float(gc0[cell * kC + ch]) * inv;
+    if (lc < cpb && cell < cells && ch < kStartCh && __bfloat162float(h2[i]) > 0.f)
+      v = __bfloat162float(gc0[cell * kC + ch]) * inv;
     g[i] = __float2bfloat16(v);
   }
 }

@@ -260,6 +260,8 @@ def main(argv=None):
     ev = sub.add_parser("eval")
     ev.add_argument("--weights", default=pretrained_path(15))
     ev.add_argument("--images", type=int, default=64)
+    ev.add_argument("--plain", default="2,3,10", help="plain-EM iteration counts (comma separated)")
+    ev.add_argument("--learned", default="2", help="iteration counts after the learned start")
     args = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
@@ -274,7 +276,9 @@ def main(argv=None):
         print(json.dumps({"train_seconds": round(secs, 1), "final_loss": hist[-1][1], "heldout": ev}))
     else:
         net = InitNet.load(args.weights)
-        print(json.dumps(evaluate(net, n_images=args.images)))
+        print(json.dumps(evaluate(net, n_images=args.images,
+                                  plain_iters=tuple(int(t) for t in args.plain.split(",")),
+                                  learned_iters=tuple(int(t) for t in args.learned.split(",")))))
     return 0
 
 

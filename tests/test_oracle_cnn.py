@@ -71,7 +71,14 @@ def test_pool_is_block_mean():
     h2, c0 = cache["h2"], cache["c"][0]
     ny, nx, f = H // v, W // v, v // 3
     ref = h2.reshape(B, ny, nx, f * f, 32).mean(axis=3)
-    np.testing.assert_allclose(c0, ref, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(c0[..., :cnn.START_CH], ref[..., :cnn.START_CH], rtol=1e-13, atol=1e-13)
+    # the last three channels are the scaled colour of the Sec. III-C start pixel (k_x v + v//2, ...)
+    c = v // 2
+    for ky in range(ny):
+        for kx in range(nx):
+            px = lab[0, :, ky * v + c, kx * v + c]
+            want = [px[0] * cnn.IN_SCALE - 1.0, px[1] * cnn.IN_SCALE, px[2] * cnn.IN_SCALE]
+            np.testing.assert_allclose(c0[0, ky, kx, cnn.START_CH:], want, rtol=1e-13, atol=1e-13)
     assert out.shape == (B, ny, nx, 16)
 
 
