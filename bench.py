@@ -669,8 +669,15 @@ def run_learned(args):
     same_time = max([T for T in range(2, ITERS + 1)
                      if sweep[f"plain_{T}"]["ms_per_step"] <= sweep[f"learned_{LEARN_T}"]["ms_per_step"]],
                     default=None)
+    ll_learned = sweep[f"learned_{LEARN_T}"]["loglik_per_pixel"]
+    t_match = min([T for T in range(2, ITERS + 1) if sweep[f"plain_{T}"]["loglik_per_pixel"] >= ll_learned],
+                  default=None)
     plain_sweep = {
         "runs": sweep,
+        "plain_iters_matching_learned_loglik": t_match,
+        "learned_speedup_vs_plain_at_its_loglik": (round(sweep[f"plain_{t_match}"]["ms_per_step"] /
+                                                         sweep[f"learned_{LEARN_T}"]["ms_per_step"], 3)
+                                                   if t_match else None),
         "plain_iters_within_0.5pct_of_plain_10": t_eq,
         "learned_speedup_vs_that_plain": round(sweep[f"plain_{t_eq}"]["ms_per_step"] /
                                                sweep[f"learned_{LEARN_T}"]["ms_per_step"], 3),
