@@ -293,6 +293,38 @@ const char *gmmsp_batch_last_error(gmmsp_batch b);
 void gmmsp_batch_destroy(gmmsp_batch b);
 
 /*
+ * Bounds-check status (no counterpart in the paper: a stand-in for a memory
+ * checker, which is not run on this hardware).  A library built with the
+ * compile flag GMMSP_CHECK_BOUNDS (paper_1612_08792_gb300/build.py,
+ * build(checked=True): _build/libgmmsp_checked.so) tests the index of every
+ * global-memory access of the EM kernels against its buffer -- candidate
+ * coefficients, pixel reads, per-cell partial sums, superpixel parameters,
+ * labels and their values, the batch table lookups -- skips an access that
+ * falls outside and records the first such event of each kernel translation
+ * unit.  The ordinary build compiles the checks away.
+ *   checked          receives 1 if this library was built with the checks,
+ *                    else 0;
+ *   first_violation  receives 0 if nothing was recorded since the last call,
+ *                    else (1 << 63) | site << 40 | (index mod 2^40), site one
+ *                    of the GMMSP_BND_* values.
+ * A checked library synchronises the device, reads and clears the status
+ * words; an unchecked one touches no device.  Either pointer may be NULL.
+ * Errors: GMMSP_E_CUDA.
+ */
+#define GMMSP_BND_GP 1         /* a candidate's packed coefficients: superpixel in [0, K) */
+#define GMMSP_BND_PIXEL_X 2    /* a pixel read: x in [0, W)                                */
+#define GMMSP_BND_PIXEL_Y 3    /* a pixel read or write: y in [0, H) (or the pixel index) */
+#define GMMSP_BND_PARTIAL_W 4  /* a cell's partial sums written: cell in [0, cells)        */
+#define GMMSP_BND_PARTIAL_R 5  /* partial sums read by the finalize: cell in [0, cells)    */
+#define GMMSP_BND_THETA 6      /* a superpixel's parameters written: k in [0, K)           */
+#define GMMSP_BND_LABEL 7      /* a label written: pixel in [0, W H)                       */
+#define GMMSP_BND_LABEL_K 8    /* a label's value: k in [0, K)                             */
+#define GMMSP_BND_CELL_LL 9    /* a cell's log-likelihood written: cell in [0, cells)      */
+#define GMMSP_BND_IMAGE 10     /* a batch item's image: in [0, n)                          */
+#define GMMSP_BND_ITEM 11      /* a batch item in its image: cell or superpixel in range   */
+gmmsp_status gmmsp_bounds_status(int *checked, unsigned long long *first_violation);
+
+/*
  * Allocation-free segmentation (the paper has no counterpart; this serves
  * callers that cannot allocate device memory where they run: code inside a
  * memory pool or a caching allocator that owns all device memory, code that

@@ -25,7 +25,7 @@ __all__ = [
     "gmmsp_default_params", "gmmsp_init", "gmmsp_reinit", "gmmsp_em_iters", "gmmsp_labels",
     "gmmsp_segment", "gmmsp_get_lab", "gmmsp_get_grid", "gmmsp_get_params", "gmmsp_set_params", "gmmsp_get_stats",
     "gmmsp_profile_kernel", "gmmsp_probe_peaks", "gmmsp_probe_fp64_helpers", "gmmsp_set_timing", "gmmsp_get_timing", "gmmsp_set_launch", "gmmsp_get_launch",
-    "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "SuperpixelsBatch",
+    "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "SuperpixelsBatch", "gmmsp_bounds_status",
     "gmmsp_batch_create", "gmmsp_batch_segment", "gmmsp_batch_get_params", "gmmsp_batch_autotune",
     "gmmsp_batch_set_launch", "gmmsp_batch_set_tuning", "gmmsp_batch_info", "gmmsp_batch_destroy", "gmmsp_status_string", "gmmsp_destroy",
     "gmmsp_batch_get_tuning", "gmmsp_batch_set_init_net", "gmmsp_batch_lab", "gmmsp_batch_targets", "gmmsp_batch_get_lab",
@@ -60,7 +60,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return os.path.join(_HERE, "_build", "libgmmsp.so")
+    """The library to load: GMMSP_LIBRARY if set (e.g. the bounds-checked build,
+    _build/libgmmsp_checked.so), else _build/libgmmsp.so."""
+    return os.environ.get("GMMSP_LIBRARY") or os.path.join(_HERE, "_build", "libgmmsp.so")
 
 
 class GmmspError(RuntimeError):
@@ -112,6 +114,7 @@ def load_library(path: str | None = None):
             "gmmsp_last_error": (ctypes.c_char_p, [P]),
             "gmmsp_status_string": (ctypes.c_char_p, [I]),
             "gmmsp_destroy": (None, [P]),
+            "gmmsp_bounds_status": (I, [pint, ctypes.POINTER(ctypes.c_ulonglong)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -119,6 +122,32 @@ def load_library(path: str | None = None):
             f.argtypes = args
         _lib = lib
         return lib
+
+
+BOUNDS_SITES = {1: "gp", 2: "pixel_x", 3: "pixel_y", 4: "partial_write", 5: "partial_read", 6: "theta",
+                7: "label", 8: "label_value", 9: "cell_ll", 10: "batch_image", 11: "batch_item"}
+
+
+def gmmsp_bounds_status():
+    """(checked, first violation or None): whether this library was built with
+    GMMSP_CHECK_BOUNDS and, if so, the first out-of-range index its EM kernels met
+    since the last call, as {"site": name, "index": i} (reading clears it)."""
+    checked, code = ctypes.c_int(), ctypes.c_ulonglong()
+    st = load_library().gmmsp_bounds_status(ctypes.byref(checked), ctypes.byref(code))
+    if st != 0:
+        raise GmmspError(st, "bounds status")
+    return bool(checked.value), bounds_decode(code.value)
+
+
+def bounds_decode(code: int):
+    """A gmmsp_bounds_status word -> None or {"site", "index"} (index sign-extended from 40 bits)."""
+    if not code:
+        return None
+    site = (code >> 40) & 0x7FFFFF
+    idx = code & ((1 << 40) - 1)
+    if idx >= 1 << 39:
+        idx -= 1 << 40
+    return {"site": BOUNDS_SITES.get(site, site), "index": idx}
 
 
 def _check(ctx, st: int):

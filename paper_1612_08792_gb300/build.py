@@ -2,7 +2,9 @@
 
 Each .cu translation unit is compiled in parallel, then linked into
 ``paper_1612_08792_gb300/_build/libgmmsp.so`` (CUDA runtime linked
-statically).  No cmake, one ``-gencode``.
+statically).  No cmake, one ``-gencode``.  ``build(checked=True)`` builds the
+bounds-checked variant (compile flag GMMSP_CHECK_BOUNDS, see
+gmmsp_bounds_status in include/gmmsp.h) into ``_build/libgmmsp_checked.so``.
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgmmsp.so")
+LIB_CHECKED = os.path.join(BUILD, "libgmmsp_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include")] + ARCH
@@ -34,8 +37,9 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _fingerprint() -> str:
+def _fingerprint(extra_flags=()) -> str:
     h = hashlib.sha256()
+    h.update(" ".join(extra_flags).encode())
     files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
         *sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))),
         os.path.abspath(__file__)]
@@ -47,17 +51,20 @@ def _fingerprint() -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "libgmmsp.stamp")
-    fp = _fingerprint()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == fp:
-        return LIB
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, checked: bool = False) -> str:
+    flags = ["-DGMMSP_CHECK_BOUNDS"] if checked else []
+    lib = LIB_CHECKED if checked else LIB
+    objdir = os.path.join(BUILD, "checked") if checked else BUILD
+    os.makedirs(objdir, exist_ok=True)
+    stamp = os.path.join(BUILD, "libgmmsp_checked.stamp" if checked else "libgmmsp.stamp")
+    fp = _fingerprint(flags)
+    if not force and os.path.exists(lib) and os.path.exists(stamp) and open(stamp).read() == fp:
+        return lib
     nvcc = _nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = flags + (["-Xptxas", "-v"] if ptxas_info else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = [nvcc, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -70,17 +77,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for _, log in results:
             if log:
                 print(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as fh:
         fh.write(fp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -653,6 +653,21 @@ gmmsp_status gmmsp_profile_kernel(gmmsp_ctx c, int which, int reps, int32_t* lab
   return out;
 }
 
+gmmsp_status gmmsp_bounds_status(int* checked, unsigned long long* first_violation) {
+#ifdef GMMSP_CHECK_BOUNDS
+  if (checked) *checked = 1;
+  if (cudaDeviceSynchronize() != cudaSuccess) return GMMSP_E_CUDA;
+  unsigned long long w[2] = {0ull, 0ull};
+  if (gmmsp::bounds_take_em(&w[0]) != cudaSuccess || gmmsp::bounds_take_prep(&w[1]) != cudaSuccess)
+    return GMMSP_E_CUDA;
+  if (first_violation) *first_violation = w[0] ? w[0] : w[1];
+#else
+  if (checked) *checked = 0;
+  if (first_violation) *first_violation = 0ull;
+#endif
+  return GMMSP_OK;
+}
+
 gmmsp_status gmmsp_set_launch(gmmsp_ctx c, int warps_per_cell) {
   if (!c) return GMMSP_E_INVALID;
   if (warps_per_cell != 1 && warps_per_cell != 2 && warps_per_cell != 4)

@@ -51,6 +51,15 @@ __device__ __forceinline__ Cell make_cell(const Geom& g, int cell) {
   return c;
 }
 
+// The colour of pixel (x, y) of image g, read through GMMSP_IN_BOUNDS (a
+// checked build yields 0 outside the image and records the event).
+template <int CM, class Src>
+__device__ __forceinline__ float4 load_pixel(const Src& s, const Geom& g, int x, int y) {
+  if (!(GMMSP_IN_BOUNDS(x, g.W, BND_PIXEL_X) && GMMSP_IN_BOUNDS(y, g.H, BND_PIXEL_Y)))
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+  return load_z<CM>(s, x, y);
+}
+
 // log2 p(z; theta_k) for one candidate: the log normaliser plus the two
 // quadratic forms, with -1/2 log2(e) Sigma^{-1} folded into the coefficients.
 // fx, fy are the pixel's coordinates relative to the cell origin (the staged

@@ -59,7 +59,7 @@ __device__ __forceinline__ float4 staged_param(const Geom& g, const Cell& c, con
   float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
   if ((c.mask >> s) & 1u) {
     const int k = (c.cy - 1 + s / 3) * g.nx + (c.cx - 1 + s % 3);
-    v = __ldg(reinterpret_cast<const float4*>(gp) + k * 4 + q);
+    if (GMMSP_IN_BOUNDS(k, g.K, BND_GP)) v = __ldg(reinterpret_cast<const float4*>(gp) + k * 4 + q);
     if (q == 0) {
       v.x += float((s % 3 - 1) * g.v);
       v.y += float((s / 3 - 1) * g.v);
@@ -166,7 +166,7 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
   if (wic * 32 + lane < npx) {
     int rx0, ry0;
     locate(wic * 32 + lane, rx0, ry0);
-    zn = load_z<CM>(lab, c.x0 + rx0, c.y0 + ry0);
+    zn = load_pixel<CM>(lab, g, c.x0 + rx0, c.y0 + ry0);
   }
   for (int base = wic * 32; base < npx; base += 32 * WPC) {
     const int p = base + lane;
@@ -175,7 +175,7 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
     if (p + 32 * WPC < npx) {
       int rx1, ry1;
       locate(p + 32 * WPC, rx1, ry1);
-      zn = load_z<CM>(lab, c.x0 + rx1, c.y0 + ry1);
+      zn = load_pixel<CM>(lab, g, c.x0 + rx1, c.y0 + ry1);
     }
     int rx = 0, ry = 0;
     if (p < npx) {
@@ -274,7 +274,7 @@ __device__ __forceinline__ void em_cell_block(const Src& lab, const Geom& g, con
   if (lane == 0) sm.part[warp][kSlots * kStats] = ll;
   if (WPC == 1) __syncwarp(); else __syncthreads();
   // Cell totals (sum over the WPC warps of the cell), written as PT.
-  if (active) {
+  if (active && GMMSP_IN_BOUNDS(cell, g.ncells, BND_PARTIAL_W)) {
     PT* out = partials + (long long)cell * kPartStride;
     const int w0 = slot * WPC;
     for (int o = t; o < kPartStride; o += 32 * WPC) {
@@ -323,7 +323,10 @@ __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch(const Bat
   EmSmem<1>& sm = *reinterpret_cast<EmSmem<1>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int cell = blockIdx.x * kEmWarps + warp; cell < total_cells; cell += gridDim.x * kEmWarps) {
-    const BatchImage& im = imgs[find_image(imgs, n, cell, 0)];
+    const int ii = find_image(imgs, n, cell, 0);
+    if (!GMMSP_IN_BOUNDS(ii, n, BND_IMAGE)) continue;
+    const BatchImage& im = imgs[ii];
+    if (!GMMSP_IN_BOUNDS(cell - im.cell_off, im.g.ncells, BND_ITEM)) continue;
     const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
     em_cell_block<PT, SHIFT, 1, LabPlanar, CM>(src, im.g, gp + (long long)im.k_off * kGP,
                                                partials + (long long)im.cell_off * kPartStride,
@@ -346,7 +349,10 @@ __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch_flat(cons
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cell = blockIdx.x * kEmWarps + warp;
   if (cell >= total_cells) return;  // whole warps only; a warp works alone on its cell
-  const BatchImage& im = imgs[find_image(imgs, n, cell, 0)];
+  const int ii = find_image(imgs, n, cell, 0);
+  if (!GMMSP_IN_BOUNDS(ii, n, BND_IMAGE)) return;
+  const BatchImage& im = imgs[ii];
+  if (!GMMSP_IN_BOUNDS(cell - im.cell_off, im.g.ncells, BND_ITEM)) return;
   const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
   em_cell_block<PT, SHIFT, 1, LabPlanar, CM>(src, im.g, gp + (long long)im.k_off * kGP,
                                              partials + (long long)im.cell_off * kPartStride, cell - im.cell_off,
@@ -380,7 +386,7 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
     if (p < npx) {
       int rx, ry;
       locate(p, rx, ry);
-      zn[j] = load_z<CM>(lab, c.x0 + rx, c.y0 + ry);
+      zn[j] = load_pixel<CM>(lab, g, c.x0 + rx, c.y0 + ry);
     }
   }
   for (int p0 = lane; p0 - lane < npx; p0 += 32 * kLabelPPL) {
@@ -393,7 +399,7 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
       if (pn < npx) {
         int x1, y1;
         locate(pn, x1, y1);
-        zn[j] = load_z<CM>(lab, c.x0 + x1, c.y0 + y1);
+        zn[j] = load_pixel<CM>(lab, g, c.x0 + x1, c.y0 + y1);
       }
       locate(p0 + 32 * j, rx[j], ry[j]);
     }
@@ -431,8 +437,9 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
           if (FULL || ((c.mask >> s) & 1u)) sum += ex2_approx(e[j][s] - m[j]);
         ll += m[j] + lg2_approx(sum);
       }
-      labels[(long long)(c.y0 + ry[j]) * g.W + (c.x0 + rx[j])] =
-          (c.cy - 1 + best[j] / 3) * g.nx + (c.cx - 1 + best[j] % 3);
+      const long long at = (long long)(c.y0 + ry[j]) * g.W + (c.x0 + rx[j]);
+      const int kl = (c.cy - 1 + best[j] / 3) * g.nx + (c.cx - 1 + best[j] % 3);
+      if (GMMSP_IN_BOUNDS(at, (long long)g.W * g.H, BND_LABEL) && GMMSP_IN_BOUNDS(kl, g.K, BND_LABEL_K)) labels[at] = kl;
     }
   }
 }
@@ -458,7 +465,7 @@ __device__ __forceinline__ void label_cell_warp(const Src& lab, const Geom& g, c
     label_cell_pixels<false, true, Src, CM>(lab, g, c, sp, lane, labels, ll);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
-  if (lane == 0) cell_ll[cell] = double(ll) * 0.69314718055994530942;
+  if (lane == 0 && GMMSP_IN_BOUNDS(cell, g.ncells, BND_CELL_LL)) cell_ll[cell] = double(ll) * 0.69314718055994530942;
 }
 
 template <class Src, int CM>
@@ -483,7 +490,10 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass_batch(const BatchI
   __shared__ float4 sp_all[kEmWarps][kSlots * 4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int cell = blockIdx.x * kEmWarps + warp; cell < total_cells; cell += gridDim.x * kEmWarps) {
-    const BatchImage& im = imgs[find_image(imgs, n, cell, 0)];
+    const int ii = find_image(imgs, n, cell, 0);
+    if (!GMMSP_IN_BOUNDS(ii, n, BND_IMAGE)) continue;
+    const BatchImage& im = imgs[ii];
+    if (!GMMSP_IN_BOUNDS(cell - im.cell_off, im.g.ncells, BND_ITEM)) continue;
     const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
     label_cell_warp<LabPlanar, CM>(src, im.g, gp + (long long)im.k_off * kGP, im.labels,
                                    cell_ll ? cell_ll + im.cell_off : nullptr, cell - im.cell_off, sp_all[warp],
@@ -559,6 +569,7 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
                                            unsigned& rs, unsigned& rc) {
   using T = typename std::conditional<SHIFT, double, float>::type;  // arithmetic type of the update
   constexpr bool kShifted = SHIFT;
+  if (!GMMSP_IN_BOUNDS(k, g.K, BND_THETA)) return;
   const int kx = k % g.nx, ky = k / g.nx;
   T S[kStats];
   float hi[kStats], lo[kStats];
@@ -577,6 +588,7 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
     for (int dx = -1; dx <= 1; ++dx) {
       const int cx = kx + dx;
       if (cx < 0 || cx >= g.ncx) continue;
+      if (!GMMSP_IN_BOUNDS(cy * g.ncx + cx, g.ncells, BND_PARTIAL_R)) continue;
       const PT* P = partials + (long long)(cy * g.ncx + cx) * kPartStride + ((1 - dy) * 3 + (1 - dx)) * kStats;
 #pragma unroll
       for (int j = 0; j < kStats; ++j) {
@@ -691,7 +703,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize_batch(const BatchImage
   for (int base = blockIdx.x * kFinThreads; base < total_k; base += stride) {
     const int k = base + threadIdx.x;
     if (k < total_k) {
-      const BatchImage& im = imgs[find_image(imgs, n, k, 1)];
+      const int ii = find_image(imgs, n, k, 1);
+      if (!GMMSP_IN_BOUNDS(ii, n, BND_IMAGE)) continue;
+      const BatchImage& im = imgs[ii];
+      if (!GMMSP_IN_BOUNDS(k - im.k_off, im.g.K, BND_ITEM)) continue;
       finalize_k<PT, SHIFT>(im.g, partials + (long long)im.cell_off * kPartStride, theta + (long long)im.k_off * kTheta,
                      gp + (long long)im.k_off * kGP, eps_s, eps_c, k - im.k_off, dead, rs, rc);
     }
@@ -752,6 +767,7 @@ __device__ __forceinline__ void finalize_l16_body(const Geom& g, const float* __
   constexpr unsigned kFull = 0xffffffffu;
   const int l = threadIdx.x & 15;
   // X: [0..14] sums, [16..20] d, [21..29] M, [30..36] products, [37..45] scratch
+  valid = valid && GMMSP_IN_BOUNDS(k, g.K, BND_THETA);
   const int kk = valid ? k : 0;
   const int kx = kk % g.nx, ky = kk / g.nx;
 
@@ -764,7 +780,8 @@ __device__ __forceinline__ void finalize_l16_body(const Geom& g, const float* __
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
         const int cy = ky + dy, cx = kx + dx;
-        const bool in = valid && l < kStats && cy >= 0 && cy < g.ncy && cx >= 0 && cx < g.ncx;
+        const bool in = valid && l < kStats && cy >= 0 && cy < g.ncy && cx >= 0 && cx < g.ncx &&
+                        GMMSP_IN_BOUNDS(cy * g.ncx + cx, g.ncells, BND_PARTIAL_R);
         v[(dy + 1) * 3 + (dx + 1)] =
             in ? __ldg(partials + (long long)(cy * g.ncx + cx) * kPartStride +
                        ((1 - dy) * 3 + (1 - dx)) * kStats + l)
@@ -955,8 +972,10 @@ __global__ void __launch_bounds__(kFin16Threads) k_finalize_l16_batch(const Batc
   __shared__ float shf[kFin16Threads / 16][8];
   const int q = threadIdx.x >> 4;
   const int kg = blockIdx.x * (kFin16Threads / 16) + q;
-  const bool valid = kg < total_k;
-  const BatchImage& im = imgs[find_image(imgs, n, valid ? kg : 0, 1)];
+  const int ii = find_image(imgs, n, kg < total_k ? kg : 0, 1);
+  const bool img_ok = GMMSP_IN_BOUNDS(ii, n, BND_IMAGE);
+  const BatchImage& im = imgs[img_ok ? ii : 0];
+  const bool valid = kg < total_k && img_ok && GMMSP_IN_BOUNDS(kg - im.k_off, im.g.K, BND_ITEM);
   finalize_l16_body(im.g, partials + (long long)im.cell_off * kPartStride, theta + (long long)im.k_off * kTheta,
                     gp + (long long)im.k_off * kGP, eps_s, eps_c, valid ? kg - im.k_off : 0, valid, sh[q], shf[q],
                     counters);
@@ -967,6 +986,19 @@ __global__ void __launch_bounds__(kFinThreads) k_ll_reduce(const double* __restr
   pdl_wait();
   pdl_trigger();
   block_ll_sum<double, kFinThreads, false>(cell_ll, 1, n, blk, ticket, out);
+}
+
+// ---------------------------------------------------------------- bounds status
+cudaError_t bounds_take_em(unsigned long long* word) {
+  *word = 0ull;
+#ifdef GMMSP_CHECK_BOUNDS
+  cudaError_t e = cudaMemcpyFromSymbol(word, g_bounds_word, sizeof(*word));
+  if (e != cudaSuccess) return e;
+  const unsigned long long zero = 0ull;
+  return cudaMemcpyToSymbol(g_bounds_word, &zero, sizeof(zero));
+#else
+  return cudaSuccess;
+#endif
 }
 
 // ---------------------------------------------------------------- launchers

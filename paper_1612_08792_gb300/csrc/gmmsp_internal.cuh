@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/gmmsp.h"
+
 #if __has_include(<nvtx3/nvToolsExt.h>)
 #include <nvtx3/nvToolsExt.h>
 #define GMMSP_HAVE_NVTX 1
@@ -115,6 +117,47 @@ __device__ __forceinline__ float4 load_z(const Src& s, int x, int y) {
   if constexpr (CM == kColourGray) return make_float4(s.load_l(x, y), 0.f, 0.f, 0.f);
   else return s.load(x, y);
 }
+
+// Bounds checking (compile flag GMMSP_CHECK_BOUNDS; a stand-in for a memory
+// checker).  A checked build tests the index of every global access at the
+// sites below against the extent of its buffer.  An index outside [0, n) is
+// not used (the load yields 0, the store is skipped) and the first such event
+// of a translation unit is kept in its status word as
+//   (1 << 63) | site << 40 | (index mod 2^40),
+// which gmmsp_bounds_status reads.  Without the flag GMMSP_IN_BOUNDS is the
+// constant true and the checks compile away.
+enum : unsigned {  // the sites, as numbered in include/gmmsp.h
+  BND_GP = GMMSP_BND_GP,
+  BND_PIXEL_X = GMMSP_BND_PIXEL_X,
+  BND_PIXEL_Y = GMMSP_BND_PIXEL_Y,
+  BND_PARTIAL_W = GMMSP_BND_PARTIAL_W,
+  BND_PARTIAL_R = GMMSP_BND_PARTIAL_R,
+  BND_THETA = GMMSP_BND_THETA,
+  BND_LABEL = GMMSP_BND_LABEL,
+  BND_LABEL_K = GMMSP_BND_LABEL_K,
+  BND_CELL_LL = GMMSP_BND_CELL_LL,
+  BND_IMAGE = GMMSP_BND_IMAGE,
+  BND_ITEM = GMMSP_BND_ITEM,
+};
+__host__ __device__ constexpr unsigned long long bounds_code(unsigned site, long long i) {
+  return (1ull << 63) | (static_cast<unsigned long long>(site) << 40) |
+         (static_cast<unsigned long long>(i) & ((1ull << 40) - 1));
+}
+#ifdef GMMSP_CHECK_BOUNDS
+static __device__ unsigned long long g_bounds_word = 0ull;  // one per translation unit
+__device__ __forceinline__ bool bounds_ok(long long i, long long n, unsigned site) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&g_bounds_word, 0ull, bounds_code(site, i));
+  return false;
+}
+#define GMMSP_IN_BOUNDS(i, n, site) ::gmmsp::bounds_ok((long long)(i), (long long)(n), (site))
+#else
+#define GMMSP_IN_BOUNDS(i, n, site) true
+#endif
+// Reads and clears the status words of the translation units with checked
+// kernels (0 when nothing was recorded or the build is unchecked).
+cudaError_t bounds_take_em(unsigned long long* word);
+cudaError_t bounds_take_prep(unsigned long long* word);
 
 // Programmatic dependent launch (off unless GMMSP_PDL=1: measured slower on
 // this pipeline of short dependent kernels).  When on, the single-image

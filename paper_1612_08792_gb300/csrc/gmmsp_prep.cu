@@ -125,9 +125,11 @@ __global__ void __launch_bounds__(256) k_lab32(const float* __restrict__ img, lo
 template <class Src>
 __device__ __forceinline__ void init_k(const Src& lab, const Geom& g, double lambda_c,
                                        double* __restrict__ theta, float* __restrict__ gp, int k) {
+  if (!GMMSP_IN_BOUNDS(k, g.K, BND_THETA)) return;
   const int kx = k % g.nx, ky = k / g.nx;
   const int x = kx * g.v + g.v / 2, y = ky * g.v + g.v / 2;
-  const float4 c = lab.load(x, y);
+  float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (GMMSP_IN_BOUNDS(x, g.W, BND_PIXEL_X) && GMMSP_IN_BOUNDS(y, g.H, BND_PIXEL_Y)) c = lab.load(x, y);
   const bool gray = g.cm == kColourGray;
   const double mu[5] = {double(x), double(y), double(c.x), gray ? 0.0 : double(c.y), gray ? 0.0 : double(c.z)};
   const double vv = double(g.v) * double(g.v), ll = lambda_c * lambda_c;
@@ -256,6 +258,18 @@ __device__ __forceinline__ int find_row_image(const BatchImage* __restrict__ img
   return lo;
 }
 
+cudaError_t bounds_take_prep(unsigned long long* word) {
+  *word = 0ull;
+#ifdef GMMSP_CHECK_BOUNDS
+  cudaError_t e = cudaMemcpyFromSymbol(word, g_bounds_word, sizeof(*word));
+  if (e != cudaSuccess) return e;
+  const unsigned long long zero = 0ull;
+  return cudaMemcpyToSymbol(g_bounds_word, &zero, sizeof(zero));
+#else
+  return cudaSuccess;
+#endif
+}
+
 // CIELAB conversion of every image of a batch: one warp per image row, rows
 // of all images taken in turn by the persistent warps.
 __global__ void __launch_bounds__(256) k_prepare_batch(const BatchImage* __restrict__ imgs, int n,
@@ -295,6 +309,7 @@ __global__ void __launch_bounds__(256) k_prepare_batch(const BatchImage* __restr
         bad += !(isfinite(L) && isfinite(a) && isfinite(b));
       }
       const long long q = (long long)y * W + x;
+      if (!GMMSP_IN_BOUNDS(q, N, BND_PIXEL_Y)) continue;
       P[q] = L;
       if (!l_only) { P[N + q] = a; P[2 * N + q] = b; }
     }
@@ -313,6 +328,7 @@ __global__ void __launch_bounds__(128) k_init_batch(const BatchImage* __restrict
       if (imgs[mid].k_off <= kg) lo = mid; else hi = mid;
     }
     const BatchImage& im = imgs[lo];
+    if (!GMMSP_IN_BOUNDS(kg - im.k_off, im.g.K, BND_ITEM)) continue;
     const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
     init_k<LabPlanar>(src, im.g, lambda_c, theta + (long long)im.k_off * kTheta,
                       gp + (long long)im.k_off * kGP, kg - im.k_off);

@@ -103,3 +103,14 @@ def test_network_host_checks(lib):
     assert lib.gmmsp_net_check(None) == 1
     assert lib.gmmsp_batch_set_init_net(None, None) == 1
     assert lib.gmmsp_init_from_net(None, None) == 1
+
+
+def test_bounds_status_of_the_ordinary_build(lib):
+    """The ordinary library has the checks compiled out and says so without touching a device;
+    the status word decodes as (1 << 63) | site << 40 | (index mod 2^40)."""
+    import paper_1612_08792_gb300 as gm
+    assert gm.gmmsp_bounds_status() == (False, None)
+    code = (1 << 63) | (5 << 40) | 1234
+    assert gm.bounds_decode(code) == {"site": "partial_read", "index": 1234}
+    assert gm.bounds_decode((1 << 63) | (2 << 40) | ((-3) & ((1 << 40) - 1))) == {"site": "pixel_x", "index": -3}
+    assert gm.bounds_decode(0) is None
