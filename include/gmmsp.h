@@ -299,7 +299,8 @@ void gmmsp_batch_destroy(gmmsp_batch b);
  * build(checked=True): _build/libgmmsp_checked.so) tests the index of every
  * global-memory access of the EM kernels against its buffer -- candidate
  * coefficients, pixel reads, per-cell partial sums, superpixel parameters,
- * labels and their values, the batch table lookups -- skips an access that
+ * labels and their values, the batch table lookups, the CIELAB writes of the
+ * learned start's converting first kernel -- skips an access that
  * falls outside and records the first such event of each kernel translation
  * unit.  The ordinary build compiles the checks away.
  *   checked          receives 1 if this library was built with the checks,

@@ -569,7 +569,7 @@ gmmsp_status gmmsp_init_from_net(gmmsp_ctx c, gmmsp_net n) {
     c->err = why;  // the network's failure: the context stays usable
     return st;
   }
-  GM_CHECK(c, gmmsp::net_enqueue_init(n, c->lab, 1, c->g, c->p.lambda_c, c->p.eps_s, c->p.eps_c, c->theta, c->gp,
+  GM_CHECK(c, gmmsp::net_enqueue_init(n, c->lab, nullptr, 1, c->g, c->p.lambda_c, c->p.eps_s, c->p.eps_c, c->theta, c->gp,
                                       c->counters, c->stream));
   return GMMSP_OK;
 }
@@ -657,10 +657,11 @@ gmmsp_status gmmsp_bounds_status(int* checked, unsigned long long* first_violati
 #ifdef GMMSP_CHECK_BOUNDS
   if (checked) *checked = 1;
   if (cudaDeviceSynchronize() != cudaSuccess) return GMMSP_E_CUDA;
-  unsigned long long w[2] = {0ull, 0ull};
-  if (gmmsp::bounds_take_em(&w[0]) != cudaSuccess || gmmsp::bounds_take_prep(&w[1]) != cudaSuccess)
+  unsigned long long w[3] = {0ull, 0ull, 0ull};
+  if (gmmsp::bounds_take_em(&w[0]) != cudaSuccess || gmmsp::bounds_take_prep(&w[1]) != cudaSuccess ||
+      gmmsp::bounds_take_cnn(&w[2]) != cudaSuccess)
     return GMMSP_E_CUDA;
-  if (first_violation) *first_violation = w[0] ? w[0] : w[1];
+  if (first_violation) *first_violation = w[0] ? w[0] : (w[1] ? w[1] : w[2]);
 #else
   if (checked) *checked = 0;
   if (first_violation) *first_violation = 0ull;

@@ -124,11 +124,17 @@ gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
   const int n = b->n;
   GB_CHECK(b, cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * gmmsp::CNT_N, s));
   const int prep_blocks = int(std::min<long long>((b->total_rows + 7) / 8, (long long)b->sm_count * 8));
-  GB_CHECK(b, gmmsp::launch_prepare_batch(b->table, n, b->total_rows, b->p.input_format, b->lab, b->counters,
-                                          prep_blocks, s));
+  // With the network on RGB8 input, its first kernel converts the cells'
+  // pixels (it reads them anyway) and the conversion pass only the rest.
+  const bool fused = b->net && b->p.input_format == GMMSP_RGB8 && b->p.colour_model == GMMSP_COLOUR_FULL;
+  if (fused)
+    GB_CHECK(b, gmmsp::launch_prepare_rest(b->table, n, b->host[0].g, b->lab, b->sm_count, s));
+  else
+    GB_CHECK(b, gmmsp::launch_prepare_batch(b->table, n, b->total_rows, b->p.input_format, b->lab,
+                                            b->counters, prep_blocks, s));
   if (b->net) {
-    GB_CHECK(b, gmmsp::net_enqueue_init(b->net, b->lab, n, b->host[0].g, b->p.lambda_c, b->p.eps_s, b->p.eps_c,
-                                        b->theta, b->gp, b->counters, s));
+    GB_CHECK(b, gmmsp::net_enqueue_init(b->net, b->lab, fused ? b->table : nullptr, n, b->host[0].g,
+                                        b->p.lambda_c, b->p.eps_s, b->p.eps_c, b->theta, b->gp, b->counters, s));
   } else {
     const int kblocks = int(std::min<long long>((b->total_k + 127) / 128, (long long)b->sm_count * 8));
     GB_CHECK(b, gmmsp::launch_init_batch(b->table, n, b->total_k, b->lab, b->p.lambda_c, b->theta, b->gp,

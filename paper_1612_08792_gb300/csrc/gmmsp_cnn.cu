@@ -36,6 +36,7 @@
 #include "../../include/gmmsp_cnn.h"
 #include "gmmsp_cnn_internal.cuh"
 #include "gmmsp_internal.cuh"
+#include "gmmsp_lab.cuh"
 #include "gmmsp_math.cuh"
 #include "gmmsp_tc.cuh"
 
@@ -349,6 +350,13 @@ __global__ void __launch_bounds__(128) k_gemm(Layer L, int rows, int kdim, int c
 // ------------------------------------------------------------------ k_pix
 struct PixArgs {
   const float* lab;  // B images, each three planes of W H floats (L, a, b), consecutive
+  // Converting mode (rgb non-null): the cells' pixels are read as sRGB from
+  // the batch table's RGB8 rows and their CIELAB values written to lab_out
+  // (planes as `lab`) on the way; `lab` is then unused.
+  const BatchImage* rgb;
+  float* lab_out;
+  const float* srgb;  // 256 decoded sRGB code values (k_srgb_table)
+  Rgb2LabConst k;
   int W, H, v, f, nx, ny;
   int cells;         // B n_x n_y
   int cpb;           // cells per block: floor(128 / f^2)
@@ -369,9 +377,14 @@ struct PixArgs {
 // MMAs run; the pooling buffer (128 x 33 floats) reuses the same bytes once
 // the second MMA has completed.  Both layers accumulate into the same 32 TMEM
 // columns (the second MMA is issued after every thread has read the first
-// result).
+// result).  In the converting mode each thread converts its patch's 9 pixels
+// in registers (its inputs) and stores their CIELAB values to the planes.
 constexpr int kPixMinBlocks = 8;
 constexpr int kPixSmem = 128 * (kC + 1) * 4;  // >= 8192 + 4096
+
+// The sRGB decoding table of the converting mode, once per network (the
+// conversion kernels' own table code, so that both give the same bits).
+__global__ void k_srgb_table(float* lin) { build_srgb_table(lin); }
 
 __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
   __shared__ __align__(1024) unsigned char smem[kPixSmem];
@@ -386,12 +399,6 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
     tc::tmem_relinquish();
   }
   if (tid == 0) tc::mbar_init(&mbar, 1);
-  if (tid < 64) {
-    const uint4* src = reinterpret_cast<const uint4*>((tid < 32 ? a.w1 : a.w2) + (tid & 31) * kC);
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      *reinterpret_cast<uint4*>(sW[tid >> 5] + tc::tile_offset(tid & 31, 8 * j, kC)) = __ldg(src + j);
-  }
   const int ff = a.f * a.f;
   const int lc = tid / ff, q = tid - lc * ff;
   const long long cell = (long long)blockIdx.x * a.cpb + lc;
@@ -402,16 +409,62 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
   const int qs = (a.v / 2) / 3, ds = (a.v / 2) % 3;
   const bool start_row = valid && q == qs * a.f + qs;
   float zs[3] = {0.f, 0.f, 0.f};
+  __shared__ float lin[256];  // converting mode: the sRGB table
+  if (a.rgb) {
+    lin[tid] = __ldg(a.srgb + tid);
+    lin[tid + 128] = __ldg(a.srgb + tid + 128);
+  }
   {
     float in[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) in[i] = 0.f;
-    if (valid) {
-      const int K = a.nx * a.ny;
-      const int img = int(cell / K), k = int(cell - (long long)img * K);
-      const int ky = k / a.nx, kx = k - ky * a.nx;
-      const int qy = q / a.f, qx = q - qy * a.f;
-      const int px0 = kx * a.v + 3 * qx, py0 = ky * a.v + 3 * qy;
+    const int K = a.nx * a.ny;
+    const int img = valid ? int(cell / K) : 0, k = valid ? int(cell - (long long)img * K) : 0;
+    const int ky = k / a.nx, kx = k - ky * a.nx;
+    const int qy = q / a.f, qx = q - qy * a.f;
+    const int px0 = kx * a.v + 3 * qx, py0 = ky * a.v + 3 * qy;
+    if (a.rgb) {
+      // all 27 code values first (independent loads), then the table, then
+      // the conversion; each pixel's CIELAB values are stored from registers
+      uint8_t code[27];
+      const BatchImage* im = a.rgb + img;
+      long long pitch = 0;
+      if (valid) {
+        pitch = im->pitch;
+        const uint8_t* S = static_cast<const uint8_t*>(im->image) + (long long)py0 * pitch + 3LL * px0;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int j = 0; j < 9; ++j) code[dy * 9 + j] = __ldg(S + dy * pitch + j);
+      }
+      __syncthreads();  // the table
+      const long long N = (long long)a.W * a.H;
+      const long long p0 = (long long)py0 * a.W + px0;
+      float* T = a.lab_out + 3 * (valid ? im->pix_off : 0) + p0;
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          if (!valid) continue;
+          const int c = (dy * 3 + dx) * 3;
+          float L, A, B;
+          srgb8_to_lab(a.k, lin, code + c, L, A, B);
+          float* t = T + (long long)dy * a.W + dx;
+          if (GMMSP_IN_BOUNDS((t - a.lab_out) + 2 * N, (long long)(a.cells / K) * 3 * N, BND_PIXEL_Y)) {
+            t[0] = L;
+            t[N] = A;
+            t[2 * N] = B;
+          }
+          in[c + 0] = fmaf(L, kInScale, -1.f);
+          in[c + 1] = A * kInScale;
+          in[c + 2] = B * kInScale;
+          if (start_row && dy == ds && dx == ds) {
+            zs[0] = in[c + 0];
+            zs[1] = in[c + 1];
+            zs[2] = in[c + 2];
+          }
+        }
+    } else if (valid) {
       const long long N = (long long)a.W * a.H;
       const float* P = a.lab + (long long)img * 3 * N;
 #pragma unroll
@@ -432,7 +485,12 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) u[i] = pack2(in[2 * i], in[2 * i + 1]);
-
+  }
+  if (tid < 64) {
+    const uint4* src = reinterpret_cast<const uint4*>((tid < 32 ? a.w1 : a.w2) + (tid & 31) * kC);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      *reinterpret_cast<uint4*>(sW[tid >> 5] + tc::tile_offset(tid & 31, 8 * j, kC)) = __ldg(src + j);
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -717,9 +775,24 @@ int grid_for(long long n, int block) {
 }
 
 }  // namespace cnn
+
+cudaError_t bounds_take_cnn(unsigned long long* word) {
+  *word = 0ull;
+#ifdef GMMSP_CHECK_BOUNDS
+  cudaError_t e = cudaMemcpyFromSymbol(word, g_bounds_word, sizeof(*word));
+  if (e != cudaSuccess) return e;
+  const unsigned long long zero = 0ull;
+  return cudaMemcpyToSymbol(g_bounds_word, &zero, sizeof(zero));
+#else
+  return cudaSuccess;
+#endif
+}
+
 }  // namespace gmmsp
 
+using gmmsp::BatchImage;
 using gmmsp::Geom;
+using gmmsp::rgb2lab_const;
 using namespace gmmsp::cnn;
 
 // --------------------------------------------------------------- the object
@@ -731,6 +804,7 @@ struct gmmsp_net_s {
   float *w32 = nullptr, *m = nullptr, *vv = nullptr, *grad = nullptr;
   __nv_bfloat16* wbf = nullptr;
   int* err = nullptr;
+  float* srgb = nullptr;  // the converting mode's sRGB table
   long long adam_t = 0;
   // workspace (grown on demand, never during stream capture)
   void* wslab = nullptr;
@@ -854,12 +928,18 @@ Layer cell_layer(gmmsp_net n, int B, const Geom& g, int l) {
 }
 
 // Forward pass; out receives [B K][16] FP32.  Training also stores x0, h1, h2.
+// With rgb non-null the first kernel reads the cells' pixels as RGB8 through
+// the batch table and writes their CIELAB values to lab_out.
 gmmsp_status enqueue_forward(gmmsp_net n, const float* lab, int B, const Geom& g, float* out, bool train,
-                             cudaStream_t s) {
+                             cudaStream_t s, const BatchImage* rgb = nullptr, float* lab_out = nullptr) {
   const long long cells = (long long)B * g.K;
   n->last_cells = cells;
   PixArgs a{};
   a.lab = lab;
+  a.rgb = rgb;
+  a.lab_out = lab_out;
+  a.srgb = n->srgb;
+  if (rgb) a.k = rgb2lab_const();
   a.W = g.W; a.H = g.H; a.v = g.v; a.f = n->f; a.nx = g.nx; a.ny = g.ny;
   a.cells = int(cells);
   a.cpb = n->cpb;
@@ -1000,11 +1080,12 @@ gmmsp_status net_reserve(gmmsp_net n, int B, const Geom& g, std::string* why) {
 
 long long net_generation(gmmsp_net n) { return n ? n->generation : -1; }
 
-cudaError_t net_enqueue_init(gmmsp_net n, const float* lab, int B, const Geom& g, double lambda_c, double eps_s,
-                             double eps_c, double* theta, float* gp, unsigned long long* counters,
-                             cudaStream_t s) {
+cudaError_t net_enqueue_init(gmmsp_net n, float* lab, const BatchImage* rgb, int B, const Geom& g,
+                             double lambda_c, double eps_s, double eps_c, double* theta, float* gp,
+                             unsigned long long* counters, cudaStream_t s) {
   if ((long long)B * g.K > n->cap_cells) return cudaErrorInvalidValue;
-  if (enqueue_forward(n, lab, B, g, n->out, false, s) != GMMSP_OK) return cudaErrorLaunchFailure;
+  if (enqueue_forward(n, lab, B, g, n->out, false, s, rgb, rgb ? lab : nullptr) != GMMSP_OK)
+    return cudaErrorLaunchFailure;
   return launch_init_from_outputs(n->out, kOut, n->out + 5, kOut, lab, B, g, lambda_c, eps_s, eps_c, theta, gp,
                                   counters, s);
 }
@@ -1051,6 +1132,7 @@ gmmsp_status gmmsp_net_create(gmmsp_net* out, int spacing, void* stream) {
   const size_t o_g = off; off += up256(np * 4);
   const size_t o_b = off; off += up256(np * 2);
   const size_t o_e = off; off += 256;
+  const size_t o_t = off; off += 256 * 4;
   const char* inj = getenv("GMMSP_FAIL_ALLOC");
   cudaError_t e = (inj && inj[0] == '1') ? cudaErrorMemoryAllocation : cudaMalloc(&n->pslab, off);
   if (e != cudaSuccess) {
@@ -1065,7 +1147,12 @@ gmmsp_status gmmsp_net_create(gmmsp_net* out, int spacing, void* stream) {
   n->grad = reinterpret_cast<float*>(b + o_g);
   n->wbf = reinterpret_cast<__nv_bfloat16*>(b + o_b);
   n->err = reinterpret_cast<int*>(b + o_e);
+  n->srgb = reinterpret_cast<float*>(b + o_t);
   e = cudaMemsetAsync(n->pslab, 0, off, n->stream);
+  if (e == cudaSuccess) {
+    k_srgb_table<<<1, 256, 0, n->stream>>>(n->srgb);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
   if (e != cudaSuccess) {
     cudaFree(n->pslab);

@@ -23,9 +23,14 @@ long long net_generation(gmmsp_net n);
 // Enqueues the network on B CIELAB images (planes of W H floats, image after
 // image) and writes theta_0 and the packed coefficients of all B K
 // superpixels.  A non-finite theta_0 counts into counters[CNT_NONFINITE].
-cudaError_t net_enqueue_init(gmmsp_net n, const float* lab, int B, const Geom& g, double lambda_c, double eps_s,
-                             double eps_c, double* theta, float* gp, unsigned long long* counters,
-                             cudaStream_t s);
+// With rgb non-null (a device batch table of B RGB8 images, all of geometry
+// g, CIELAB planes at lab + 3 pix_off) the network's first kernel also does
+// the sRGB -> CIELAB conversion of every pixel inside the n_x v x n_y v
+// cell region and writes it to lab; the pixels outside it are left to the
+// caller (launch_prepare_batch with skip_cells).
+cudaError_t net_enqueue_init(gmmsp_net n, float* lab, const BatchImage* rgb, int B, const Geom& g,
+                             double lambda_c, double eps_s, double eps_c, double* theta, float* gp,
+                             unsigned long long* counters, cudaStream_t s);
 
 // theta_0 and the packed coefficients of B K superpixels from the network's
 // output parametrisation given as two device arrays: superpixel i's 5 mean

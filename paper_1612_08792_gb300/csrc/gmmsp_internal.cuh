@@ -158,6 +158,7 @@ __device__ __forceinline__ bool bounds_ok(long long i, long long n, unsigned sit
 // kernels (0 when nothing was recorded or the build is unchecked).
 cudaError_t bounds_take_em(unsigned long long* word);
 cudaError_t bounds_take_prep(unsigned long long* word);
+cudaError_t bounds_take_cnn(unsigned long long* word);
 
 // Programmatic dependent launch (off unless GMMSP_PDL=1: measured slower on
 // this pipeline of short dependent kernels).  When on, the single-image
@@ -239,6 +240,11 @@ cudaError_t launch_pack_theta(const Geom& g, double* theta, float* gp, int* bad,
 // Grayscale model (the images' g.cm): plane L only, as launch_rgb2lab.
 cudaError_t launch_prepare_batch(const BatchImage* imgs, int n, long long total_rows, int input_format,
                                  float* lab, unsigned long long* counters, int blocks, cudaStream_t s);
+// RGB8 input, full colour model, n images of geometry g: the pixels outside
+// the n_x v x n_y v cell region only (the network's converting first kernel
+// writes the others).
+cudaError_t launch_prepare_rest(const BatchImage* imgs, int n, const Geom& g, float* lab, int sm_count,
+                                cudaStream_t s);
 cudaError_t launch_init_batch(const BatchImage* imgs, int n, int total_k, const float* lab,
                               double lambda_c, double* theta, float* gp, int blocks, cudaStream_t s);
 // minb >= 6: the non-persistent variant (one cell per warp, registers capped

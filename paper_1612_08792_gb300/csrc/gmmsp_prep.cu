@@ -20,37 +20,13 @@
 //    parameters supplied by the caller (resume / external initialisation).
 #include <math.h>
 
+#include <algorithm>
+
 #include "gmmsp_internal.cuh"
+#include "gmmsp_lab.cuh"
 #include "gmmsp_math.cuh"
 
 namespace gmmsp {
-
-struct Rgb2LabConst {
-  float m[9];         // linear sRGB -> XYZ, row major
-  float inv_white[3]; // 1 / (Xn, Yn, Zn)
-};
-
-__device__ __forceinline__ float cielab_f(float t) {
-  // CIE 1976: cube root above (6/29)^3, the linear segment below.  The cube
-  // root is taken as 2^(log2(t) / 3) on the special-function unit
-  // (lg2.approx, ex2.approx; t is a normal number there): relative error
-  // about 3e-7, i.e. under 3e-4 in L*, a*, b*, at two instructions instead
-  // of a full-precision cbrtf, three times per pixel.
-  const float d3 = 216.f / 24389.f;             // (6/29)^3
-  const float slope = 841.f / 108.f;            // 1 / (3 (6/29)^2)
-  float lg, cr;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(t));
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(cr) : "f"(lg * (1.f / 3.f)));
-  return t > d3 ? cr : fmaf(slope, t, 4.f / 29.f);
-}
-
-// sRGB decoding of the 256 code values (the transfer curve of IEC 61966-2-1).
-__device__ __forceinline__ void build_srgb_table(float* lin) {
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-    const float c = float(i) * (1.f / 255.f);
-    lin[i] = c <= 0.04045f ? c * (1.f / 12.92f) : powf((c + 0.055f) * (1.f / 1.055f), 2.4f);
-  }
-}
 
 __global__ void __launch_bounds__(256) k_rgb2lab(const uint8_t* __restrict__ img, long long pitch,
                                                  int W, int H, float* __restrict__ lab,
@@ -64,17 +40,12 @@ __global__ void __launch_bounds__(256) k_rgb2lab(const uint8_t* __restrict__ img
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
        idx += (long long)gridDim.x * blockDim.x) {
     const int y = int(idx / W), x = int(idx - (long long)y * W);
-    const uint8_t* p = img + (long long)y * pitch + 3LL * x;
-    const float r = lin[p[0]], g = lin[p[1]], b = lin[p[2]];
-    const float* m = k.m;
-    const float X = fmaf(m[0], r, fmaf(m[1], g, m[2] * b)) * k.inv_white[0];
-    const float Y = fmaf(m[3], r, fmaf(m[4], g, m[5] * b)) * k.inv_white[1];
-    const float Z = fmaf(m[6], r, fmaf(m[7], g, m[8] * b)) * k.inv_white[2];
-    const float fx = cielab_f(X), fy = cielab_f(Y), fz = cielab_f(Z);
-    lab[idx] = 116.f * fy - 16.f;
+    float L, A, B;
+    srgb8_to_lab(k, lin, img + (long long)y * pitch + 3LL * x, L, A, B);
+    lab[idx] = L;
     if (!l_only) {
-      lab[N + idx] = 500.f * (fx - fy);
-      lab[2 * N + idx] = 200.f * (fy - fz);
+      lab[N + idx] = A;
+      lab[2 * N + idx] = B;
     }
   }
 }
@@ -206,6 +177,11 @@ static Rgb2LabConst make_rgb2lab_const() {
   return k;
 }
 
+Rgb2LabConst rgb2lab_const() {
+  static const Rgb2LabConst k = make_rgb2lab_const();
+  return k;
+}
+
 cudaError_t launch_rgb2lab(const uint8_t* img, long long pitch, const Geom& g, float* lab,
                            unsigned long long* counters, cudaStream_t s) {
   (void)counters;
@@ -294,14 +270,7 @@ __global__ void __launch_bounds__(256) k_prepare_batch(const BatchImage* __restr
       if (input_format == 2) {  // grey levels
         L = 116.f * cielab_f(lin[reinterpret_cast<const uint8_t*>(src)[x]]) - 16.f;
       } else if (input_format == 0) {
-        const uint8_t* p = reinterpret_cast<const uint8_t*>(src) + 3LL * x;
-        const float r = lin[p[0]], g = lin[p[1]], bl = lin[p[2]];
-        const float* m = k.m;
-        const float X = fmaf(m[0], r, fmaf(m[1], g, m[2] * bl)) * k.inv_white[0];
-        const float Y = fmaf(m[3], r, fmaf(m[4], g, m[5] * bl)) * k.inv_white[1];
-        const float Z = fmaf(m[6], r, fmaf(m[7], g, m[8] * bl)) * k.inv_white[2];
-        const float fx = cielab_f(X), fy = cielab_f(Y), fz = cielab_f(Z);
-        L = 116.f * fy - 16.f; a = 500.f * (fx - fy); b = 200.f * (fy - fz);
+        srgb8_to_lab(k, lin, reinterpret_cast<const uint8_t*>(src) + 3LL * x, L, a, b);
       } else {
         const float* p = reinterpret_cast<const float*>(src) + 3LL * x;
         L = p[0];
@@ -316,6 +285,43 @@ __global__ void __launch_bounds__(256) k_prepare_batch(const BatchImage* __restr
   }
   bad = __reduce_add_sync(0xffffffffu, bad);
   if (lane == 0 && bad) atomicAdd(&counters[CNT_NONFINITE], (unsigned long long)bad);
+}
+
+// sRGB -> CIELAB of the pixels outside the n_x v x n_y v cell region of n
+// images of one geometry g (the right strip x >= n_x v, y < n_y v, then the
+// bottom strip y >= n_y v), each thread taking pixels in turn.
+__global__ void __launch_bounds__(256) k_prepare_rest(const BatchImage* __restrict__ imgs, int n, Geom g,
+                                                      float* __restrict__ lab, Rgb2LabConst k) {
+  __shared__ float lin[256];
+  build_srgb_table(lin);
+  __syncthreads();
+  const int cx = g.nx * g.v, cy = g.ny * g.v;
+  const long long right = (long long)(g.W - cx) * cy;
+  const long long per = right + (long long)g.W * (g.H - cy);
+  const long long N = (long long)g.W * g.H;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < per * n;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int img = int(r / per);
+    const long long q = r - (long long)img * per;
+    int x, y;
+    if (q < right) {
+      y = int(q / (g.W - cx));
+      x = cx + int(q - (long long)y * (g.W - cx));
+    } else {
+      const long long t = q - right;
+      y = cy + int(t / g.W);
+      x = int(t - (long long)(y - cy) * g.W);
+    }
+    const BatchImage& im = imgs[img];
+    const long long i = (long long)y * g.W + x;
+    if (!GMMSP_IN_BOUNDS(i, N, BND_PIXEL_Y)) continue;
+    float L, A, B;
+    srgb8_to_lab(k, lin, static_cast<const uint8_t*>(im.image) + (long long)y * im.pitch + 3LL * x, L, A, B);
+    float* P = lab + 3 * im.pix_off;
+    P[i] = L;
+    P[N + i] = A;
+    P[2 * N + i] = B;
+  }
 }
 
 __global__ void __launch_bounds__(128) k_init_batch(const BatchImage* __restrict__ imgs, int n, int total_k,
@@ -355,6 +361,17 @@ cudaError_t launch_prepare_batch(const BatchImage* imgs, int n, long long total_
                                  float* lab, unsigned long long* counters, int blocks, cudaStream_t s) {
   static const Rgb2LabConst k = make_rgb2lab_const();
   k_prepare_batch<<<blocks, 256, 0, s>>>(imgs, n, int(total_rows), input_format, lab, k, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_rest(const BatchImage* imgs, int n, const Geom& g, float* lab, int sm_count,
+                                cudaStream_t s) {
+  static const Rgb2LabConst k = make_rgb2lab_const();
+  const long long per =
+      (long long)(g.W - g.nx * g.v) * (g.ny * g.v) + (long long)g.W * (g.H - g.ny * g.v);
+  if (per * n == 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((per * n + 255) / 256, (long long)sm_count * 4);
+  k_prepare_rest<<<unsigned(blocks), 256, 0, s>>>(imgs, n, g, lab, k);
   return cudaGetLastError();
 }
 
