@@ -371,16 +371,23 @@ struct PixArgs {
 
 // Row r of block b is patch q = r mod f^2 of cell b cpb + r / f^2; the patch
 // covers the pixels (k_x v + 3 (q mod f) + dx, k_y v + 3 (q / f) + dy),
-// dx, dy in {0, 1, 2}; input channel (3 dy + dx) 3 + colour.
+// dx, dy in {0, 1, 2}; input channel (3 dy + dx) 3 + colour.  The inputs are
+// gathered by patch rows: thread t takes patch (q mod f = t mod f, q / f =
+// t / (cpb f)) of the block's cell (t mod (cpb f)) / f, so that a warp's
+// loads run along image rows across the block's cells; the thread writes the
+// patch's row of the A tile.  After the MMAs thread t owns row t.
 //
 // Shared memory: the A tile (8 KB) and both weight tiles (4 KB) while the
-// MMAs run; the pooling buffer (128 x 33 floats) reuses the same bytes once
-// the second MMA has completed.  Both layers accumulate into the same 32 TMEM
-// columns (the second MMA is issued after every thread has read the first
-// result).  In the converting mode each thread converts its patch's 9 pixels
-// in registers (its inputs) and stores their CIELAB values to the planes.
+// MMAs run; the pooling buffer (128 rows of 16 BF16 pairs, 17 words apart)
+// reuses the same bytes once the second MMA has completed.  Both layers
+// accumulate into the same 32 TMEM columns (the second MMA is issued after
+// every thread has read the first result).  In the converting mode each
+// thread converts its patch's 9 pixels in registers (its inputs) and stores
+// their CIELAB values to the planes.
 constexpr int kPixMinBlocks = 8;
-constexpr int kPixSmem = 128 * (kC + 1) * 4;  // >= 8192 + 4096
+constexpr int kPixSmem = 128 * kC * 2 + 2 * kC * kC * 2;  // A + weight tiles (12 KB)
+constexpr int kPoolLd = kC / 2 + 1;                       // words per pooling row
+static_assert(128 * kPoolLd * 4 <= kPixSmem, "pooling buffer");
 
 // The sRGB decoding table of the converting mode, once per network (the
 // conversion kernels' own table code, so that both give the same bits).
@@ -392,7 +399,7 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
   __shared__ uint32_t tmem_sh;
   unsigned char* sA = smem;
   unsigned char (*sW)[kC * kC * 2] = reinterpret_cast<unsigned char (*)[kC * kC * 2]>(smem + 128 * kC * 2);
-  float (*sH)[kC + 1] = reinterpret_cast<float (*)[kC + 1]>(smem);
+  uint32_t (*sH)[kPoolLd] = reinterpret_cast<uint32_t (*)[kPoolLd]>(smem);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
     tc::tmem_alloc(&tmem_sh, 32);
@@ -400,14 +407,21 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
   }
   if (tid == 0) tc::mbar_init(&mbar, 1);
   const int ff = a.f * a.f;
-  const int lc = tid / ff, q = tid - lc * ff;
-  const long long cell = (long long)blockIdx.x * a.cpb + lc;
-  const bool valid = lc < a.cpb && cell < a.cells;
-  const long long grow = (long long)blockIdx.x * 128 + tid;  // row of the training buffers
+  // row tid (after the MMAs)
+  const int lc = tid / ff;
+  const bool valid = lc < a.cpb && (long long)blockIdx.x * a.cpb + lc < a.cells;
+  // the patch this thread gathers (patch-row order) and its row of the A tile
+  const int prow = a.cpb * a.f;                  // patches per patch row of the block
+  const int qy = tid / prow, qr = tid - qy * prow;
+  const int lci = qr / a.f, qx = qr - lci * a.f;
+  const bool pad = qy >= a.f;                    // tid >= cpb f^2: a zero row
+  const int row_in = pad ? tid : lci * ff + qy * a.f + qx;
+  const int cell = blockIdx.x * a.cpb + lci;  // < cells + cpb, an int
+  const bool valid_in = !pad && cell < a.cells;
   uint32_t u[16];
   // the Sec. III-C start pixel (k_x v + v/2, k_y v + v/2) lies in patch (qs, qs) at (ds, ds)
   const int qs = (a.v / 2) / 3, ds = (a.v / 2) % 3;
-  const bool start_row = valid && q == qs * a.f + qs;
+  const bool start_row = valid_in && qy == qs && qx == qs;
   float zs[3] = {0.f, 0.f, 0.f};
   __shared__ float lin[256];  // converting mode: the sRGB table
   if (a.rgb) {
@@ -419,9 +433,8 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) in[i] = 0.f;
     const int K = a.nx * a.ny;
-    const int img = valid ? int(cell / K) : 0, k = valid ? int(cell - (long long)img * K) : 0;
+    const int img = valid_in ? int(cell / K) : 0, k = valid_in ? int(cell - (long long)img * K) : 0;
     const int ky = k / a.nx, kx = k - ky * a.nx;
-    const int qy = q / a.f, qx = q - qy * a.f;
     const int px0 = kx * a.v + 3 * qx, py0 = ky * a.v + 3 * qy;
     if (a.rgb) {
       // all 27 code values first (independent loads), then the table, then
@@ -429,7 +442,7 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
       uint8_t code[27];
       const BatchImage* im = a.rgb + img;
       long long pitch = 0;
-      if (valid) {
+      if (valid_in) {
         pitch = im->pitch;
         const uint8_t* S = static_cast<const uint8_t*>(im->image) + (long long)py0 * pitch + 3LL * px0;
 #pragma unroll
@@ -440,12 +453,12 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
       __syncthreads();  // the table
       const long long N = (long long)a.W * a.H;
       const long long p0 = (long long)py0 * a.W + px0;
-      float* T = a.lab_out + 3 * (valid ? im->pix_off : 0) + p0;
+      float* T = a.lab_out + 3 * (valid_in ? im->pix_off : 0) + p0;
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
-          if (!valid) continue;
+          if (!valid_in) continue;
           const int c = (dy * 3 + dx) * 3;
           float L, A, B;
           srgb8_to_lab(a.k, lin, code + c, L, A, B);
@@ -464,7 +477,7 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
             zs[2] = in[c + 2];
           }
         }
-    } else if (valid) {
+    } else if (valid_in) {
       const long long N = (long long)a.W * a.H;
       const float* P = a.lab + (long long)img * 3 * N;
 #pragma unroll
@@ -495,8 +508,8 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const uint4 v4 = make_uint4(u[4 * j], u[4 * j + 1], u[4 * j + 2], u[4 * j + 3]);
-    *reinterpret_cast<uint4*>(sA + tc::tile_offset(tid, 8 * j, kC)) = v4;
-    if (a.x0) reinterpret_cast<uint4*>(a.x0 + grow * kC)[j] = v4;
+    *reinterpret_cast<uint4*>(sA + tc::tile_offset(row_in, 8 * j, kC)) = v4;
+    if (a.x0) reinterpret_cast<uint4*>(a.x0 + ((long long)blockIdx.x * 128 + row_in) * kC)[j] = v4;
   }
   tc::fence_async_smem();
   tc::fence_before_sync();
@@ -540,7 +553,7 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
     for (int j = 0; j < 4; ++j) {
       const uint4 v4 = make_uint4(u[4 * j], u[4 * j + 1], u[4 * j + 2], u[4 * j + 3]);
       if (layer == 0) *reinterpret_cast<uint4*>(sA + tc::tile_offset(tid, 8 * j, kC)) = v4;
-      if (store) reinterpret_cast<uint4*>(store + grow * kC)[j] = v4;
+      if (store) reinterpret_cast<uint4*>(store + ((long long)blockIdx.x * 128 + tid) * kC)[j] = v4;
     }
     if (layer == 0) {
       tc::fence_async_smem();
@@ -550,22 +563,25 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
     } else {
       __syncthreads();  // every thread is past the tiles before they are overwritten
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        sH[tid][2 * i] = bf_lo(u[i]);
-        sH[tid][2 * i + 1] = bf_hi(u[i]);
-      }
+      for (int i = 0; i < 16; ++i) sH[tid][i] = u[i];
       __syncthreads();
-      for (int idx = tid; idx < a.cpb * kC; idx += 128) {
-        const int l = idx >> 5, ch = idx & 31;
+      // pooling: channel pair (2 cp, 2 cp + 1) of cell l, summed over its f^2 rows in order
+      for (int idx = tid; idx < a.cpb * (kC / 2); idx += 128) {
+        const int l = idx >> 4, cp = idx & 15;
         const long long cl = (long long)blockIdx.x * a.cpb + l;
-        if (cl >= a.cells || ch >= kStartCh) continue;
-        float s = 0.f;
-        for (int p = 0; p < ff; ++p) s += sH[l * ff + p][ch];
-        a.c0[cl * kC + ch] = __float2bfloat16(s / float(ff));
+        if (cl >= a.cells || 2 * cp >= kStartCh) continue;
+        float s0 = 0.f, s1 = 0.f;
+        for (int p = 0; p < ff; ++p) {
+          const uint32_t w = sH[l * ff + p][cp];
+          s0 += bf_lo(w);
+          s1 += bf_hi(w);
+        }
+        a.c0[cl * kC + 2 * cp] = __float2bfloat16(s0 / float(ff));
+        if (2 * cp + 1 < kStartCh) a.c0[cl * kC + 2 * cp + 1] = __float2bfloat16(s1 / float(ff));
       }
       if (start_row) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a.c0[cell * kC + kStartCh + c] = __float2bfloat16(zs[c]);
+        for (int c = 0; c < 3; ++c) a.c0[(long long)cell * kC + kStartCh + c] = __float2bfloat16(zs[c]);
       }
     }
   }
