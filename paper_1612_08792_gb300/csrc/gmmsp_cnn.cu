@@ -439,16 +439,29 @@ __global__ void __launch_bounds__(128, kPixMinBlocks) k_pix(PixArgs a) {
     if (a.rgb) {
       // all 27 code values first (independent loads), then the table, then
       // the conversion; each pixel's CIELAB values are stored from registers
+      // A patch row is 9 consecutive bytes; they are read as the three aligned
+      // 32-bit words that hold them.  The first word holds the row's first
+      // byte and the last word its last, so no word reaches past the page of
+      // a byte of the image (the bytes after the 9th are not used).
       uint8_t code[27];
       const BatchImage* im = a.rgb + img;
-      long long pitch = 0;
       if (valid_in) {
-        pitch = im->pitch;
+        const long long pitch = im->pitch;
         const uint8_t* S = static_cast<const uint8_t*>(im->image) + (long long)py0 * pitch + 3LL * px0;
 #pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
+        for (int dy = 0; dy < 3; ++dy) {
+          const uintptr_t at = reinterpret_cast<uintptr_t>(S + dy * pitch);
+          const uint32_t* w = reinterpret_cast<const uint32_t*>(at & ~uintptr_t(3));
+          const uint32_t sh = uint32_t(at & 3) * 8;
+          const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2);
+          const uint32_t lo = __funnelshift_r(w0, w1, sh), hi = __funnelshift_r(w1, w2, sh);
 #pragma unroll
-          for (int j = 0; j < 9; ++j) code[dy * 9 + j] = __ldg(S + dy * pitch + j);
+          for (int j = 0; j < 4; ++j) {
+            code[dy * 9 + j] = uint8_t(lo >> (8 * j));
+            code[dy * 9 + 4 + j] = uint8_t(hi >> (8 * j));
+          }
+          code[dy * 9 + 8] = uint8_t(w2 >> sh);
+        }
       }
       __syncthreads();  // the table
       const long long N = (long long)a.W * a.H;
