@@ -5,7 +5,8 @@
 // (see gmmsp_internal.cuh), so one warp (or 2 or 4, the autotuned launch
 // shape) takes one cell: it stages the <= 9 candidates' packed parameters in
 // shared memory (read back as warp-wide broadcasts) and walks the cell's
-// pixels 32 at a time:
+// pixels 32 at a time (a cell of 32 b + 1 pixels takes its last pixel first,
+// one candidate per lane, instead of ending in a one-pixel batch):
 //   E:  each lane evaluates log2 p(z; theta_k) of its pixel for the
 //       candidates (Eq. gaussian with the block covariance), forms the
 //       posteriors R_ik (Eq. Rik) with the log-sum-exp held in registers, and
@@ -157,28 +158,77 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
     cy = SHIFT ? -p0.y : float((1 - ms / 3) * g.v);
     if (SHIFT) { mL = p0.z; ma = p0.w; mb = p1.x; }
   }
-  // The colour of this lane's next pixel is loaded one batch ahead.
   auto locate = [&](int p, int& rx, int& ry) {
     ry = __float2int_rz((float(p) + 0.5f) * inv_cw);  // exact floor(p / cw)
     rx = p - ry * c.cw;
   };
+  // the statistics of one (pixel, slot ms) pair with posterior r into acc
+  auto add_stats = [&](float r, float dx, float dy, float dL, float da, float db) {
+    const float rxd = r * dx, ryd = r * dy, rL = r * dL;
+    acc[0] += r;
+    acc[1] += rxd; acc[2] += ryd; acc[3] += rL;
+    acc[6] = fmaf(rxd, dx, acc[6]);
+    acc[7] = fmaf(rxd, dy, acc[7]);
+    acc[8] = fmaf(ryd, dy, acc[8]);
+    acc[9] = fmaf(rL, dL, acc[9]);
+    if constexpr (CM != kColourGray) {
+      const float ra = r * da, rb = r * db;
+      acc[4] += ra; acc[5] += rb;
+      if constexpr (CM == kColourFull) {
+        acc[10] = fmaf(rL, da, acc[10]);
+        acc[11] = fmaf(rL, db, acc[11]);
+      }
+      acc[12] = fmaf(ra, da, acc[12]);
+      acc[13] = fmaf(ra, db, acc[13]);
+      acc[14] = fmaf(rb, db, acc[14]);
+    }
+  };
+  // A cell of 32 b + 1 pixels (v = 15: 225) would end in a batch of one
+  // pixel that costs a full E part.  That pixel (the last) is taken first,
+  // one slot per lane: lane s < 9 evaluates slot s, the log-sum-exp runs
+  // over lanes 0-15 by butterflies (lanes 9-15 hold -inf), and lane s adds
+  // its pair's statistics to its own accumulators (lane s holds slot s's
+  // phase-0 sums).  The batches then cover the other 32 b pixels.
+  int npx_b = npx;
+  if (WPC == 1 && npx > 32 && (npx & 31) == 1) {
+    npx_b = npx - 1;
+    int rx, ry;
+    locate(npx_b, rx, ry);
+    const float4 z = load_pixel<CM>(lab, g, c.x0 + rx, c.y0 + ry);
+    const bool on = lane < kSlots && (FULL || ((c.mask >> lane) & 1u));
+    const float q = on ? log2_density<CM>(sp + 4 * (lane < kSlots ? lane : 0), float(rx), float(ry), z)
+                       : -INFINITY;
+    float m = q;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const float e = on ? ex2_approx(q - m) : 0.f;
+    float sum = e;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) ll += m + lg2_approx(sum);
+    if (on && m_on) {
+      const float r = e * rcp_approx(sum);
+      add_stats(r, float(rx) + cx, float(ry) + cy, z.x - mL, z.y - ma, z.z - mb);
+    }
+  }
+  // The colour of this lane's next pixel is loaded one batch ahead.
   float4 zn = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (wic * 32 + lane < npx) {
+  if (wic * 32 + lane < npx_b) {
     int rx0, ry0;
     locate(wic * 32 + lane, rx0, ry0);
     zn = load_pixel<CM>(lab, g, c.x0 + rx0, c.y0 + ry0);
   }
-  for (int base = wic * 32; base < npx; base += 32 * WPC) {
+  for (int base = wic * 32; base < npx_b; base += 32 * WPC) {
     const int p = base + lane;
     float R[kSlots];
     const float4 z = zn;
-    if (p + 32 * WPC < npx) {
+    if (p + 32 * WPC < npx_b) {
       int rx1, ry1;
       locate(p + 32 * WPC, rx1, ry1);
       zn = load_pixel<CM>(lab, g, c.x0 + rx1, c.y0 + ry1);
     }
     int rx = 0, ry = 0;
-    if (p < npx) {
+    if (p < npx_b) {
       locate(p, rx, ry);
       e_pixel<FULL, CM>(sp, c.mask, float(rx), float(ry), z, R, ll);
     } else {
@@ -198,29 +248,9 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
         const float r = Rw[q * kRStride + ms];
         const float2 xy = XYw[q];
         const float4 zz = Zw[q];
-        const float dx = xy.x + cx, dy = xy.y + cy;
-        const float dL = zz.x - mL;
-        const float rxd = r * dx, ryd = r * dy, rL = r * dL;
-        acc[0] += r;
-        acc[1] += rxd; acc[2] += ryd; acc[3] += rL;
-        acc[6] = fmaf(rxd, dx, acc[6]);
-        acc[7] = fmaf(rxd, dy, acc[7]);
-        acc[8] = fmaf(ryd, dy, acc[8]);
-        acc[9] = fmaf(rL, dL, acc[9]);
-        if constexpr (CM != kColourGray) {
-          const float da = zz.y - ma, db = zz.z - mb;
-          const float ra = r * da, rb = r * db;
-          acc[4] += ra; acc[5] += rb;
-          if constexpr (CM == kColourFull) {
-            acc[10] = fmaf(rL, da, acc[10]);
-            acc[11] = fmaf(rL, db, acc[11]);
-          }
-          acc[12] = fmaf(ra, da, acc[12]);
-          acc[13] = fmaf(ra, db, acc[13]);
-          acc[14] = fmaf(rb, db, acc[14]);
-        }
+        add_stats(r, xy.x + cx, xy.y + cy, zz.x - mL, zz.y - ma, zz.z - mb);
       };
-      const int np = min(32, npx - base);
+      const int np = min(32, npx_b - base);
       if (np == 32) {
         // a full batch: pixels ph, ph + 3, ..., fixed offsets, no loop control
 #pragma unroll
