@@ -402,12 +402,48 @@ template <bool FULL, bool LL, class Src, int CM>
 __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
                                                   const Cell& c, const float4* sp, int lane,
                                                   int32_t* __restrict__ labels, float& ll) {
-  const int npx = c.cw * c.ch;
+  const int npx_all = c.cw * c.ch;
   const float inv_cw = 1.f / float(c.cw);
   auto locate = [&](int p, int& rx, int& ry) {
     ry = __float2int_rz((float(p) + 0.5f) * inv_cw);  // exact floor(p / cw)
     rx = p - ry * c.cw;
   };
+  // start at the cell's first candidate, so that the label is one of the
+  // pixel's candidates (Eq. obtLi) even where no density compares (NaN input)
+  const int first = __ffs(c.mask) - 1;
+  // A cell of 32 b + 1 pixels (v = 15: 225) takes its last pixel first, one
+  // candidate per lane (lane s < 9: slot s): the argmax is the smallest slot
+  // reaching the maximum (butterflies over lanes 0-15), as in the loop below.
+  // The steps then cover 32 b pixels, and a last step of 32 pixels skips its
+  // second pixel per lane.
+  int npx = npx_all;
+  if (npx > 32 && (npx & 31) == 1) {
+    npx = npx_all - 1;
+    int rx, ry;
+    locate(npx, rx, ry);
+    const float4 z = load_pixel<CM>(lab, g, c.x0 + rx, c.y0 + ry);
+    const bool on = lane < kSlots && (FULL || ((c.mask >> lane) & 1u));
+    const float q = on ? log2_density<CM>(sp + 4 * (lane < kSlots ? lane : 0), float(rx), float(ry), z)
+                       : -INFINITY;
+    float m = q;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int best = on && q == m ? lane : 16;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (best == 16) best = first;
+    if (LL) {
+      float sum = on ? ex2_approx(q - m) : 0.f;
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) ll += m + lg2_approx(sum);
+    }
+    if (lane == 0) {
+      const long long at = (long long)(c.y0 + ry) * g.W + (c.x0 + rx);
+      const int kl = (c.cy - 1 + best / 3) * g.nx + (c.cx - 1 + best % 3);
+      if (GMMSP_IN_BOUNDS(at, (long long)g.W * g.H, BND_LABEL) && GMMSP_IN_BOUNDS(kl, g.K, BND_LABEL_K)) labels[at] = kl;
+    }
+  }
   float4 zn[kLabelPPL];
 #pragma unroll
   for (int j = 0; j < kLabelPPL; ++j) {
@@ -419,11 +455,14 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
       zn[j] = load_pixel<CM>(lab, g, c.x0 + rx, c.y0 + ry);
     }
   }
-  for (int p0 = lane; p0 - lane < npx; p0 += 32 * kLabelPPL) {
-    float4 z[kLabelPPL];
-    int rx[kLabelPPL], ry[kLabelPPL];
+  // One step: J pixels per lane (p0, p0 + 32, ...), the colours of the next
+  // step's pixels loaded ahead into zn.
+  auto step = [&](auto jt, int p0) {
+    constexpr int J = decltype(jt)::value;
+    float4 z[J];
+    int rx[J], ry[J];
 #pragma unroll
-    for (int j = 0; j < kLabelPPL; ++j) {
+    for (int j = 0; j < J; ++j) {
       z[j] = zn[j];
       const int pn = p0 + 32 * (j + kLabelPPL);
       if (pn < npx) {
@@ -433,14 +472,11 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
       }
       locate(p0 + 32 * j, rx[j], ry[j]);
     }
-    float e[kLabelPPL][kSlots];
-    float m[kLabelPPL];
-    int best[kLabelPPL];
-    // start at the cell's first candidate, so that the label is one of the
-    // pixel's candidates (Eq. obtLi) even where no density compares (NaN input)
-    const int first = __ffs(c.mask) - 1;
+    float e[J][kSlots];
+    float m[J];
+    int best[J];
 #pragma unroll
-    for (int j = 0; j < kLabelPPL; ++j) {
+    for (int j = 0; j < J; ++j) {
       m[j] = -INFINITY;
       best[j] = first;
     }
@@ -448,17 +484,17 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
     for (int s = 0; s < kSlots; ++s) {
       if (FULL || ((c.mask >> s) & 1u)) {
 #pragma unroll
-        for (int j = 0; j < kLabelPPL; ++j) {
+        for (int j = 0; j < J; ++j) {
           e[j][s] = log2_density<CM>(sp + 4 * s, float(rx[j]), float(ry[j]), z[j]);
           if (e[j][s] > m[j]) { m[j] = e[j][s]; best[j] = s; }
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < kLabelPPL; ++j) e[j][s] = 0.f;
+        for (int j = 0; j < J; ++j) e[j][s] = 0.f;
       }
     }
 #pragma unroll
-    for (int j = 0; j < kLabelPPL; ++j) {
+    for (int j = 0; j < J; ++j) {
       if (p0 + 32 * j >= npx) continue;
       if (LL) {
         float sum = 0.f;
@@ -471,7 +507,11 @@ __device__ __forceinline__ void label_cell_pixels(const Src& lab, const Geom& g,
       const int kl = (c.cy - 1 + best[j] / 3) * g.nx + (c.cx - 1 + best[j] % 3);
       if (GMMSP_IN_BOUNDS(at, (long long)g.W * g.H, BND_LABEL) && GMMSP_IN_BOUNDS(kl, g.K, BND_LABEL_K)) labels[at] = kl;
     }
-  }
+  };
+  // kLabelPPL pixels per lane while more than 32 remain, then one
+  int p0 = lane;
+  for (; p0 - lane + 32 < npx; p0 += 32 * kLabelPPL) step(std::integral_constant<int, kLabelPPL>{}, p0);
+  if (p0 - lane < npx) step(std::integral_constant<int, 1>{}, p0);
 }
 
 // One cell of the label pass, run by one warp.
@@ -512,7 +552,7 @@ __global__ void __launch_bounds__(kEmWarps * 32) k_label_pass(Src lab, Geom g, c
 }
 
 template <int CM>
-__global__ void __launch_bounds__(kEmWarps * 32) k_label_pass_batch(const BatchImage* __restrict__ imgs, int n,
+__global__ void __launch_bounds__(kEmWarps * 32, 5) k_label_pass_batch(const BatchImage* __restrict__ imgs, int n,
                                                                     int total_cells,
                                                                     const float* __restrict__ lab,
                                                                     const float* __restrict__ gp,

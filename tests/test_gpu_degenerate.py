@@ -114,15 +114,19 @@ def test_large_spacing(gm, W, H, v):
     check(got, ref)
 
 
-def test_nan_pixels_keep_labels_in_candidate_sets(gm):
+@pytest.mark.parametrize("v", [8, 15])
+def test_nan_pixels_keep_labels_in_candidate_sets(gm, v):
     """A NaN pixel in a corner cell (no density compares) and one in the remainder corner: every label
     still names one of its pixel's candidates (Eq. Ik, obtLi), on the context and allocation-free paths,
-    and the context path reports the input as GMMSP_E_NUMERIC."""
+    and the context path reports the input as GMMSP_E_NUMERIC.  At v = 15 a corner cell has 225 =
+    7 x 32 + 1 pixels, and its last pixel (14, 14), taken apart from the 32-pixel batches, is NaN too."""
     import torch
-    W, H, v, T = 97, 61, 8, 3                       # remainder strips 1 and 5 pixels wide
+    W, H, T = 97, 61, 3                             # remainder strips 1 and 5 (v = 8), 7 and 1 (v = 15)
     lab = oracle.rgb2lab(voronoi_image(W, H, 12, 8.0, 17)).astype(np.float32)
     lab[0, 0] = np.nan
     lab[H - 1, W - 1, 1] = np.nan
+    if v == 15:
+        lab[14, 14] = np.nan
     g = oracle.grid(W, H, spacing=v)
     cand, _ = oracle.candidates(g)
 
