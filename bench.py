@@ -527,10 +527,8 @@ NET_FLOPS_PER_CELL = 2 * (3 * 288 * 32 + 288 * 16)
 # 96 such images (dram__bytes_read.sum + dram__bytes_write.sum), scaled per image
 # (traffic grows with the image count), per launch variant (blocks per SM); a variant
 # not captured with the current kernel reports null.
-#   6: one-cell-per-warp k_em_pass_batch_flat, 80 registers: 182.08 MB + 27.55 MB;
-#   7: the same capped at 72 registers (some spill):          182.11 MB + 28.41 MB.
-EM_BATCH_TRAFFIC_PER_IMAGE = {6: int((182.081280e6 + 27.553280e6) / 96),
-                              7: int((182.106112e6 + 28.412928e6) / 96)}
+#   7: one-cell-per-warp k_em_pass_batch_flat capped at 72 registers: 182.12 MB + 28.57 MB.
+EM_BATCH_TRAFFIC_PER_IMAGE = {7: int((182.123264e6 + 28.572928e6) / 96)}
 
 
 def measured_peaks():
