@@ -629,7 +629,9 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
 }
 
 // Update of superpixel k from the partial sums of its <= 9 cells (see the
-// header comment); the counters are incremented by the caller.  SHIFT: the
+// header comment).  Adds to the caller's tallies: dead (no weight), rs and rc
+// (eigenvalues raised to the floor, spatial and colour), which a thread that
+// updates several superpixels sums over them.  SHIFT: the
 // mixed-precision path (pair sums rounded to FP64, FP64 arithmetic, moments
 // about the previous mean); otherwise the FP32 variant.
 template <typename PT, bool SHIFT>
@@ -673,7 +675,7 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
   }
   const T Wk = S[ST_W];
   if (!(Wk >= T(1e-8))) {
-    dead = 1;  // reading: a superpixel with no weight keeps theta_k
+    dead += 1;  // reading: a superpixel with no weight keeps theta_k
   } else {
     float* G = gp + (long long)k * kGP;
     const T iw = Num<T>::rcp(Wk);
@@ -705,16 +707,15 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
 #pragma unroll
       for (int j = 2; j < 5; ++j) mu[j] = dl[j];
     }
-    rs = clamp_sym2<T>(cs, T(eps_s));
+    rs += clamp_sym2<T>(cs, T(eps_s));
     if (g.cm == kColourFull) {
-      rc = clamp_sym3<T>(cc, T(eps_c));
+      rc += clamp_sym3<T>(cc, T(eps_c));
     } else {
       // Eq. (BlockSigma1) / grayscale: no L-(a, b) entries; each block floored on its own
       cc[1] = cc[2] = T(0);
-      rc = 0;
       if (!(cc[0] >= T(eps_c))) {
         cc[0] = T(eps_c);
-        rc = 1;
+        rc += 1;
       }
       if (g.cm == kColourSplit) {
         T ab[3] = {cc[3], cc[4], cc[5]};
