@@ -8,7 +8,8 @@ network must see the same inputs: theta_0 from RGB8 input equals theta_0 from
 those CIELAB planes given as float32 input (the unfused path), exactly.
 Cases cover the spacings 3 (128 cells per block), 12, 15 and 33 (one cell
 per block), sizes with remainder strips on both sides and with none, a
-partial last block and row pitches wider than the image.
+partial last block, row pitches wider than the image and images whose
+first byte is not 4-byte aligned.
 """
 import numpy as np
 import pytest
@@ -23,6 +24,7 @@ CASES = [
     (15, 480, 315, 2, 3),
     (3, 64, 37, 2, 0),
     (12, 97, 61, 3, 5),
+    (15, 481, 321, 2, 7),
     (33, 100, 70, 2, 0),
 ]
 
@@ -38,12 +40,15 @@ def gm():
 
 
 def rgb_images(W, H, B, pad, seed):
-    """B RGB8 CUDA tensors of W x H; with pad > 0 each is a view of a wider image (pitch 3 (W + pad))."""
+    """B RGB8 CUDA tensors of W x H; with pad > 0 each is a view of a wider image (pitch 3 (W + pad))
+    that starts pad // 2 columns in, so that its first byte is not 4-byte aligned when pad // 2 is
+    odd (the converting kernel reads the patch rows as aligned words)."""
     import torch
     out = []
     for i in range(B):
         img = voronoi_image(W + pad, H, 40, 8.0, seed + i)
-        out.append(torch.from_numpy(img).cuda()[:, :W])
+        x0 = pad // 2
+        out.append(torch.from_numpy(img).cuda()[:, x0:x0 + W])
     return out
 
 
