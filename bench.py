@@ -710,8 +710,9 @@ def run_learned(args):
     # end to end through the public API: pinned host images in, host labels out.  Two batch
     # contexts (each with its network copy and stream) take alternate steps, so that one
     # step's host copies overlap the other's kernels; every step still copies its own
-    # images in and its labels out.  The serial form (one context, copy - segment - copy)
-    # is reported beside it.
+    # images in and its labels out, each as one copy (the images stacked in one tensor, the
+    # labels in the context's one buffer).  The serial form (one context, copy - segment -
+    # copy) is reported beside it.
     host_imgs = buf.cpu().pin_memory()
     stream2 = torch.cuda.Stream()
     with torch.cuda.stream(stream2):
@@ -722,17 +723,16 @@ def run_learned(args):
         learned2.set_init_net(net2)
     slots = []
     for ctx, st in ((learned, stream), (learned2, stream2)):
-        dev_in = torch.empty_like(buf)
-        slots.append(dict(ctx=ctx, stream=st, dev_in=dev_in, dev_list=[dev_in[i] for i in range(n)],
-                          host_labels=torch.empty((n, H, W), dtype=torch.int32).pin_memory(),
+        slots.append(dict(ctx=ctx, stream=st, dev_in=torch.empty_like(buf),
+                          host_labels=torch.empty(n * H * W, dtype=torch.int32).pin_memory(),
                           done=torch.cuda.Event()))
 
     def e2e_issue(slot):
+        # one copy in (the n images, stacked), the segment, one copy out (the labels buffer)
         with torch.cuda.stream(slot["stream"]):
             slot["dev_in"].copy_(host_imgs, non_blocking=True)
-            labs = slot["ctx"].segment(slot["dev_list"], LEARN_T)
-            for i in range(n):
-                slot["host_labels"][i].copy_(labs[i], non_blocking=True)
+            slot["ctx"].segment_stacked(slot["dev_in"], LEARN_T)
+            slot["host_labels"].copy_(slot["ctx"].labels_buffer, non_blocking=True)
             slot["done"].record(slot["stream"])
 
     def e2e_run(steps, pipelined):
@@ -794,7 +794,8 @@ def run_learned(args):
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": n * N * 3,
                 "d2h_bytes_per_step": n * N * 4,
                 "how": "two batch contexts on two streams take alternate steps (copies of one step overlap "
-                       "the kernels of the other); each step copies its images in and its labels out",
+                       "the kernels of the other); each step copies its images in (one copy of the stacked "
+                       "images) and its labels out (one copy of the context's label buffer)",
                 "serial": round(e2e_serial, 3)},
         "gpu_launches": (1 + 5 + 1 + 2 * LEARN_T + 1) * args.steps,
         "clocks": clocks, "clocks_plain": clocks_p,

@@ -399,6 +399,10 @@ def gmmsp_batch_create(widths, heights, params: gmmsp_params, stream=None):
 
 
 def _ptr_array(tensors):
+    """A C array of device addresses: from tensors (or addresses), or passed through when it is
+    one already (callers that keep their arrays skip rebuilding them on every call)."""
+    if isinstance(tensors, ctypes.Array):
+        return tensors
     return (ctypes.c_void_p * len(tensors))(*[_dptr(t) for t in tensors])
 
 
@@ -739,15 +743,36 @@ class SuperpixelsBatch:
         self.shapes = [(int(h), int(w)) for (h, w) in shapes]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.b = gmmsp_batch_create([w for _, w in self.shapes], [h for h, _ in self.shapes], p, self.stream)
-        self.labels = [torch.empty((h, w), dtype=torch.int32, device="cuda") for h, w in self.shapes]
+        # the labels of all images in one buffer (image after image), one view per image
+        self.labels_buffer = torch.empty(sum(h * w for h, w in self.shapes), dtype=torch.int32, device="cuda")
+        self.labels, off = [], 0
+        for h, w in self.shapes:
+            self.labels.append(self.labels_buffer[off:off + h * w].view(h, w))
+            off += h * w
+        self._label_ptrs = _ptr_array(self.labels)
 
     @staticmethod
     def _pitch(t) -> int:
         return int(t.stride(0) * t.element_size())
 
     def segment(self, images, iters: int = 10, want_loglik: bool = False):
-        ll = gmmsp_batch_segment(self.b, images, [self._pitch(t) for t in images], iters, self.labels,
+        ll = gmmsp_batch_segment(self.b, images, [self._pitch(t) for t in images], iters, self._label_ptrs,
                                  want_loglik)
+        return (self.labels, ll) if want_loglik else self.labels
+
+    def segment_stacked(self, images, iters: int = 10, want_loglik: bool = False):
+        """segment() for a batch of images of one size given as one (n, H, W, C) (or, for
+        grey levels, (n, H, W)) CUDA tensor whose rows are packed (each image's H rows
+        pitch bytes apart): the image addresses are computed from its strides instead of
+        being gathered from n tensors."""
+        n = len(self.shapes)
+        if images.shape[0] != n or any(sh != tuple(images.shape[1:3]) for sh in self.shapes):
+            raise ValueError("segment_stacked wants one (n, H, W[, C]) tensor of the batch's (single) size")
+        es = images.element_size()
+        base = images.data_ptr()
+        ptrs = (ctypes.c_void_p * n)(*[base + i * images.stride(0) * es for i in range(n)])
+        pitches = np.full(n, images.stride(1) * es, dtype=np.int32)
+        ll = gmmsp_batch_segment(self.b, ptrs, pitches, iters, self._label_ptrs, want_loglik)
         return (self.labels, ll) if want_loglik else self.labels
 
     def autotune(self, images, reps: int = 3, cache: str | None = None):
