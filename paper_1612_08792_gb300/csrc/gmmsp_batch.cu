@@ -143,8 +143,10 @@ gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
   const int eb = em_blocks(b);
   const int fblocks = int(std::min<long long>((b->total_k + 31) / 32, (long long)b->sm_count * 16));
   for (int t = 0; t < iters; ++t) {
+    // the first pass follows the start (Sec. III-C or learned): diagonal blocks
     GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, n, b->total_cells, b->lab, b->gp, b->partials,
-                                            b->p.precision, eb, b->blocks_per_sm, b->p.colour_model, s));
+                                            b->p.precision, eb, b->blocks_per_sm, b->p.colour_model, s,
+                                            t == 0));
     GB_CHECK(b, gmmsp::launch_finalize_batch(b->table, n, b->total_k, b->partials, b->theta, b->gp,
                                              b->p.eps_s, b->p.eps_c, b->counters, b->p.precision,
                                              use_fin16(b) ? 0 : fblocks, s));

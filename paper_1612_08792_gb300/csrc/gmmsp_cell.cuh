@@ -64,8 +64,27 @@ __device__ __forceinline__ float4 load_pixel(const Src& s, const Geom& g, int x,
 // quadratic forms, with -1/2 log2(e) Sigma^{-1} folded into the coefficients.
 // fx, fy are the pixel's coordinates relative to the cell origin (the staged
 // mean is relative to the same origin).
-template <int CM>
+// DIAG: both blocks diagonal (the Sec. III-C start and the learned start, whose
+// packed 2xy, 2La, 2Lb and 2ab coefficients are exactly +-0): the same
+// operations without the zero terms, so the same bits, and the normaliser
+// read alone instead of the fourth float4.
+template <int CM, bool DIAG = false>
 __device__ __forceinline__ float log2_density(const float4* P, float fx, float fy, float4 z) {
+  if constexpr (DIAG) {
+    const float4 p0 = P[0], p1 = P[1], p2 = P[2];
+    const float dx = fx - p0.x, dy = fy - p0.y;
+    const float dL = z.x - p0.z;
+    float q = reinterpret_cast<const float*>(P + 3)[2];
+    q = fmaf(p1.y * dx, dx, q);                      // xx dx^2
+    q = fmaf(p1.w * dy, dy, q);                      // yy dy^2
+    q = fmaf(p2.x * dL, dL, q);                      // LL dL^2
+    if constexpr (CM != kColourGray) {
+      const float da = z.y - p0.w, db = z.z - p1.x;
+      q = fmaf(p2.y * da, da, q);                    // aa da^2
+      q = fmaf(p2.z * db, db, q);                    // bb db^2
+    }
+    return q;
+  }
   const float4 p0 = P[0], p1 = P[1], p2 = P[2], p3 = P[3];
   const float dx = fx - p0.x, dy = fy - p0.y;
   const float dL = z.x - p0.z;

@@ -77,7 +77,7 @@ __device__ __forceinline__ void stage_params(const Geom& g, const Cell& c, const
 
 // E part for one pixel: the posteriors of its candidates (Eq. Rik) into
 // R[0..8] (zero for slots off the grid) and ln-sum-exp in log2 units into ll.
-template <bool FULL, int CM>
+template <bool FULL, int CM, bool DIAG = false>
 __device__ __forceinline__ void e_pixel(const float4* sp, unsigned mask, float fx, float fy, float4 z,
                                         float (&R)[kSlots],
                                         float& ll) {
@@ -86,7 +86,7 @@ __device__ __forceinline__ void e_pixel(const float4* sp, unsigned mask, float f
   for (int s = 0; s < kSlots; ++s) {
     R[s] = 0.f;
     if (FULL || ((mask >> s) & 1u)) {
-      R[s] = log2_density<CM>(sp + 4 * s, fx, fy, z);
+      R[s] = log2_density<CM, DIAG>(sp + 4 * s, fx, fy, z);
       m = fmaxf(m, R[s]);
     }
   }
@@ -136,7 +136,7 @@ struct EmSmem {
 template <int WPC>
 constexpr int em_smem_bytes() { return int(sizeof(EmSmem<WPC>)); }
 
-template <bool FULL, bool SHIFT, int WPC, class Src, int CM>
+template <bool FULL, bool SHIFT, int WPC, class Src, int CM, bool DIAG = false>
 __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, const Cell& c,
                                              EmSmem<WPC>& sm, int slot, int warp, int lane, int wic,
                                              float (&acc)[kStats], float& ll) {
@@ -196,7 +196,7 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
     locate(npx_b, rx, ry);
     const float4 z = load_pixel<CM>(lab, g, c.x0 + rx, c.y0 + ry);
     const bool on = lane < kSlots && (FULL || ((c.mask >> lane) & 1u));
-    const float q = on ? log2_density<CM>(sp + 4 * (lane < kSlots ? lane : 0), float(rx), float(ry), z)
+    const float q = on ? log2_density<CM, DIAG>(sp + 4 * (lane < kSlots ? lane : 0), float(rx), float(ry), z)
                        : -INFINITY;
     float m = q;
 #pragma unroll
@@ -230,7 +230,7 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
     int rx = 0, ry = 0;
     if (p < npx_b) {
       locate(p, rx, ry);
-      e_pixel<FULL, CM>(sp, c.mask, float(rx), float(ry), z, R, ll);
+      e_pixel<FULL, CM, DIAG>(sp, c.mask, float(rx), float(ry), z, R, ll);
     } else {
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) R[s] = 0.f;
@@ -267,7 +267,7 @@ __device__ __forceinline__ void em_cell_warp(const Src& lab, const Geom& g, cons
 
 // One cell of the fused pass, run by the WPC warps of cell slot `slot` of the
 // block (all threads of the block call it together when WPC > 1).
-template <typename PT, bool SHIFT, int WPC, class Src, int CM>
+template <typename PT, bool SHIFT, int WPC, class Src, int CM, bool DIAG = false>
 __device__ __forceinline__ void em_cell_block(const Src& lab, const Geom& g, const float* __restrict__ gp,
                                               PT* __restrict__ partials, int cell, bool active,
                                               EmSmem<WPC>& sm, int warp, int lane, int slot, int wic,
@@ -285,9 +285,9 @@ __device__ __forceinline__ void em_cell_block(const Src& lab, const Geom& g, con
   float ll = 0.f;
   if (active) {
     if (c.mask == 0x1ffu)
-      em_cell_warp<true, SHIFT, WPC, Src, CM>(lab, g, c, sm, slot, warp, lane, wic, acc, ll);
+      em_cell_warp<true, SHIFT, WPC, Src, CM, DIAG>(lab, g, c, sm, slot, warp, lane, wic, acc, ll);
     else
-      em_cell_warp<false, SHIFT, WPC, Src, CM>(lab, g, c, sm, slot, warp, lane, wic, acc, ll);
+      em_cell_warp<false, SHIFT, WPC, Src, CM, DIAG>(lab, g, c, sm, slot, warp, lane, wic, acc, ll);
   }
   // Per-warp totals: add the three lanes of each slot, and the lanes' log-likelihoods.
 #pragma unroll
@@ -383,8 +383,9 @@ __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch(const Bat
 // Non-persistent variant: one cell per warp over a grid sized to the work,
 // registers capped so that MINB blocks fit on an SM (6: 80 registers and 8
 // bytes of spill; 7: 72 registers and some spill); the autotuner's choice of
-// 6 or 7 blocks per SM selects it.
-template <typename PT, bool SHIFT, int MINB, int CM>
+// 6 or 7 blocks per SM selects it.  DIAG: every superpixel's blocks are
+// diagonal (the first pass after either start).
+template <typename PT, bool SHIFT, int MINB, int CM, bool DIAG = false>
 __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch_flat(const BatchImage* __restrict__ imgs, int n,
                                                                       int total_cells,
                                                                       const float* __restrict__ lab,
@@ -400,9 +401,9 @@ __global__ void __launch_bounds__(kEmWarps * 32, MINB) k_em_pass_batch_flat(cons
   const BatchImage& im = imgs[ii];
   if (!GMMSP_IN_BOUNDS(cell - im.cell_off, im.g.ncells, BND_ITEM)) return;
   const LabPlanar src{lab + 3 * im.pix_off, (long long)im.g.W * im.g.H, im.g.W};
-  em_cell_block<PT, SHIFT, 1, LabPlanar, CM>(src, im.g, gp + (long long)im.k_off * kGP,
-                                             partials + (long long)im.cell_off * kPartStride, cell - im.cell_off,
-                                             true, sm, warp, lane, warp, 0, lane);
+  em_cell_block<PT, SHIFT, 1, LabPlanar, CM, DIAG>(src, im.g, gp + (long long)im.k_off * kGP,
+                                                   partials + (long long)im.cell_off * kPartStride,
+                                                   cell - im.cell_off, true, sm, warp, lane, warp, 0, lane);
 }
 
 // Label pass: argmax posterior per pixel (ties to the smaller k, i.e. the
@@ -1202,16 +1203,15 @@ namespace gmmsp {
 
 template <int CM>
 static void em_pass_batch_mixed(const BatchImage* imgs, int n, int total_cells, const float* lab, const float* gp,
-                                float* partials, int blocks, int minb, cudaStream_t s) {
+                                float* partials, int blocks, int minb, bool diag, cudaStream_t s) {
   constexpr int smem = em_smem_bytes<1>();
   if (minb >= 6) {  // one cell per warp over a grid sized to the work
     const int nb = (total_cells + kEmWarps - 1) / kEmWarps;
-    if (minb >= 7)
-      k_em_pass_batch_flat<float, true, 7, CM><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                             partials);
-    else
-      k_em_pass_batch_flat<float, true, 6, CM><<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
-                                                                             partials);
+    auto kernel = minb >= 7 ? (diag ? k_em_pass_batch_flat<float, true, 7, CM, true>
+                                    : k_em_pass_batch_flat<float, true, 7, CM, false>)
+                            : (diag ? k_em_pass_batch_flat<float, true, 6, CM, true>
+                                    : k_em_pass_batch_flat<float, true, 6, CM, false>);
+    kernel<<<nb, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp, partials);
   } else {
     k_em_pass_batch<float, true, 5, CM><<<blocks, kEmWarps * 32, smem, s>>>(imgs, n, total_cells, lab, gp,
                                                                           partials);
@@ -1220,7 +1220,7 @@ static void em_pass_batch_mixed(const BatchImage* imgs, int n, int total_cells, 
 
 cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
                                  const float* gp, void* partials, int precision, int blocks, int minb,
-                                 int cm, cudaStream_t s) {
+                                 int cm, cudaStream_t s, bool diag) {
   constexpr int smem = em_smem_bytes<1>();
   if (precision == 1) {  // full colour model only
     if (cm != kColourFull) return cudaErrorInvalidValue;
@@ -1236,9 +1236,9 @@ cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells,
   }
   float* part = static_cast<float*>(partials);
   switch (cm) {
-    case kColourFull: em_pass_batch_mixed<kColourFull>(imgs, n, total_cells, lab, gp, part, blocks, minb, s); break;
-    case kColourSplit: em_pass_batch_mixed<kColourSplit>(imgs, n, total_cells, lab, gp, part, blocks, minb, s); break;
-    case kColourGray: em_pass_batch_mixed<kColourGray>(imgs, n, total_cells, lab, gp, part, blocks, minb, s); break;
+    case kColourFull: em_pass_batch_mixed<kColourFull>(imgs, n, total_cells, lab, gp, part, blocks, minb, diag, s); break;
+    case kColourSplit: em_pass_batch_mixed<kColourSplit>(imgs, n, total_cells, lab, gp, part, blocks, minb, diag, s); break;
+    case kColourGray: em_pass_batch_mixed<kColourGray>(imgs, n, total_cells, lab, gp, part, blocks, minb, diag, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -249,10 +249,12 @@ cudaError_t launch_init_batch(const BatchImage* imgs, int n, int total_k, const 
                               double lambda_c, double* theta, float* gp, int blocks, cudaStream_t s);
 // minb >= 6: the non-persistent variant (one cell per warp, registers capped
 // for 6 blocks per SM; `blocks` is then ignored); otherwise the persistent
-// kernel on `blocks` blocks.
+// kernel on `blocks` blocks.  diag: every superpixel's covariance blocks are
+// diagonal (true after either start, until the first finalize); the mixed-
+// precision one-cell-per-warp kernels then skip the zero terms (same bits).
 cudaError_t launch_em_pass_batch(const BatchImage* imgs, int n, int total_cells, const float* lab,
                                  const float* gp, void* partials, int precision, int blocks, int minb,
-                                 int cm, cudaStream_t s);
+                                 int cm, cudaStream_t s, bool diag = false);
 // blocks == 0 (mixed precision and the full colour model only): 16 lanes per
 // superpixel, one block per 4 superpixels; otherwise one thread per
 // superpixel on `blocks` blocks.
