@@ -521,6 +521,7 @@ LEARN_IMAGES, LEARN_V, LEARN_T, HELD_OUT0 = 256, 15, 2, 1_000_000
 # Algorithmic tensor-core work of the network per 481 x 321 image at spacing 15
 # (32 x 21 cells, 5 x 5 patches each): two 1 x 1 layers per patch (27 -> 32,
 # 32 -> 32) and four 3 x 3 layers per cell (288 -> 32 three times, 288 -> 16).
+E2E_CONTEXTS = 3  # batch contexts taking the end-to-end steps in turn
 NET_FLOPS_PER_PATCH = 2 * (27 * 32 + 32 * 32)
 NET_FLOPS_PER_CELL = 2 * (3 * 288 * 32 + 288 * 16)
 # DRAM bytes per 481 x 321 image of one batched E + M pass, from an ncu capture on
@@ -707,22 +708,25 @@ def run_learned(args):
     instr = units * INSTR_PER_CAND + n * N * INSTR_PER_PIXEL
     achieved_i = instr / (em_ms * 1e-3) / 1e12
 
-    # end to end through the public API: pinned host images in, host labels out.  Two batch
-    # contexts (each with its network copy and stream) take alternate steps, so that one
-    # step's host copies overlap the other's kernels; every step still copies its own
+    # end to end through the public API: pinned host images in, host labels out.
+    # E2E_CONTEXTS batch contexts (each with its network copy and stream) take steps in
+    # turn, so that one step's host copies overlap the others' kernels; every step still copies its own
     # images in and its labels out, each as one copy (the images stacked in one tensor, the
     # labels in the context's one buffer).  The serial form (one context, copy - segment -
     # copy) is reported beside it.
     host_imgs = buf.cpu().pin_memory()
-    stream2 = torch.cuda.Stream()
-    with torch.cuda.stream(stream2):
-        net2 = load_pretrained(LEARN_V, stream=stream2)
-        learned2 = gm.SuperpixelsBatch([(H, W)] * n, spacing=LEARN_V, stream=stream2)
-        t1 = learned.tuning()
-        gm.gmmsp_batch_set_tuning(learned2.b, t1["blocks_per_sm"], t1["finalize16"])
-        learned2.set_init_net(net2)
+    t1 = learned.tuning()
+    extra = []  # (stream, net, context) of the contexts beyond the first
+    for _ in range(E2E_CONTEXTS - 1):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            net_x = load_pretrained(LEARN_V, stream=st)
+            ctx_x = gm.SuperpixelsBatch([(H, W)] * n, spacing=LEARN_V, stream=st)
+            gm.gmmsp_batch_set_tuning(ctx_x.b, t1["blocks_per_sm"], t1["finalize16"])
+            ctx_x.set_init_net(net_x)
+        extra.append((st, net_x, ctx_x))
     slots = []
-    for ctx, st in ((learned, stream), (learned2, stream2)):
+    for ctx, st in [(learned, stream)] + [(c, st) for st, _, c in extra]:
         slots.append(dict(ctx=ctx, stream=st, dev_in=torch.empty_like(buf),
                           host_labels=torch.empty(n * H * W, dtype=torch.int32).pin_memory(),
                           done=torch.cuda.Event()))
@@ -737,7 +741,7 @@ def run_learned(args):
 
     def e2e_run(steps, pipelined):
         for k in range(steps):
-            slot = slots[k % 2] if pipelined else slots[0]
+            slot = slots[k % len(slots)] if pipelined else slots[0]
             slot["done"].synchronize()      # its previous step (labels on the host) is complete
             e2e_issue(slot)
         for slot in slots:
@@ -754,8 +758,9 @@ def run_learned(args):
     t0 = time.perf_counter()
     e2e_run(e2e_steps, False)
     e2e_serial = whole_job_value(world, n * N * e2e_steps, max_over_ranks(time.perf_counter() - t0, world))
-    learned2.close()
-    net2.close()
+    for _, net_x, ctx_x in extra:
+        ctx_x.close()
+        net_x.close()
 
     peaks = measured_peaks()
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
@@ -793,8 +798,8 @@ def run_learned(args):
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else "fallback"},
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": n * N * 3,
                 "d2h_bytes_per_step": n * N * 4,
-                "how": "two batch contexts on two streams take alternate steps (copies of one step overlap "
-                       "the kernels of the other); each step copies its images in (one copy of the stacked "
+                "how": f"{E2E_CONTEXTS} batch contexts on as many streams take steps in turn (copies of one "
+                       "step overlap the kernels of the others); each step copies its images in (one copy of the stacked "
                        "images) and its labels out (one copy of the context's label buffer)",
                 "serial": round(e2e_serial, 3)},
         "gpu_launches": (1 + 5 + 1 + 2 * LEARN_T + 1) * args.steps,
