@@ -232,6 +232,7 @@ gmmsp_status gmmsp_batch_create(gmmsp_batch* out, int n, const int* widths, cons
       return GMMSP_E_INVALID;
     }
   }
+  for (BatchImage& im : b->host) im.uniform = b->uniform ? 1 : 0;
   b->total_pix = pix;
   b->total_rows = int(rows);
   b->total_cells = int(cells);

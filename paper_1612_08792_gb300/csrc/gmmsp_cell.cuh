@@ -41,13 +41,13 @@ __device__ __forceinline__ Cell make_cell(const Geom& g, int cell) {
   c.y0 = c.cy * g.v;
   c.cw = min(g.v, g.W - c.x0);
   c.ch = min(g.v, g.H - c.y0);
-  unsigned m = 0;
-#pragma unroll
-  for (int s = 0; s < kSlots; ++s) {
-    const int kx = c.cx - 1 + s % 3, ky = c.cy - 1 + s / 3;
-    if (kx >= 0 && kx < g.nx && ky >= 0 && ky < g.ny) m |= 1u << s;
-  }
-  c.mask = m;
+  // slot s = 3 r + q is seed (c_x - 1 + q, c_y - 1 + r): the product of a column
+  // mask (q) and a row mask (r) of the seeds on the grid
+  const unsigned cols = (c.cx >= 1 && c.cx - 1 < g.nx ? 1u : 0u) | (c.cx < g.nx ? 2u : 0u) |
+                        (c.cx + 1 < g.nx ? 4u : 0u);
+  const unsigned rows = (c.cy >= 1 && c.cy - 1 < g.ny ? 1u : 0u) | (c.cy < g.ny ? 2u : 0u) |
+                        (c.cy + 1 < g.ny ? 4u : 0u);
+  c.mask = (rows & 1u ? cols : 0u) | (rows & 2u ? cols << 3 : 0u) | (rows & 4u ? cols << 6 : 0u);
   return c;
 }
 
@@ -111,6 +111,10 @@ __device__ __forceinline__ float log2_density(const float4* P, float fx, float f
 // superpixel when which == 1): binary search over the images' prefix offsets.
 __device__ __forceinline__ int find_image(const BatchImage* __restrict__ imgs, int n, int item,
                                           int which /*0 cells, 1 superpixels*/) {
+  if (imgs[0].uniform) {  // images of one geometry: a division
+    const int i = item / (which == 0 ? imgs[0].g.ncells : imgs[0].g.K);
+    return i < n ? i : n - 1;
+  }
   int lo = 0, hi = n;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;

@@ -198,6 +198,7 @@ struct BatchImage {
   int row_off;         // first row of the image in the batch's list of rows
   int cell_off;        // first cell of the image in the batch
   int k_off;           // first superpixel of the image in the batch
+  int uniform;         // 1 when every image of the table has this geometry
 };
 
 // Device counters (unsigned long long): dead, raised_s, raised_c, nonfinite input.
