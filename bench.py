@@ -750,9 +750,10 @@ def run_learned(args):
     e2e_steps = max(4, args.steps // 4)
     e2e_run(4, True)
     barrier()
-    t0 = time.perf_counter()
-    e2e_run(e2e_steps, True)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    with ClockSampler(local) as clk_e2e:
+        t0 = time.perf_counter()
+        e2e_run(e2e_steps, True)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e = whole_job_value(world, n * N * e2e_steps, e2e_s)
     barrier()
     t0 = time.perf_counter()
@@ -801,7 +802,7 @@ def run_learned(args):
                 "how": f"{E2E_CONTEXTS} batch contexts on as many streams take steps in turn (copies of one "
                        "step overlap the kernels of the others); each step copies its images in (one copy of the stacked "
                        "images) and its labels out (one copy of the context's label buffer)",
-                "serial": round(e2e_serial, 3)},
+                "serial": round(e2e_serial, 3), "clocks": clk_e2e.summary()},
         "gpu_launches": (1 + 5 + 1 + 2 * LEARN_T + 1) * args.steps,
         "clocks": clocks, "clocks_plain": clocks_p,
         "weights": os.path.relpath(pretrained_path(LEARN_V), ROOT),
