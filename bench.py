@@ -528,8 +528,8 @@ NET_FLOPS_PER_CELL = 2 * (3 * 288 * 32 + 288 * 16)
 # 96 such images (dram__bytes_read.sum + dram__bytes_write.sum), scaled per image
 # (traffic grows with the image count), per launch variant (blocks per SM); a variant
 # not captured with the current kernel reports null.
-#   7: one-cell-per-warp k_em_pass_batch_flat capped at 72 registers: 182.12 MB + 28.57 MB.
-EM_BATCH_TRAFFIC_PER_IMAGE = {7: int((182.123264e6 + 28.572928e6) / 96)}
+#   7: one-cell-per-warp k_em_pass_batch_flat capped at 72 registers: 182.06 MB + 29.63 MB.
+EM_BATCH_TRAFFIC_PER_IMAGE = {7: int((182.059520e6 + 29.629184e6) / 96)}
 
 
 def measured_peaks():
