@@ -872,7 +872,7 @@ def run_profile_case(args):
         bt = gm.SuperpixelsBatch([(H, W)] * args.images, spacing=LEARN_V)
         bt.autotune(imgs, reps=2)  # the launch choices of the timed step
         if args.blocks_per_sm:
-            bt.set_launch(args.blocks_per_sm)
+            bt.set_launch(args.blocks_per_sm, first_pass=args.first_pass if args.first_pass else None)
         bt.set_init_net(net)
         for _ in range(2):
             bt.segment(imgs, LEARN_T)
@@ -1160,6 +1160,8 @@ def main():
     ap.add_argument("--warps-per-cell", type=int, default=0, help="with --profile-case: launch shape")
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="with --profile-case --workload learned481: E+M pass variant (after the autotuner)")
+    ap.add_argument("--first-pass", type=int, default=0,
+                    help="with --blocks-per-sm: the first E+M pass's variant (0: the autotuner's)")
     ap.add_argument("--workload", default="learned481",
                     choices=["learned481", "481x321", "3840x2160", "batch256", "conn256", "metrics256"],
                     help="learned481 (the headline line); 481x321, 3840x2160 or batch256 (other lines); "

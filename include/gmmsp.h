@@ -259,9 +259,19 @@ gmmsp_status gmmsp_autotune(gmmsp_ctx c, int reps, int *best, double *times_ms);
  *   persistent grid of that many blocks per SM; 6, 7: one cell per warp with
  *   the registers capped for that occupancy), keeps the fastest, then times
  *   the two finalize kernels and keeps the faster; times_ms NULL or 5
- *   doubles (E + M pass, in candidate order).  Synchronises.
+ *   doubles (E + M pass, in candidate order).  The first pass of a segment
+ *   (its covariance blocks are diagonal after either start, Sec. III-C or the
+ *   learned one) gets a choice of its own: the diagonal kernels at 6 and 7
+ *   are timed too, and the fastest of them and the 3-5 times is kept.
+ *   Synchronises.
  * gmmsp_batch_set_launch: blocks per SM of the E + M pass (1..16; >= 6
- *   selects the one-cell-per-warp kernel).
+ *   selects the one-cell-per-warp kernel); the first pass keeps its own
+ *   choice where the autotuner or gmmsp_batch_set_first_pass made one.
+ * gmmsp_batch_set_first_pass: blocks per SM of a segment's first E + M pass
+ *   (1..16, or 0: the same as the other passes; the default).
+ * gmmsp_batch_get_first_pass: the first pass's blocks per SM in effect and,
+ *   in times_ms (NULL or 2 doubles), the autotuned times of its diagonal
+ *   kernels at 6 and 7 (ms; 0 before gmmsp_batch_autotune).
  * gmmsp_batch_info: totals over the batch (any pointer may be NULL).
  */
 typedef struct gmmsp_batch_s *gmmsp_batch;
@@ -274,6 +284,8 @@ gmmsp_status gmmsp_batch_get_params(gmmsp_batch b, int i, double *mu_host, doubl
 gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void *const *images_dev, const int *pitches,
                                   int32_t *const *labels_dev, int reps, int *best, double *times_ms);
 gmmsp_status gmmsp_batch_set_launch(gmmsp_batch b, int blocks_per_sm);
+gmmsp_status gmmsp_batch_set_first_pass(gmmsp_batch b, int blocks_per_sm);
+gmmsp_status gmmsp_batch_get_first_pass(gmmsp_batch b, int *blocks_per_sm, double *times_ms);
 /* Launch choices of b: blocks per SM of the E + M pass, whether the finalize
  * runs 16 lanes per superpixel (1) or one thread per superpixel (0), and the
  * two finalize times the autotuner measured (ms; 0 before gmmsp_batch_autotune).
@@ -281,7 +293,8 @@ gmmsp_status gmmsp_batch_set_launch(gmmsp_batch b, int blocks_per_sm);
 gmmsp_status gmmsp_batch_get_tuning(gmmsp_batch b, int *blocks_per_sm, int *finalize16, double *finalize_ms);
 /* Sets both launch choices, e.g. from a tuning cache (blocks_per_sm 1..16,
  * finalize16 0 or 1; finalize16 has an effect only where the 16-lane
- * finalize applies: mixed precision, full colour model). */
+ * finalize applies: mixed precision, full colour model).  The first E + M
+ * pass follows blocks_per_sm again until gmmsp_batch_set_first_pass. */
 gmmsp_status gmmsp_batch_set_tuning(gmmsp_batch b, int blocks_per_sm, int finalize16);
 gmmsp_status gmmsp_batch_info(gmmsp_batch b, long long *total_pixels, int *total_k, int *total_cells);
 /* Copies image i's CIELAB colours (Sec. III-A, after the conversion of Sec.

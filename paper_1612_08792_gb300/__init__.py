@@ -28,7 +28,7 @@ __all__ = [
     "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "SuperpixelsBatch", "gmmsp_bounds_status",
     "gmmsp_batch_create", "gmmsp_batch_segment", "gmmsp_batch_get_params", "gmmsp_batch_autotune",
     "gmmsp_batch_set_launch", "gmmsp_batch_set_tuning", "gmmsp_batch_info", "gmmsp_batch_destroy", "gmmsp_status_string", "gmmsp_destroy",
-    "gmmsp_batch_get_tuning", "gmmsp_batch_set_init_net", "gmmsp_batch_lab", "gmmsp_batch_targets", "gmmsp_batch_get_lab",
+    "gmmsp_batch_get_tuning", "gmmsp_batch_set_first_pass", "gmmsp_batch_get_first_pass", "gmmsp_batch_set_init_net", "gmmsp_batch_lab", "gmmsp_batch_targets", "gmmsp_batch_get_lab",
     "gmmsp_net_param_count", "gmmsp_net_create", "gmmsp_net_set_weights", "gmmsp_net_get_weights",
     "gmmsp_net_forward", "gmmsp_net_grad", "gmmsp_net_adam", "gmmsp_net_train_step", "gmmsp_net_get_activation",
     "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_net_get_adam", "gmmsp_net_set_adam", "gmmsp_set_init", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
@@ -370,6 +370,8 @@ def _batch_lib():
             "gmmsp_batch_info": (I, [P, ctypes.POINTER(ctypes.c_longlong), pint, pint]),
             "gmmsp_batch_get_lab": (I, [P, I, P]),
             "gmmsp_batch_get_tuning": (I, [P, pint, pint, P]),
+            "gmmsp_batch_set_first_pass": (I, [P, I]),
+            "gmmsp_batch_get_first_pass": (I, [P, pint, P]),
             "gmmsp_batch_last_error": (ctypes.c_char_p, [P]),
             "gmmsp_batch_destroy": (None, [P]),
         }
@@ -454,13 +456,29 @@ def gmmsp_batch_get_lab(b, i, H, W):
     return out
 
 
+def gmmsp_batch_set_first_pass(b, blocks_per_sm: int) -> None:
+    """Blocks per SM of a segment's first E + M pass (0: as the other passes)."""
+    _bcheck(b, _batch_lib().gmmsp_batch_set_first_pass(b, int(blocks_per_sm)))
+
+
+def gmmsp_batch_get_first_pass(b):
+    """(blocks per SM in effect, {6: ms, 7: ms} of the autotuned diagonal kernels)."""
+    bps = ctypes.c_int()
+    ms = np.zeros(2)
+    _bcheck(b, _batch_lib().gmmsp_batch_get_first_pass(b, ctypes.byref(bps), ms.ctypes.data_as(ctypes.c_void_p)))
+    return bps.value, {6: float(ms[0]), 7: float(ms[1])}
+
+
 def gmmsp_batch_get_tuning(b):
     bps, f16 = ctypes.c_int(), ctypes.c_int()
     ms = np.zeros(2)
     _bcheck(b, _batch_lib().gmmsp_batch_get_tuning(b, ctypes.byref(bps), ctypes.byref(f16),
                                                    ms.ctypes.data_as(ctypes.c_void_p)))
+    first, first_ms = gmmsp_batch_get_first_pass(b)
     return {"blocks_per_sm": bps.value, "finalize16": bool(f16.value),
-            "finalize_ms": {"16_lanes": float(ms[0]), "thread_per_superpixel": float(ms[1])}}
+            "finalize_ms": {"16_lanes": float(ms[0]), "thread_per_superpixel": float(ms[1])},
+            "first_pass_blocks_per_sm": first,
+            "first_pass_diag_ms": {str(k): v for k, v in first_ms.items()}}
 
 
 def gmmsp_batch_destroy(b) -> None:
@@ -789,18 +807,26 @@ class SuperpixelsBatch:
             hit = tuning_cache.lookup(cache, key)
             if hit is not None:
                 gmmsp_batch_set_tuning(self.b, hit["blocks_per_sm"], hit["finalize16"])
+                first = hit.get("first_pass_blocks_per_sm")
+                if isinstance(first, int) and 0 <= first <= 16:
+                    gmmsp_batch_set_first_pass(self.b, first)
                 return hit["blocks_per_sm"], {int(k): float(v) for k, v in hit.get("em_pass_ms", {}).items()}
         best, times = gmmsp_batch_autotune(self.b, images, [self._pitch(t) for t in images], self.labels, reps)
         if key is not None:
             from . import tuning_cache
             t = self.tuning()
             tuning_cache.store(cache, key, {"blocks_per_sm": int(best), "finalize16": bool(t["finalize16"]),
+                                            "first_pass_blocks_per_sm": int(t["first_pass_blocks_per_sm"]),
                                             "em_pass_ms": {str(k): v for k, v in times.items()},
                                             "finalize_ms": t["finalize_ms"]})
         return best, times
 
-    def set_launch(self, blocks_per_sm: int) -> None:
+    def set_launch(self, blocks_per_sm: int, first_pass: int | None = None) -> None:
+        """Blocks per SM of the E + M pass; `first_pass` that of a segment's first pass
+        (None keeps the current choice, 0 follows `blocks_per_sm`)."""
         gmmsp_batch_set_launch(self.b, blocks_per_sm)
+        if first_pass is not None:
+            gmmsp_batch_set_first_pass(self.b, first_pass)
 
     def info(self):
         return gmmsp_batch_info(self.b)

@@ -33,6 +33,8 @@ struct gmmsp_batch_s {
   cudaStream_t stream = nullptr;
   int sm_count = 152;
   int blocks_per_sm = 4;           // persistent grid of the E + M pass (autotuned)
+  int first_bps = 0;               // the first E + M pass (diagonal blocks); 0: as blocks_per_sm
+  double first_ms[2] = {0.0, 0.0}; // autotuned first-pass times at 6 and 7 blocks per SM
   int label_blocks_per_sm = 4;     // persistent grid of the label pass (its occupancy)
   bool fin16 = false;              // finalize with 16 lanes per superpixel (autotuned)
   double fin_ms[2] = {0.0, 0.0};   // autotuned finalize times: 16 lanes, one thread per superpixel
@@ -54,6 +56,7 @@ struct gmmsp_batch_s {
   int g_iters = -1;
   bool g_ll = false;
   int g_bps = -1;
+  int g_fbps = -1;
   gmmsp_net g_net = nullptr;
   long long g_gen = -1;
   gmmsp::ConnScratch conn;         // post-processing scratch, kept between calls
@@ -113,11 +116,13 @@ bool use_fin16(gmmsp_batch b) {
   return b->fin16 && b->p.precision != GMMSP_PREC_FP32 && b->p.colour_model == GMMSP_COLOUR_FULL;
 }
 
-int em_blocks(gmmsp_batch b) {
+int em_blocks(gmmsp_batch b, int bps) {
   const long long need = (b->total_cells + 3) / 4;
-  const long long cap = (long long)b->sm_count * b->blocks_per_sm;
+  const long long cap = (long long)b->sm_count * bps;
   return int(need < cap ? need : cap);
 }
+
+int first_bps(gmmsp_batch b) { return b->first_bps > 0 ? b->first_bps : b->blocks_per_sm; }
 
 gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
   cudaStream_t s = b->stream;
@@ -140,12 +145,13 @@ gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
     GB_CHECK(b, gmmsp::launch_init_batch(b->table, n, b->total_k, b->lab, b->p.lambda_c, b->theta, b->gp,
                                          kblocks, s));
   }
-  const int eb = em_blocks(b);
   const int fblocks = int(std::min<long long>((b->total_k + 31) / 32, (long long)b->sm_count * 16));
   for (int t = 0; t < iters; ++t) {
-    // the first pass follows the start (Sec. III-C or learned): diagonal blocks
+    // the first pass follows the start (Sec. III-C or learned): diagonal blocks,
+    // with a launch choice of its own
+    const int bps = t == 0 ? first_bps(b) : b->blocks_per_sm;
     GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, n, b->total_cells, b->lab, b->gp, b->partials,
-                                            b->p.precision, eb, b->blocks_per_sm, b->p.colour_model, s,
+                                            b->p.precision, em_blocks(b, bps), bps, b->p.colour_model, s,
                                             t == 0));
     GB_CHECK(b, gmmsp::launch_finalize_batch(b->table, n, b->total_k, b->partials, b->theta, b->gp,
                                              b->p.eps_s, b->p.eps_c, b->counters, b->p.precision,
@@ -320,7 +326,7 @@ gmmsp_status gmmsp_batch_segment(gmmsp_batch b, const void* const* images_dev, c
   } else {
     const long long gen = gmmsp::net_generation(b->net);
     if (!(b->exec && b->g_iters == iters && b->g_ll == want_ll && b->g_bps == b->blocks_per_sm &&
-          b->g_net == b->net && b->g_gen == gen)) {
+          b->g_fbps == first_bps(b) && b->g_net == b->net && b->g_gen == gen)) {
       drop_graph(b);
       GB_CHECK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       st = enqueue_batch(b, iters, want_ll);
@@ -340,6 +346,7 @@ gmmsp_status gmmsp_batch_segment(gmmsp_batch b, const void* const* images_dev, c
       b->g_iters = iters;
       b->g_ll = want_ll;
       b->g_bps = b->blocks_per_sm;
+      b->g_fbps = first_bps(b);
       b->g_net = b->net;
       b->g_gen = gen;
     }
@@ -392,6 +399,7 @@ gmmsp_status gmmsp_batch_get_lab(gmmsp_batch b, int i, float* lab_host) {
 gmmsp_status gmmsp_batch_set_tuning(gmmsp_batch b, int blocks_per_sm, int finalize16) {
   if (!b || blocks_per_sm < 1 || blocks_per_sm > 16 || finalize16 < 0 || finalize16 > 1) return GMMSP_E_INVALID;
   b->blocks_per_sm = blocks_per_sm;
+  b->first_bps = 0;
   b->fin16 = finalize16 != 0;
   drop_graph(b);
   return GMMSP_OK;
@@ -400,6 +408,22 @@ gmmsp_status gmmsp_batch_set_tuning(gmmsp_batch b, int blocks_per_sm, int finali
 gmmsp_status gmmsp_batch_set_launch(gmmsp_batch b, int blocks_per_sm) {
   if (!b || blocks_per_sm < 1 || blocks_per_sm > 16) return GMMSP_E_INVALID;
   b->blocks_per_sm = blocks_per_sm;
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_batch_set_first_pass(gmmsp_batch b, int blocks_per_sm) {
+  if (!b || blocks_per_sm < 0 || blocks_per_sm > 16) return GMMSP_E_INVALID;
+  b->first_bps = blocks_per_sm;
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_batch_get_first_pass(gmmsp_batch b, int* blocks_per_sm, double* times_ms) {
+  if (!b) return GMMSP_E_INVALID;
+  if (blocks_per_sm) *blocks_per_sm = first_bps(b);
+  if (times_ms) {
+    times_ms[0] = b->first_ms[0];
+    times_ms[1] = b->first_ms[1];
+  }
   return GMMSP_OK;
 }
 
@@ -419,28 +443,41 @@ gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void* const* images_dev, 
   cudaEvent_t e0, e1;
   GB_CHECK(b, cudaEventCreate(&e0));
   GB_CHECK(b, cudaEventCreate(&e1));
-  double best_ms = 1e30;
-  int best_c = b->blocks_per_sm;
-  for (int i = 0; i < 5; ++i) {
-    b->blocks_per_sm = cand[i];
-    const int eb = em_blocks(b);
+  // mean time of one E + M pass at `bps` blocks per SM, after a warm-up launch;
+  // theta stays the start's, so its covariance blocks are diagonal throughout
+  auto time_pass = [&](int bps, bool diag, double* per) -> gmmsp_status {
+    const int eb = em_blocks(b, bps);
     GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, b->n, b->total_cells, b->lab, b->gp, b->partials,
-                                            b->p.precision, eb, b->blocks_per_sm, b->p.colour_model,
-                                            b->stream));  // warm-up
+                                            b->p.precision, eb, bps, b->p.colour_model, b->stream, diag));
     GB_CHECK(b, cudaEventRecord(e0, b->stream));
     for (int r = 0; r < reps; ++r)
       GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, b->n, b->total_cells, b->lab, b->gp, b->partials,
-                                              b->p.precision, eb, b->blocks_per_sm, b->p.colour_model,
-                                              b->stream));
+                                              b->p.precision, eb, bps, b->p.colour_model, b->stream, diag));
     GB_CHECK(b, cudaEventRecord(e1, b->stream));
     GB_CHECK(b, cudaEventSynchronize(e1));
     float ms = 0.f;
     GB_CHECK(b, cudaEventElapsedTime(&ms, e0, e1));
-    const double per = double(ms) / reps;
+    *per = double(ms) / reps;
+    return GMMSP_OK;
+  };
+  double best_ms = 1e30, first_best = 1e30;
+  int best_c = b->blocks_per_sm, first_c = 0;
+  for (int i = 0; i < 5; ++i) {
+    double per = 0.0;
+    st = time_pass(cand[i], false, &per);
+    if (st != GMMSP_OK) return st;
     if (times_ms) times_ms[i] = per;
     if (per < best_ms) { best_ms = per; best_c = cand[i]; }
+    if (cand[i] < 6 && per < first_best) { first_best = per; first_c = cand[i]; }  // no diagonal variant
+  }
+  // the first pass: the diagonal kernels of the one-cell-per-warp launch
+  for (int i = 0; i < 2; ++i) {
+    st = time_pass(6 + i, true, &b->first_ms[i]);
+    if (st != GMMSP_OK) return st;
+    if (b->first_ms[i] < first_best) { first_best = b->first_ms[i]; first_c = 6 + i; }
   }
   b->blocks_per_sm = best_c;
+  b->first_bps = first_c;
   if (b->p.precision != GMMSP_PREC_FP32 && b->p.colour_model == GMMSP_COLOUR_FULL) {
     // finalize: 16 lanes per superpixel against one thread per superpixel
     // (theta changes here; every segment starts again from theta_0)

@@ -3,8 +3,8 @@ batch shape another process has tuned on the same kind of GPU.
 
 Key: the GPU name, the spacing (or K) asked for, the colour model, the
 precision, the image count and the total pixel count in quarter-octave
-buckets.  Value: the E + M pass blocks per SM, the 16-lane finalize choice
-and the measured E + M times.  Writes go through a temporary file and an
+buckets.  Value: the E + M pass blocks per SM, the 16-lane finalize choice,
+the measured E + M times and (optional) the first pass's blocks per SM.  Writes go through a temporary file and an
 atomic rename; a file that cannot be parsed reads as empty.
 """
 from __future__ import annotations

@@ -89,6 +89,8 @@ def test_invalid_arguments_rejected_on_host(lib, W, H, K, sp, pitch, eps):
 def test_null_context_calls(lib):
     assert lib.gmmsp_em_iters(None, 1, None) == 1
     assert lib.gmmsp_labels(None, None, None) == 1
+    assert lib.gmmsp_batch_set_first_pass(None, 6) == 1
+    assert lib.gmmsp_batch_get_first_pass(None, None, None) == 1
     lib.gmmsp_destroy(None)
 
 

@@ -115,6 +115,7 @@ def test_tuning_cache_applies_stored_choices(gm, tmp_path):
     assert best2 == best and times2 == times
     assert b.tuning()["blocks_per_sm"] == tun["blocks_per_sm"]
     assert b.tuning()["finalize16"] == tun["finalize16"]
+    assert b.tuning()["first_pass_blocks_per_sm"] == tun["first_pass_blocks_per_sm"]
     for x, y in zip(b.segment(imgs, iters=3), ref):
         assert (x.cpu().numpy() == y.cpu().numpy()).mean() >= 0.9999
     b.close()

@@ -75,6 +75,25 @@ def test_batch_launch_variants_match_oracle(gm, plain_case, bps, fin16):
     bt.close()
 
 
+@pytest.mark.parametrize("bps,first", [(7, 6), (6, 7), (7, 4), (4, 7)])
+def test_batch_first_pass_launch_of_its_own(gm, plain_case, bps, first):
+    """A segment's first E + M pass (diagonal blocks) at another launch choice than the rest."""
+    import torch
+    labs, refs = plain_case
+    dev = [torch.from_numpy(x).cuda() for x in labs]
+    bt = gm.SuperpixelsBatch([(H, W) for (W, H) in SIZES], spacing=V, lab_input=True)
+    gm.gmmsp_batch_set_tuning(bt.b, bps, True)
+    assert bt.tuning()["first_pass_blocks_per_sm"] == bps  # follows until set
+    bt.set_launch(bps, first_pass=first)
+    assert bt.tuning()["first_pass_blocks_per_sm"] == first and bt.tuning()["blocks_per_sm"] == bps
+    labels, ll = bt.segment(dev, iters=T, want_loglik=True)
+    torch.cuda.synchronize()
+    for i, (W, H) in enumerate(SIZES):
+        mu, cs, cc = bt.get_params(i, refs[i].grid.K)
+        check_image(mu, cs, cc, labels[i].cpu().numpy(), ll[i], refs[i], (bps, first, i, W, H))
+    bt.close()
+
+
 @pytest.fixture(scope="module")
 def learned_case(gm):
     """The trained network's theta_0 on the GPU for LEARN_B images of the learned start's workload."""
