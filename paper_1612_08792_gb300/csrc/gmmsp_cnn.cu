@@ -746,17 +746,17 @@ __global__ void k_init_from_net(const float* __restrict__ dmu, int ds, const flo
       o[5 + q] = logeig[i * ls + q];
     }
     const double v = g.v, l2 = lambda_c * lambda_c;
-    double mu[5] = {x + v * double(o[0]), y + v * double(o[1]), double(P[j]) + kColourUnit * double(o[2]),
-                    double(P[N + j]) + kColourUnit * double(o[3]),
-                    double(P[2 * N + j]) + kColourUnit * double(o[4])};
+    double mu[5] = {x + v * widen(o[0]), y + v * widen(o[1]), widen(P[j]) + kColourUnit * widen(o[2]),
+                    widen(P[N + j]) + kColourUnit * widen(o[3]),
+                    widen(P[2 * N + j]) + kColourUnit * widen(o[4])};
     mu[0] = fmin(fmax(mu[0], double(kx - 1) * v), double(kx + 2) * v);
     mu[1] = fmin(fmax(mu[1], double(ky - 1) * v), double(ky + 2) * v);
     const float lo = -10.f, hi = 10.f;
-    const double cs[3] = {fmax(v * v * exp(double(fminf(fmaxf(o[5], lo), hi))), eps_s), 0.0,
-                          fmax(v * v * exp(double(fminf(fmaxf(o[6], lo), hi))), eps_s)};
-    const double cc[6] = {fmax(l2 * exp(double(fminf(fmaxf(o[7], lo), hi))), eps_c), 0.0, 0.0,
-                          fmax(l2 * exp(double(fminf(fmaxf(o[8], lo), hi))), eps_c), 0.0,
-                          fmax(l2 * exp(double(fminf(fmaxf(o[9], lo), hi))), eps_c)};
+    const double cs[3] = {fmax(v * v * exp(widen(fminf(fmaxf(o[5], lo), hi))), eps_s), 0.0,
+                          fmax(v * v * exp(widen(fminf(fmaxf(o[6], lo), hi))), eps_s)};
+    const double cc[6] = {fmax(l2 * exp(widen(fminf(fmaxf(o[7], lo), hi))), eps_c), 0.0, 0.0,
+                          fmax(l2 * exp(widen(fminf(fmaxf(o[8], lo), hi))), eps_c), 0.0,
+                          fmax(l2 * exp(widen(fminf(fmaxf(o[9], lo), hi))), eps_c)};
     double* th = theta + i * kTheta;
     bool fin = true;
     for (int q = 0; q < 5; ++q) {

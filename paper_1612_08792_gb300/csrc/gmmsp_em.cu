@@ -688,7 +688,7 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
   }
   if (SHIFT) {
 #pragma unroll
-    for (int j = 0; j < kStats; ++j) S[j] = T(double(hi[j]) + double(lo[j]));
+    for (int j = 0; j < kStats; ++j) S[j] = T(widen(hi[j]) + widen(lo[j]));
   }
   const T Wk = S[ST_W];
   if (!(Wk >= T(1e-8))) {
@@ -697,7 +697,10 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
     float* G = gp + (long long)k * kGP;
     const T iw = Num<T>::rcp(Wk);
     T mu[5], cs[3], cc[6];
-    const T ox = T(kx * g.v), oy = T(ky * g.v);  // origin of k's cell
+    // origin of k's cell (through FP32, exact below 2^24)
+    const int ix = kx * g.v, iy = ky * g.v;
+    const T ox = ix < (1 << 24) ? from_f32<T>(float(ix)) : T(ix);
+    const T oy = iy < (1 << 24) ? from_f32<T>(float(iy)) : T(iy);
     // Moments about r: Sigma = S2 / W - d d^T with d = S1 / W.  The shifted
     // path has r = mu_ref, the FP32 mean the E-step subtracted (spatial part
     // relative to the cell origin); the raw path has r = 0.
@@ -714,10 +717,10 @@ __device__ __forceinline__ void finalize_k(const Geom& g, const PT* __restrict__
     cc[4] = fma(-dl[3], dl[4], S[ST_S2C + 4] * iw);
     cc[5] = fma(-dl[4], dl[4], S[ST_S2C + 5] * iw);
     if (kShifted) {
-      mu[0] = ox + (T(G[0]) + dl[0]);
-      mu[1] = oy + (T(G[1]) + dl[1]);
+      mu[0] = ox + (from_f32<T>(G[0]) + dl[0]);
+      mu[1] = oy + (from_f32<T>(G[1]) + dl[1]);
 #pragma unroll
-      for (int j = 2; j < 5; ++j) mu[j] = T(G[j]) + dl[j];
+      for (int j = 2; j < 5; ++j) mu[j] = from_f32<T>(G[j]) + dl[j];
     } else {
       mu[0] = ox + dl[0];
       mu[1] = oy + dl[1];

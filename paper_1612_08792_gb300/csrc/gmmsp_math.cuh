@@ -28,6 +28,7 @@
 
 #include <math.h>
 
+#include "gmmsp_fpconv.cuh"
 #include "gmmsp_internal.cuh"
 
 namespace gmmsp {
@@ -41,8 +42,8 @@ template <> struct Num<double> {
   // 1/x: FP32 estimate (MUFU, relative error < 2^-22), two Newton steps.
   static __device__ __forceinline__ double rcp(double x) {
     float r0;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(float(x)));
-    double r = double(r0);
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(narrow(x)));
+    double r = widen(r0);
     double e = fma(-x, r, 1.0);
     r = fma(r, e, r);
     e = fma(-x, r, 1.0);
@@ -50,7 +51,7 @@ template <> struct Num<double> {
   }
   // sqrt(x), x > 0: FP32 estimate of 1/sqrt, two Newton steps, then x * rsqrt.
   static __device__ __forceinline__ double sqrt_(double x) {
-    double y = double(rsqrtf(float(x)));
+    double y = widen(rsqrtf(narrow(x)));
     const double hx = 0.5 * x;
     y = y * fma(-hx * y, y, 1.5);
     y = y * fma(-hx * y, y, 1.5);
@@ -62,7 +63,7 @@ template <> struct Num<double> {
     const long long b = __double_as_longlong(x);
     const int e = int((b >> 52) & 0x7ff) - 1023;
     const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
-    return float(e) + __log2f(float(m));
+    return float(e) + __log2f(narrow(m));
   }
 };
 
@@ -143,11 +144,12 @@ __device__ int clamp_sym3(T* A, T eps) {
   const T c0 = a00 * fma(a11, a22, -a12 * a12) - a01 * fma(a01, a22, -a12 * a02) +
                a02 * fma(a01, a12, -a11 * a02);
   float f1, f2, f3;
-  eig3_seed(float(a00), float(a01), float(a02), float(a11), float(a12), float(a22), f1, f2, f3);
-  const int n = (T(f1) < eps) + (T(f2) < eps) + (T(f3) < eps);
+  eig3_seed(to_f32(a00), to_f32(a01), to_f32(a02), to_f32(a11), to_f32(a12), to_f32(a22), f1, f2, f3);
+  const T t1 = from_f32<T>(f1), t2 = from_f32<T>(f2), t3 = from_f32<T>(f3);
+  const int n = (t1 < eps) + (t2 < eps) + (t3 < eps);
   if (n == 0) return 0;
-  const T spread = T(f3) - T(f1);
-  const T scale = fabs(T(f3)) + eps;
+  const T spread = t3 - t1;
+  const T scale = fabs(t3) + eps;
   if (n == 3 || spread <= T(1e-6) * scale) {
     const T f = (n == 3) ? eps : (c2 / T(3) > eps ? c2 / T(3) : eps);
     A[0] = f; A[1] = T(0); A[2] = T(0); A[3] = f; A[4] = T(0); A[5] = f;
@@ -156,13 +158,13 @@ __device__ int clamp_sym3(T* A, T eps) {
   // The raised eigenvalue (n = 1) or the one kept (n = 2), polished by two
   // Newton steps on the cubic; the other two enter only through their sum and
   // product, which follow from the cubic's coefficients.
-  T lj = (n == 1) ? T(f1) : T(f3);
+  T lj = (n == 1) ? t1 : t3;
   T dp = T(0);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const T pv = fma(fma(lj - c2, lj, c1), lj, -c0);   // p(lj)
     dp = fma(fma(T(3), lj, -T(2) * c2), lj, c1);        // p'(lj)
-    if (fabs(dp) > T(1e-12) * scale * scale) lj -= pv * T(__frcp_rn(float(dp)));
+    if (fabs(dp) > T(1e-12) * scale * scale) lj -= pv * from_f32<T>(__frcp_rn(to_f32(dp)));
   }
   dp = fma(fma(T(3), lj, -T(2) * c2), lj, c1);  // (lj - la)(lj - lb)
   if (!(fabs(dp) > T(1e-12) * scale * scale)) {
@@ -213,9 +215,9 @@ __device__ bool pack_gp(const T* mu, const T* cs, const T* cc_in, T ox, T oy, fl
     if (!(cs[0] > T(0) && ds > T(0) && cc_in[0] > T(0))) return false;
     const T hs = T(-0.5) * M::kLog2e * M::rcp(ds);
     const T hc = T(-0.5) * M::kLog2e * M::rcp(cc_in[0]);
-    o[0] = make_float4(float(mu[0] - ox), float(mu[1] - oy), float(mu[2]), 0.f);
-    o[1] = make_float4(0.f, float(hs * cs[2]), float(T(-2) * hs * cs[1]), float(hs * cs[0]));
-    o[2] = make_float4(float(hc), 0.f, 0.f, 0.f);
+    o[0] = make_float4(to_f32(mu[0] - ox), to_f32(mu[1] - oy), to_f32(mu[2]), 0.f);
+    o[1] = make_float4(0.f, to_f32(hs * cs[2]), to_f32(T(-2) * hs * cs[1]), to_f32(hs * cs[0]));
+    o[2] = make_float4(to_f32(hc), 0.f, 0.f, 0.f);
     const float lnorm = -0.5f * (M::log2_(ds) + M::log2_(cc_in[0])) - float(M::kHalf3_Log2_2Pi);
     o[3] = make_float4(0.f, 0.f, lnorm, 0.f);
     return true;
@@ -233,11 +235,11 @@ __device__ bool pack_gp(const T* mu, const T* cs, const T* cc_in, T ox, T oy, fl
   if (!(cs[0] > T(0) && ds > T(0) && cc[0] > T(0) && c22 > T(0) && dc > T(0))) return false;
   const T hs = T(-0.5) * M::kLog2e * M::rcp(ds);   // -(1/2) log2(e) / det
   const T hc = T(-0.5) * M::kLog2e * M::rcp(dc);
-  o[0] = make_float4(float(mu[0] - ox), float(mu[1] - oy), float(mu[2]), float(mu[3]));
-  o[1] = make_float4(float(mu[4]), float(hs * cs[2]), float(T(-2) * hs * cs[1]), float(hs * cs[0]));
-  o[2] = make_float4(float(hc * c00), float(hc * c11), float(hc * c22), float(T(2) * hc * c01));
+  o[0] = make_float4(to_f32(mu[0] - ox), to_f32(mu[1] - oy), to_f32(mu[2]), to_f32(mu[3]));
+  o[1] = make_float4(to_f32(mu[4]), to_f32(hs * cs[2]), to_f32(T(-2) * hs * cs[1]), to_f32(hs * cs[0]));
+  o[2] = make_float4(to_f32(hc * c00), to_f32(hc * c11), to_f32(hc * c22), to_f32(T(2) * hc * c01));
   const float lnorm = -0.5f * (M::log2_(ds) + M::log2_(dc)) - float(M::kHalfD_Log2_2Pi);
-  o[3] = make_float4(float(T(2) * hc * c02), float(T(2) * hc * c12), lnorm, 0.f);
+  o[3] = make_float4(to_f32(T(2) * hc * c02), to_f32(T(2) * hc * c12), lnorm, 0.f);
   return true;
 }
 
