@@ -286,6 +286,23 @@ gmmsp_status gmmsp_batch_autotune(gmmsp_batch b, const void *const *images_dev, 
 gmmsp_status gmmsp_batch_set_launch(gmmsp_batch b, int blocks_per_sm);
 gmmsp_status gmmsp_batch_set_first_pass(gmmsp_batch b, int blocks_per_sm);
 gmmsp_status gmmsp_batch_get_first_pass(gmmsp_batch b, int *blocks_per_sm, double *times_ms);
+/* One E + M pass from the start, for checking the first-pass kernels (Algorithm
+ * 1 steps 1-3: the conversion and theta_0 as a segment begins, Sec. III-C or
+ * the network; then the E-step, Eq. Rik, and the M-step partial sums of Eq.
+ * UpdateMu / UpdateSigS / UpdateSigC per cell), at blocks_per_sm (1..16, as
+ * gmmsp_batch_set_launch) with diagonal 1 (the kernel that leaves the zero
+ * off-diagonal covariance terms of theta_0 out) or 0 (the general kernel).
+ * Copies the per-cell partials to partials_host: total_cells rows of 136 FP32
+ * values (9 candidate slots x 15 statistics, then the cell's log-likelihood;
+ * mixed precision: statistics about the previous mean, log2 units; FP32
+ * precision: raw moments, nats), *n_floats of them.  With partials_host
+ * NULL only *n_floats is set.  Images, pitches and labels as
+ * gmmsp_batch_segment (labels are not written).  Synchronises the batch's
+ * stream.  Errors: GMMSP_E_INVALID for a NULL handle, both outputs NULL or an
+ * argument out of range; GMMSP_E_CUDA on a CUDA error. */
+gmmsp_status gmmsp_batch_first_pass_partials(gmmsp_batch b, const void *const *images_dev, const int *pitches,
+                                             int32_t *const *labels_dev, int blocks_per_sm, int diagonal,
+                                             float *partials_host, long long *n_floats);
 /* Launch choices of b: blocks per SM of the E + M pass, whether the finalize
  * runs 16 lanes per superpixel (1) or one thread per superpixel (0), and the
  * two finalize times the autotuner measured (ms; 0 before gmmsp_batch_autotune).

@@ -28,7 +28,8 @@ __all__ = [
     "gmmsp_autotune", "gmmsp_segment_lab_noalloc", "gmmsp_last_error", "SuperpixelsBatch", "gmmsp_bounds_status",
     "gmmsp_batch_create", "gmmsp_batch_segment", "gmmsp_batch_get_params", "gmmsp_batch_autotune",
     "gmmsp_batch_set_launch", "gmmsp_batch_set_tuning", "gmmsp_batch_info", "gmmsp_batch_destroy", "gmmsp_status_string", "gmmsp_destroy",
-    "gmmsp_batch_get_tuning", "gmmsp_batch_set_first_pass", "gmmsp_batch_get_first_pass", "gmmsp_batch_set_init_net", "gmmsp_batch_lab", "gmmsp_batch_targets", "gmmsp_batch_get_lab",
+    "gmmsp_batch_get_tuning", "gmmsp_batch_set_first_pass", "gmmsp_batch_get_first_pass",
+    "gmmsp_batch_first_pass_partials", "gmmsp_batch_set_init_net", "gmmsp_batch_lab", "gmmsp_batch_targets", "gmmsp_batch_get_lab",
     "gmmsp_net_param_count", "gmmsp_net_create", "gmmsp_net_set_weights", "gmmsp_net_get_weights",
     "gmmsp_net_forward", "gmmsp_net_grad", "gmmsp_net_adam", "gmmsp_net_train_step", "gmmsp_net_get_activation",
     "gmmsp_net_check", "gmmsp_net_destroy", "gmmsp_net_get_adam", "gmmsp_net_set_adam", "gmmsp_set_init", "gmmsp_init_from_net", "gmmsp_tc_wait_selftest",
@@ -372,6 +373,7 @@ def _batch_lib():
             "gmmsp_batch_get_tuning": (I, [P, pint, pint, P]),
             "gmmsp_batch_set_first_pass": (I, [P, I]),
             "gmmsp_batch_get_first_pass": (I, [P, pint, P]),
+            "gmmsp_batch_first_pass_partials": (I, [P, P, P, P, I, I, P, P]),
             "gmmsp_batch_last_error": (ctypes.c_char_p, [P]),
             "gmmsp_batch_destroy": (None, [P]),
         }
@@ -434,6 +436,20 @@ def gmmsp_batch_autotune(b, images, pitches, labels, reps=3):
                                                  _ptr_array(labels), int(reps), ctypes.byref(best),
                                                  times.ctypes.data_as(ctypes.c_void_p)))
     return best.value, dict(zip((3, 4, 5, 6, 7), times.tolist()))
+
+
+def gmmsp_batch_first_pass_partials(b, images, pitches, labels, blocks_per_sm: int, diagonal: bool):
+    """One E + M pass from the start; the per-cell partials as a (cells, 136) float32 array."""
+    lib = _batch_lib()
+    nf = ctypes.c_longlong()
+    _bcheck(b, lib.gmmsp_batch_first_pass_partials(b, None, None, None, int(blocks_per_sm), int(bool(diagonal)),
+                                                   None, ctypes.byref(nf)))
+    out = np.empty(nf.value, dtype=np.float32)
+    pit = np.ascontiguousarray(pitches, dtype=np.int32)
+    _bcheck(b, lib.gmmsp_batch_first_pass_partials(b, _ptr_array(images), pit.ctypes.data_as(ctypes.c_void_p),
+                                                   _ptr_array(labels), int(blocks_per_sm), int(bool(diagonal)),
+                                                   out.ctypes.data_as(ctypes.c_void_p), None))
+    return out.reshape(-1, 136)
 
 
 def gmmsp_batch_set_launch(b, blocks_per_sm: int) -> None:
@@ -820,6 +836,11 @@ class SuperpixelsBatch:
                                             "em_pass_ms": {str(k): v for k, v in times.items()},
                                             "finalize_ms": t["finalize_ms"]})
         return best, times
+
+    def first_pass_partials(self, images, blocks_per_sm: int, diagonal: bool):
+        """The per-cell partials of one E + M pass from the start (a check of the first-pass kernels)."""
+        return gmmsp_batch_first_pass_partials(self.b, images, [self._pitch(t) for t in images], self.labels,
+                                               blocks_per_sm, diagonal)
 
     def set_launch(self, blocks_per_sm: int, first_pass: int | None = None) -> None:
         """Blocks per SM of the E + M pass; `first_pass` that of a segment's first pass

@@ -124,7 +124,9 @@ int em_blocks(gmmsp_batch b, int bps) {
 
 int first_bps(gmmsp_batch b) { return b->first_bps > 0 ? b->first_bps : b->blocks_per_sm; }
 
-gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
+// The start of a segment: the CIELAB conversion and theta_0 (Sec. III-C or
+// the network), whose covariance blocks are diagonal.
+gmmsp_status enqueue_start(gmmsp_batch b) {
   cudaStream_t s = b->stream;
   const int n = b->n;
   GB_CHECK(b, cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * gmmsp::CNT_N, s));
@@ -145,6 +147,14 @@ gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
     GB_CHECK(b, gmmsp::launch_init_batch(b->table, n, b->total_k, b->lab, b->p.lambda_c, b->theta, b->gp,
                                          kblocks, s));
   }
+  return GMMSP_OK;
+}
+
+gmmsp_status enqueue_batch(gmmsp_batch b, int iters, bool want_ll) {
+  cudaStream_t s = b->stream;
+  const int n = b->n;
+  const gmmsp_status st = enqueue_start(b);
+  if (st != GMMSP_OK) return st;
   const int fblocks = int(std::min<long long>((b->total_k + 31) / 32, (long long)b->sm_count * 16));
   for (int t = 0; t < iters; ++t) {
     // the first pass follows the start (Sec. III-C or learned): diagonal blocks,
@@ -424,6 +434,30 @@ gmmsp_status gmmsp_batch_get_first_pass(gmmsp_batch b, int* blocks_per_sm, doubl
     times_ms[0] = b->first_ms[0];
     times_ms[1] = b->first_ms[1];
   }
+  return GMMSP_OK;
+}
+
+gmmsp_status gmmsp_batch_first_pass_partials(gmmsp_batch b, const void* const* images_dev, const int* pitches,
+                                             int32_t* const* labels_dev, int blocks_per_sm, int diagonal,
+                                             float* partials_host, long long* n_floats) {
+  if (!b || (!partials_host && !n_floats) || blocks_per_sm < 1 || blocks_per_sm > 16 || diagonal < 0 ||
+      diagonal > 1)
+    return GMMSP_E_INVALID;
+  const long long nf = (long long)b->total_cells * gmmsp::kPartStride;
+  if (n_floats) *n_floats = nf;
+  if (!partials_host) return GMMSP_OK;
+  if (b->state == GMMSP_E_CUDA || b->state == GMMSP_E_NOMEM) return GMMSP_E_STATE;
+  b->state = GMMSP_OK;
+  gmmsp_status st = upload_table(b, images_dev, pitches, labels_dev);
+  if (st != GMMSP_OK) return st;
+  st = enqueue_start(b);
+  if (st != GMMSP_OK) return st;
+  GB_CHECK(b, gmmsp::launch_em_pass_batch(b->table, b->n, b->total_cells, b->lab, b->gp, b->partials,
+                                          b->p.precision, em_blocks(b, blocks_per_sm), blocks_per_sm,
+                                          b->p.colour_model, b->stream, diagonal != 0));
+  GB_CHECK(b, cudaMemcpyAsync(partials_host, b->partials, size_t(nf) * sizeof(float), cudaMemcpyDeviceToHost,
+                              b->stream));
+  GB_CHECK(b, cudaStreamSynchronize(b->stream));
   return GMMSP_OK;
 }
 

@@ -119,3 +119,29 @@ def test_tuning_cache_applies_stored_choices(gm, tmp_path):
     for x, y in zip(b.segment(imgs, iters=3), ref):
         assert (x.cpu().numpy() == y.cpu().numpy()).mean() >= 0.9999
     b.close()
+
+
+@pytest.mark.parametrize("start,colour", [("plain", "full"), ("plain", "split"), ("plain", "gray"),
+                                          ("learned", "full")])
+def test_first_pass_diagonal_kernel_equals_general(gm, start, colour):
+    """Both starts give axis-aligned covariances, so the first E + M pass runs a kernel that leaves
+    the zero off-diagonal terms out. Its per-cell partials must equal the general kernel's (value
+    for value), at both launch choices of the one-cell-per-warp kernel (Eq. Rik, UpdateMu,
+    UpdateSigS/C)."""
+    import torch
+    from synth.voronoi_torch import voronoi_batch
+    n, H, W = 6, 321, 481
+    buf = voronoi_batch(W, H, 150, 8.0, list(range(40, 40 + n)))
+    imgs = [buf[i] for i in range(n)]
+    bt = gm.SuperpixelsBatch([(H, W)] * n, spacing=15, colour=colour)
+    if start == "learned":
+        from paper_1612_08792_gb300.learned_init import load_pretrained
+        bt.set_init_net(load_pretrained(15))
+    for bps in (6, 7):
+        gen = bt.first_pass_partials(imgs, bps, diagonal=False)
+        diag = bt.first_pass_partials(imgs, bps, diagonal=True)
+        assert gen.shape == (bt.info()[2], 136) and np.isfinite(gen).all()
+        assert gen[:, 0:135:15].sum() > 0  # posterior weights present
+        assert np.array_equal(diag, gen), (bps, int((diag != gen).sum()))
+    bt.close()
+    torch.cuda.synchronize()
