@@ -132,3 +132,47 @@ def test_learned_start_then_two_iterations_match_oracle(gm, learned_case, bps):
         mu, cs, cc = bt.get_params(i, K)
         check_image(mu, cs, cc, labels[i].cpu().numpy(), ll[i], refs[i], ("learned", bps, i))
     bt.close()
+
+
+def test_headline_step_at_full_size(gm):
+    """The learned start + 2 iterations on the full headline batch, as bench.py times it: 256
+    held-out 481x321 sRGB images (seeds 1,000,000 + i, 150 regions, sigma 8), spacing 15, RGB8
+    input converted inside the network's first kernel, the autotuner's launch choices.
+    Every label map of the batch: each label is the index of one of its pixel's 3 x 3 seeds
+    (Eq. obtLi, the window of Eq. Ik). Images 0, 127 and 255: theta_2, the labels and L(theta_2)
+    against the oracle (Algorithm 1 steps 2-7) started from the GPU's theta_0 on the GPU's CIELAB."""
+    import torch
+    from paper_1612_08792_gb300.learned_init import load_pretrained
+    from synth.voronoi_torch import voronoi_batch
+    n, W, H, v = 256, 481, 321, 15
+    nx, ny = W // v, H // v
+    K = nx * ny
+    buf = voronoi_batch(W, H, 150, 8.0, range(1_000_000, 1_000_000 + n))
+    imgs = [buf[i] for i in range(n)]
+    net = load_pretrained(v)
+    bt = gm.SuperpixelsBatch([(H, W)] * n, spacing=v)
+    bt.autotune(imgs, reps=2)
+    bt.set_init_net(net)
+    sample = (0, 127, 255)
+    bt.segment(imgs, iters=0)  # theta_0 and the CIELAB of the step's start
+    torch.cuda.synchronize()
+    theta0 = {i: oracle.Theta(*bt.get_params(i, K)) for i in sample}
+    labs = {i: bt.get_lab(i) for i in sample}
+    labels, ll = bt.segment(imgs, iters=2, want_loglik=True)
+    torch.cuda.synchronize()
+    net.check()
+
+    lab_all = torch.stack(labels).long()
+    ys = torch.arange(H, device=lab_all.device).view(1, H, 1)
+    xs = torch.arange(W, device=lab_all.device).view(1, 1, W)
+    kx, ky = lab_all % nx, lab_all // nx
+    assert bool(((lab_all >= 0) & (lab_all < K)).all())
+    assert bool(((kx - xs // v).abs() <= 1).all()) and bool(((ky - ys // v).abs() <= 1).all())
+    assert np.all(np.isfinite(ll))
+
+    for i in sample:
+        ref = oracle.em(labs[i].astype(np.float64), W, H, spacing=v, T=2, theta0=theta0[i])
+        mu, cs, cc = bt.get_params(i, K)
+        check_image(mu, cs, cc, labels[i].cpu().numpy(), ll[i], ref, ("full size", i))
+    bt.close()
+    net.close()
