@@ -145,3 +145,46 @@ def test_first_pass_diagonal_kernel_equals_general(gm, start, colour):
         assert np.array_equal(diag, gen), (bps, int((diag != gen).sum()))
     bt.close()
     torch.cuda.synchronize()
+
+
+def test_batch256_at_full_size(gm):
+    """The batch256 workload at full size, as bench.py times it: 256 sRGB images of the five sizes
+    320x240 ... 1920x1080 (171 Mpx), spacing 15, 10 plain-EM iterations, the autotuner's launch
+    choices. Every label map: each label is one of its pixel's 3 x 3 seeds (Eq. obtLi). The first
+    image of each size: theta_10, labels and L against the oracle (Algorithm 1 steps 1-7) on the
+    GPU's CIELAB."""
+    import torch
+    from synth.voronoi import batch_sizes
+    sizes = batch_sizes(256)
+    cache, imgs = {}, []
+    for i, (Wi, Hi) in enumerate(sizes):  # the bench's images: 4 seeded images per size, reused
+        key = (Wi, Hi, i % 4)
+        if key not in cache:
+            cache[key] = torch.from_numpy(voronoi_image(Wi, Hi, batch_regions(Wi, Hi), 8.0, seed=i % 4)).cuda()
+        imgs.append(cache[key])
+    v, T = 15, 10
+    bt = gm.SuperpixelsBatch([(h, w) for (w, h) in sizes], spacing=v)
+    bt.autotune(imgs, reps=2)
+    labels, ll = bt.segment(imgs, iters=T, want_loglik=True)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(ll))
+    for i, (Wi, Hi) in enumerate(sizes):
+        nx, ny = Wi // v, Hi // v
+        lab_i = labels[i].long()
+        ys = torch.arange(Hi, device=lab_i.device).view(Hi, 1)
+        xs = torch.arange(Wi, device=lab_i.device).view(1, Wi)
+        ok = (lab_i >= 0) & (lab_i < nx * ny) & ((lab_i % nx - xs // v).abs() <= 1) & \
+             ((lab_i // nx - ys // v).abs() <= 1)
+        assert bool(ok.all()), (i, Wi, Hi)
+    for size in sorted(set(sizes)):
+        i = sizes.index(size)
+        Wi, Hi = size
+        ref = oracle.em(bt.get_lab(i).astype(np.float64), Wi, Hi, spacing=v, T=T)
+        mu, cs, cc = bt.get_params(i, (Wi // v) * (Hi // v))
+        assert parity.mean_rel_err(mu, ref.theta.mu) <= parity.MEAN_TOL
+        assert parity.cov_rel_err(cs, ref.theta.cs) <= parity.COV_TOL
+        assert parity.cov_rel_err(cc, ref.theta.cc) <= parity.COV_TOL
+        a, nd, worst = parity.label_report(labels[i].cpu().numpy(), ref.labels, ref.margin)
+        assert a >= parity.LABEL_AGREE and worst < parity.MARGIN_TOL, (size, a, nd, worst)
+        assert abs(ll[i] - ref.loglik[-1]) <= parity.LL_RTOL * abs(ref.loglik[-1]), (size, ll[i], ref.loglik[-1])
+    bt.close()
