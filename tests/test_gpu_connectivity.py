@@ -105,3 +105,29 @@ def test_batch_connectivity(gm):
             total[k] += rst[k]
     assert all(st[k] == total[k] for k in total), (st, total)
     bt.close()
+
+
+def test_batch_connectivity_at_full_size(gm):
+    """The conn256 workload at full size, as bench.py times it: the label maps of 256 held-out
+    481x321 images (seeds 1,000,000 + i, 150 regions, sigma 8) after 10 plain-EM iterations at
+    spacing 15, one batch call of Algorithm 1, step 8. Maps 0, 127 and 255 equal the oracle's
+    on the device CIELAB; every map keeps its labels in [0, K)."""
+    import torch
+    from synth.voronoi_torch import voronoi_batch
+    n, W, H, v = 256, 481, 321, 15
+    K = (W // v) * (H // v)
+    buf = voronoi_batch(W, H, 150, 8.0, range(1_000_000, 1_000_000 + n))
+    bt = gm.SuperpixelsBatch([(H, W)] * n, spacing=v)
+    bt.segment([buf[i] for i in range(n)], iters=10)
+    torch.cuda.synchronize()
+    sample = (0, 127, 255)
+    before = {i: bt.labels[i].cpu().numpy() for i in sample}
+    st = bt.connectivity()
+    torch.cuda.synchronize()
+    for i in sample:
+        ref, _ = oc.enforce_connectivity(before[i], bt.get_lab(i), K)
+        np.testing.assert_array_equal(bt.labels[i].cpu().numpy(), ref)
+    after = torch.stack(bt.labels)
+    assert bool(((after >= 0) & (after < K)).all())
+    assert min(st.values()) >= 0
+    bt.close()

@@ -86,3 +86,24 @@ def test_many_equals_oracle_per_image(gm):
     with pytest.raises(gm.GmmspError):
         gm.gmmsp_segmentation_metrics_many([labels[0], bad], gts[:2], [cases[0][2], cases[1][2]],
                                            [cases[0][3], cases[1][3]])
+
+
+def test_many_at_full_size(gm):
+    """The metrics256 workload at full size, as bench.py times it: BR, UE (Eq. ue) and ASA (Eq.
+    asa) of the label maps of 256 held-out 481x321 images (seeds 1,000,000 + i) after 10
+    plain-EM iterations at spacing 15, against the generator's 150 regions, in one batched call.
+    Maps 0, 127 and 255 equal the oracle's exactly."""
+    import torch
+    from synth.voronoi_torch import voronoi_batch
+    n, W, H, v, G = 256, 481, 321, 15, 150
+    K = (W // v) * (H // v)
+    regs = torch.empty((n, H, W), dtype=torch.int32, device="cuda")
+    buf = voronoi_batch(W, H, G, 8.0, range(1_000_000, 1_000_000 + n), regions_out=regs)
+    bt = gm.SuperpixelsBatch([(H, W)] * n, spacing=v)
+    labels = bt.segment([buf[i] for i in range(n)], iters=10)
+    torch.cuda.synchronize()
+    out = gm.gmmsp_segmentation_metrics_many(labels, [regs[i] for i in range(n)], K, G)
+    assert len(out) == n
+    for i in (0, 127, 255):
+        check_equal(out[i], om.all_metrics(labels[i].cpu().numpy(), regs[i].cpu().numpy(), 2, 0.05))
+    bt.close()
