@@ -823,9 +823,7 @@ class SuperpixelsBatch:
             hit = tuning_cache.lookup(cache, key)
             if hit is not None:
                 gmmsp_batch_set_tuning(self.b, hit["blocks_per_sm"], hit["finalize16"])
-                first = hit.get("first_pass_blocks_per_sm")
-                if isinstance(first, int) and 0 <= first <= 16:
-                    gmmsp_batch_set_first_pass(self.b, first)
+                gmmsp_batch_set_first_pass(self.b, hit.get("first_pass_blocks_per_sm", 0))
                 return hit["blocks_per_sm"], {int(k): float(v) for k, v in hit.get("em_pass_ms", {}).items()}
         best, times = gmmsp_batch_autotune(self.b, images, [self._pitch(t) for t in images], self.labels, reps)
         if key is not None:

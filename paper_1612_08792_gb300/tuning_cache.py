@@ -38,6 +38,9 @@ def lookup(path: str, key: str):
     bps, f16 = entry.get("blocks_per_sm"), entry.get("finalize16")
     if not (isinstance(bps, int) and 1 <= bps <= 16 and isinstance(f16, bool)):
         return None
+    first = entry.get("first_pass_blocks_per_sm", 0)  # 0: the first pass follows blocks_per_sm
+    if not (isinstance(first, int) and not isinstance(first, bool) and 0 <= first <= 16):
+        return None
     return entry
 
 

@@ -22,6 +22,11 @@ def test_round_trip_and_bad_files(tmp_path):
     assert set(json.load(open(path))) == {"j", "k"}
     tc.store(path, "bad", {"blocks_per_sm": 99, "finalize16": False})
     assert tc.lookup(path, "bad") is None                     # out of range entries are ignored
+    tc.store(path, "f", {"blocks_per_sm": 7, "finalize16": False, "first_pass_blocks_per_sm": 6})
+    assert tc.lookup(path, "f")["first_pass_blocks_per_sm"] == 6
+    for bad in (17, -1, "6", True):
+        tc.store(path, "fb", {"blocks_per_sm": 7, "finalize16": False, "first_pass_blocks_per_sm": bad})
+        assert tc.lookup(path, "fb") is None
     with open(path, "w") as fh:
         fh.write("{not json")
     assert tc.lookup(path, "k") is None and tc.load(path) == {}
