@@ -10,10 +10,10 @@
 //  * widen_bits: exact. Every binary32 value is a binary64 value. Subnormal
 //    inputs are left to the caller (false).
 //  * narrow_bits: rounds to nearest, ties to even. It handles zeros and
-//    results in the normal binary32 range, including a rounding carry into the
-//    exponent, which turns the largest finite magnitude into infinity. It
-//    returns false for subnormal or overflowing results and for infinities and
-//    NaNs, which the caller converts with the hardware instruction.
+//    magnitudes in [2^-126, 2^128), including a rounding carry into the
+//    exponent (which takes magnitudes just below 2^128 to infinity). It
+//    returns false for other nonzero magnitudes and for infinities and NaNs,
+//    which the caller converts with the hardware instruction.
 //
 // Pure integer code: the host test suite checks both against the C casts.
 #pragma once
@@ -38,7 +38,8 @@ GMMSP_FPCONV_FN bool widen_bits(uint32_t b, uint32_t& hi, uint32_t& lo) {
   return true;
 }
 
-// binary64 encoding (hi, lo words) -> binary32 encoding, nearest even.
+// binary64 encoding (hi, lo words) -> binary32 encoding, nearest even;
+// false outside zero and [2^-126, 2^128) in magnitude.
 GMMSP_FPCONV_FN bool narrow_bits(uint32_t hi, uint32_t lo, uint32_t& out) {
   const uint32_t sign = hi & 0x80000000u, e = (hi >> 20) & 0x7ffu;
   if (e == 0u && ((hi & 0xfffffu) | lo) == 0u) {  // +-0
